@@ -1,0 +1,895 @@
+/*
+ * spmc_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, serial FP64 CPU restatement of the hp-version time-stepping
+ * spectral Monte Carlo method (residual iteration, Section 2.4 and Algorithm 1),
+ * written from the paper for checking the CUDA path.  Only tests/,
+ * __graft_entry__.smoke() and bench.py's cpu_baseline leg may load it.  It shares
+ * no code, header, table or constant generator with the CUDA library.
+ *
+ * Every routine follows the definition it cites, term by term: no blocking, no
+ * sum factorisation, no precomputed time slices.  The residual at a walker point
+ * is the direct sum over all coefficients of Eq. (u_N).  OpenMP is used only to
+ * run independent nodes side by side; every per-node sum is sequential, so the
+ * result does not depend on the thread count.
+ *
+ * Readings of points where the paper is silent or garbled (each listed with its
+ * reason in the design notes):
+ *   - spatial nodes are Jacobi-Gauss (1,1) interior nodes (Section 2.3);
+ *   - time nodes are shifted LGL, or left Gauss-Radau (includes t_{n-1});
+ *   - b_qk uses reference-interval weights with gamma_q = 2/(2q+1), q < M_n, and
+ *     the discrete norm for q = M_n (Eq. timeLag);
+ *   - -d^2/dx^2 phi_p = (p+1)(p+2) P_p^{(1,1)}, not the printed (p+1) (Eq. u_N);
+ *   - the d/dt coefficients sum over l > q with l+q odd and keep the spatial basis
+ *     phi_p (Legendre derivative identity; the printed P_p^{(1,1)} is garbled);
+ *   - along a walk the integrand time runs backward from t_{n,l} to t_{n-1}
+ *     (Feynman-Kac for the backward heat semigroup, Eq. fkx_2);
+ *   - N_* = max(1, ceil(N_ref (t_{n,l}-t_{n-1})/h_n)) (Eq. time division);
+ *   - walk_mode 0 (the solver's walk): balls inside Omega ("a ball B_r(x_j)
+ *     inside the domain", Section 2.2) of radius min(J, dist to the boundary),
+ *     each step weighted by the ball's mean exit time, the step integral
+ *     estimated at a Green-function point of the ball (the representation
+ *     W(x) E_{Q_r}[f(Y, t_q)] of Lemma 3.3's proof) and a random sub-step time;
+ *     the fixed-radius walk with point evaluation at the centres is unstable
+ *     for the spectral degrees used here;
+ *   - walk_mode 1 (the walk of Table 1): fixed radius J, Q_L sums q = 0..L-1
+ *     with L from Eq. indexL, so L = 0 when X_1 exits;
+ *   - directions: d=1 one sign bit; d=2 angle 2 pi U; d>=3 normalised Box-Muller
+ *     Gaussians (Lemma Xlocation only asks for a uniform direction);
+ *   - the first iterate is the constant-in-time extension of row 0 (Remark 2.1);
+ *   - Philox4x32-10 keyed by the 64-bit seed, counter (word block, sample, node,
+ *     instance|interval|iteration): the paper does not name a generator.
+ *
+ * Parity pins (tests under tests/): Gauss tables against scipy, analysis matrices
+ * against Legendre-form basis values from numpy, reconstruction and derivative
+ * maps against numpy polynomial calculus, the polynomial fixed point (r == 0),
+ * the fixed-step walk mean against an exact lattice Markov-chain computation,
+ * the inside-ball walk against Dynkin's formula, Philox against an independent
+ * implementation, exit probabilities against Table 1, and convergence to
+ * closed-form solutions.  The adjoint is checked by forward-mode
+ * tangents (orc_solve_tangent) and central differences on common random numbers.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_MAXD 5
+#define ORC_MAXN 64
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplies with a     */
+/* Weyl-sequence key schedule.                                                */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+    uint32_t y1 = (uint32_t)prod1;
+    uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+    uint32_t y3 = (uint32_t)prod0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The random words of one walk.  Word w of the walk of (sample, node) in
+ * (instance, interval, iteration) is lane w%4 of Philox at counter
+ * (w/4, sample, node, instance<<20 | interval<<10 | iteration). */
+typedef struct {
+  uint32_t key[2];
+  uint32_t ctr[4];
+  uint32_t block[4];
+  int64_t cached;
+} orc_stream;
+
+static void stream_init(orc_stream* s, uint64_t seed, uint32_t sample, uint32_t node,
+                        int instance, int interval, int iteration) {
+  s->key[0] = (uint32_t)(seed & 0xffffffffu);
+  s->key[1] = (uint32_t)(seed >> 32);
+  s->ctr[0] = 0;
+  s->ctr[1] = sample;
+  s->ctr[2] = node;
+  s->ctr[3] = ((uint32_t)(instance & 0xfff) << 20) | ((uint32_t)(interval & 0x3ff) << 10) |
+              (uint32_t)(iteration & 0x3ff);
+  s->cached = -1;
+}
+
+static uint32_t stream_word(orc_stream* s, int64_t w) {
+  int64_t blk = w / 4;
+  if (blk != s->cached) {
+    s->ctr[0] = (uint32_t)blk;
+    orc_philox4x32_10(s->ctr, s->key, s->block);
+    s->cached = blk;
+  }
+  return s->block[w % 4];
+}
+
+/* Uniform on (0,1) from two words, 53 bits: ((a>>5) 2^26 + (b>>6) + 1/2) 2^-53. */
+double orc_u01_pair(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+/* Words drawn per walk step for dimension d. */
+int orc_words_per_step(int d) {
+  if (d == 1) return 1;
+  if (d == 2) return 2;
+  return 4 * ((d + 1) / 2);
+}
+
+/* Direction theta_q, uniform on S^{d-1} (Lemma Xlocation), from the step's words. */
+static void draw_direction(orc_stream* s, int d, int64_t step_index, double* theta) {
+  int64_t w0 = step_index * (int64_t)orc_words_per_step(d);
+  if (d == 1) {
+    uint32_t a = stream_word(s, w0);
+    theta[0] = (a >> 31) ? -1.0 : 1.0;
+    return;
+  }
+  if (d == 2) {
+    double U = orc_u01_pair(stream_word(s, w0), stream_word(s, w0 + 1));
+    theta[0] = cos(2.0 * ORC_PI * U);
+    theta[1] = sin(2.0 * ORC_PI * U);
+    return;
+  }
+  double z[ORC_MAXD + 1];
+  int npairs = (d + 1) / 2;
+  for (int k = 0; k < npairs; ++k) {
+    double U1 = orc_u01_pair(stream_word(s, w0 + 4 * k), stream_word(s, w0 + 4 * k + 1));
+    double U2 = orc_u01_pair(stream_word(s, w0 + 4 * k + 2), stream_word(s, w0 + 4 * k + 3));
+    double R = sqrt(-2.0 * log(U1));
+    z[2 * k] = R * cos(2.0 * ORC_PI * U2);
+    z[2 * k + 1] = R * sin(2.0 * ORC_PI * U2);
+  }
+  double nrm = 0.0;
+  for (int e = 0; e < d; ++e) nrm += z[e] * z[e];
+  nrm = sqrt(nrm);
+  for (int e = 0; e < d; ++e) theta[e] = z[e] / nrm;
+}
+
+/* Inside-ball walk (walk_mode 0): the words of one step, padded to whole
+ * Philox blocks: [next-step direction | Green point direction | Green radius
+ * uniform(s), a pair of words each | one word choosing the time sub-point]. */
+int orc_ball_words_per_step(int d) {
+  int wd = orc_words_per_step(d);
+  int wr = (d == 2) ? 4 : 2;
+  int w = 2 * wd + wr + 1;
+  return (w + 3) / 4 * 4;
+}
+
+/* Direction from the words starting at w0 (same laws as draw_direction). */
+static void direction_at(orc_stream* s, int d, int64_t w0, double* theta) {
+  if (d == 1) {
+    theta[0] = (stream_word(s, w0) >> 31) ? -1.0 : 1.0;
+    return;
+  }
+  if (d == 2) {
+    double U = orc_u01_pair(stream_word(s, w0), stream_word(s, w0 + 1));
+    theta[0] = cos(2.0 * ORC_PI * U);
+    theta[1] = sin(2.0 * ORC_PI * U);
+    return;
+  }
+  double z[ORC_MAXD + 1];
+  int npairs = (d + 1) / 2;
+  for (int k = 0; k < npairs; ++k) {
+    double U1 = orc_u01_pair(stream_word(s, w0 + 4 * k), stream_word(s, w0 + 4 * k + 1));
+    double U2 = orc_u01_pair(stream_word(s, w0 + 4 * k + 2), stream_word(s, w0 + 4 * k + 3));
+    double R = sqrt(-2.0 * log(U1));
+    z[2 * k] = R * cos(2.0 * ORC_PI * U2);
+    z[2 * k + 1] = R * sin(2.0 * ORC_PI * U2);
+  }
+  double nrm = 0.0;
+  for (int e = 0; e < d; ++e) nrm += z[e] * z[e];
+  nrm = sqrt(nrm);
+  for (int e = 0; e < d; ++e) theta[e] = z[e] / nrm;
+}
+
+/* Radial law of the ball's Green function G_r(0, y) (the expected occupation
+ * density of Brownian motion started at the centre and killed on the sphere),
+ * as a fraction v = |y|/r: d=1: density 2(1-v); d=2: density 4 v log(1/v);
+ * d>=3: density proportional to v - v^{d-1}. */
+double orc_green_radius(int d, double U1, double U2) {
+  if (d == 1) return 1.0 - sqrt(U1);
+  if (d == 2) return sqrt(U1 * U2);
+  /* CDF F(v) = (d v^2 - 2 v^d)/(d-2), solved for F(v) = U1 by bisection */
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 60; ++it) {
+    double v = 0.5 * (lo + hi);
+    double vd = 1.0;
+    for (int k = 0; k < d; ++k) vd *= v;
+    double F = (d * v * v - 2.0 * vd) / (d - 2.0);
+    if (F < U1) lo = v; else hi = v;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Orthogonal polynomials (Section 2.3).                                      */
+/* ------------------------------------------------------------------------- */
+/* Legendre L_0..L_m at x by the three-term recurrence. */
+void orc_legendre(int m, double x, double* L) {
+  L[0] = 1.0;
+  if (m >= 1) L[1] = x;
+  for (int k = 1; k < m; ++k) L[k + 1] = ((2.0 * k + 1.0) * x * L[k] - k * L[k - 1]) / (k + 1.0);
+}
+
+/* Jacobi P_0^{(1,1)}..P_m^{(1,1)} at x:
+ * n(n+2) P_n = (2n+1)(n+1) x P_{n-1} - n(n+1) P_{n-2}, P_0 = 1, P_1 = 2x. */
+void orc_jacobi11(int m, double x, double* P) {
+  P[0] = 1.0;
+  if (m >= 1) P[1] = 2.0 * x;
+  for (int n = 2; n <= m; ++n)
+    P[n] = ((2.0 * n + 1.0) * (n + 1.0) * x * P[n - 1] - n * (n + 1.0) * P[n - 2]) / (n * (n + 2.0));
+}
+
+/* Babuska-Shen basis phi_p = (1-x^2) P_p^{(1,1)}, p = 0..m (Section 2.3). */
+void orc_phi(int m, double x, double* phi) {
+  double P[ORC_MAXN + 2];
+  orc_jacobi11(m, x, P);
+  for (int p = 0; p <= m; ++p) phi[p] = (1.0 - x * x) * P[p];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-type nodes and weights.                                              */
+/* ------------------------------------------------------------------------- */
+/* Jacobi-Gauss (1,1): the n zeros of P_n^{(1,1)} and the weights for the
+ * weight function (1-x^2):  w_j = 8(n+1)/((n+2)(1-x_j^2) P_n'(x_j)^2), with
+ * (1-x^2) P_n' = (n+1) P_{n-1} - n x P_n.  Newton with deflation of the roots
+ * already found, started from Chebyshev-type guesses. */
+void orc_jg11_nodes(int n, double* x, double* w) {
+  double P[ORC_MAXN + 2];
+  for (int j = 0; j < n; ++j) {
+    double z = -cos(ORC_PI * (j + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      orc_jacobi11(n, z, P);
+      double dP = ((n + 1.0) * P[n - 1] - n * z * P[n]) / (1.0 - z * z);
+      double defl = 0.0;
+      for (int k = 0; k < j; ++k) defl += 1.0 / (z - x[k]);
+      double step = P[n] / (dP - P[n] * defl);
+      z -= step;
+      if (fabs(step) < 1e-16 * (1.0 + fabs(z))) break;
+    }
+    x[j] = z;
+  }
+  /* sort ascending */
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b)
+      if (x[b] < x[a]) { double t = x[a]; x[a] = x[b]; x[b] = t; }
+  for (int j = 0; j < n; ++j) {
+    orc_jacobi11(n, x[j], P);
+    double dP = ((n + 1.0) * P[n - 1] - n * x[j] * P[n]) / (1.0 - x[j] * x[j]);
+    w[j] = 8.0 * (n + 1.0) / ((n + 2.0) * (1.0 - x[j] * x[j]) * dP * dP);
+  }
+}
+
+/* Legendre-Gauss-Lobatto, M+1 points: -1, the zeros of L_M' (which are the
+ * Jacobi-Gauss (1,1) nodes of order M-1), +1; w_k = 2/(M(M+1) L_M(x_k)^2). */
+void orc_lgl_nodes(int M, double* xi, double* w) {
+  double L[ORC_MAXN + 2], dummy[ORC_MAXN + 2];
+  xi[0] = -1.0;
+  xi[M] = 1.0;
+  if (M >= 2) orc_jg11_nodes(M - 1, xi + 1, dummy);
+  for (int k = 0; k <= M; ++k) {
+    orc_legendre(M, xi[k], L);
+    w[k] = 2.0 / (M * (M + 1.0) * L[M] * L[M]);
+  }
+}
+
+/* Left Gauss-Radau, M+1 points including -1: the zeros of L_M + L_{M+1};
+ * w_0 = 2/(M+1)^2, w_k = (1-x_k)/((M+1)^2 L_M(x_k)^2). */
+void orc_radau_left_nodes(int M, double* xi, double* w) {
+  double L[ORC_MAXN + 3];
+  xi[0] = -1.0;
+  for (int j = 1; j <= M; ++j) {
+    double z = -cos(ORC_PI * (2.0 * j) / (2.0 * M + 1.0));
+    for (int it = 0; it < 100; ++it) {
+      orc_legendre(M + 1, z, L);
+      double F = L[M] + L[M + 1];
+      /* (1-z^2) L_m' = m (L_{m-1} - z L_m) */
+      double dLM = M * (L[M - 1] - z * L[M]) / (1.0 - z * z);
+      double dLM1 = (M + 1.0) * (L[M] - z * L[M + 1]) / (1.0 - z * z);
+      double dF = dLM + dLM1;
+      double defl = 0.0;
+      for (int k = 0; k < j; ++k) defl += 1.0 / (z - xi[k]);
+      double step = F / (dF - F * defl);
+      z -= step;
+      if (fabs(step) < 1e-16 * (1.0 + fabs(z))) break;
+    }
+    xi[j] = z;
+  }
+  for (int a = 1; a <= M; ++a)
+    for (int b = a + 1; b <= M; ++b)
+      if (xi[b] < xi[a]) { double t = xi[a]; xi[a] = xi[b]; xi[b] = t; }
+  for (int k = 0; k <= M; ++k) {
+    orc_legendre(M, xi[k], L);
+    w[k] = (k == 0) ? 2.0 / ((M + 1.0) * (M + 1.0))
+                    : (1.0 - xi[k]) / ((M + 1.0) * (M + 1.0) * L[M] * L[M]);
+  }
+}
+
+void orc_time_nodes(int family, int M, double* xi, double* w) {
+  if (family == 0) orc_lgl_nodes(M, xi, w);
+  else orc_radau_left_nodes(M, xi, w);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Analysis matrices (Eqs. spacelag, timeLag).                                */
+/* ------------------------------------------------------------------------- */
+/* A[p*n + j] = omega_j P_p^{(1,1)}(x_j) / ((1-x_j^2) gamma~_p),
+ * gamma~_p = 8(p+1)/((2p+3)(p+2)). */
+void orc_space_analysis(int n, double* A) {
+  double x[ORC_MAXN], w[ORC_MAXN], P[ORC_MAXN + 2];
+  orc_jg11_nodes(n, x, w);
+  for (int j = 0; j < n; ++j) {
+    orc_jacobi11(n - 1, x[j], P);
+    for (int p = 0; p < n; ++p) {
+      double gt = 8.0 * (p + 1.0) / ((2.0 * p + 3.0) * (p + 2.0));
+      A[p * n + j] = w[j] * P[p] / ((1.0 - x[j] * x[j]) * gt);
+    }
+  }
+}
+
+/* B[q*(M+1) + k] = L_q(xi_k) w_k / gamma_q on the reference interval:
+ * gamma_q = 2/(2q+1) for q < M, gamma_M = sum_k L_M(xi_k)^2 w_k. */
+void orc_time_analysis(int family, int M, double* B) {
+  double xi[ORC_MAXN + 1], w[ORC_MAXN + 1], L[ORC_MAXN + 2];
+  double Lv[(ORC_MAXN + 1) * (ORC_MAXN + 1)];
+  orc_time_nodes(family, M, xi, w);
+  for (int k = 0; k <= M; ++k) {
+    orc_legendre(M, xi[k], L);
+    for (int q = 0; q <= M; ++q) Lv[q * (M + 1) + k] = L[q];
+  }
+  for (int q = 0; q <= M; ++q) {
+    double gamma;
+    if (q < M) gamma = 2.0 / (2.0 * q + 1.0);
+    else {
+      gamma = 0.0;
+      for (int k = 0; k <= M; ++k) gamma += Lv[q * (M + 1) + k] * Lv[q * (M + 1) + k] * w[k];
+    }
+    for (int k = 0; k <= M; ++k) B[q * (M + 1) + k] = Lv[q * (M + 1) + k] * w[k] / gamma;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Problem description.                                                       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int dim;          /* d, Omega = (-1,1)^d */
+  int n_space;      /* JG(1,1) nodes per dimension = spatial modes per dimension */
+  int time_family;  /* 0 = LGL, 1 = left Gauss-Radau */
+  int n_ref;        /* N_* rule: N_* = max(1, ceil(n_ref (t_l - t_{n-1}) / h_n)) */
+  int64_t M;        /* samples per node */
+  double kappa;     /* diffusion coefficient: L = -kappa Delta */
+  uint64_t seed;
+  int instance;
+  int f_kind;       /* 0: f = s (c0 + c1 u + c2 u^2 + c3 u^3); 1: f = s sin(u) */
+  double f_coef[4];
+  double f_scale;   /* s */
+  int ex_kind;      /* 0: none; 1: e^{-beta t} prod sin(pi x_e); 2: e^{-beta t} prod cos(pi x_e/2);
+                       3: (1+t+t^2) prod (1-x_e^2)(1+x_e) */
+  double ex_beta;
+  int n_threads;
+  int walk_mode;    /* 0: balls inside Omega (radius min(J, dist)), 1: fixed radius J (Lemma Xlocation) */
+  double shell;     /* inside-ball walk: absorbed once dist(X, boundary) < shell */
+  int max_steps;    /* inside-ball walk: cap on the number of quadrature terms */
+  int n_sub;        /* inside-ball walk: time sub-points per full step (a power of two) */
+} orc_problem;
+
+static int64_t ipow(int64_t b, int e) { int64_t r = 1; while (e-- > 0) r *= b; return r; }
+
+double orc_f(const orc_problem* pb, double u) {
+  if (pb->f_kind == 1) return pb->f_scale * sin(u);
+  return pb->f_scale * (pb->f_coef[0] + u * (pb->f_coef[1] + u * (pb->f_coef[2] + u * pb->f_coef[3])));
+}
+
+double orc_df(const orc_problem* pb, double u) {
+  if (pb->f_kind == 1) return pb->f_scale * cos(u);
+  return pb->f_scale * (pb->f_coef[1] + u * (2.0 * pb->f_coef[2] + 3.0 * u * pb->f_coef[3]));
+}
+
+/* d f / d s (the reaction scale), used by the tangent solve. */
+static double orc_df_ds(const orc_problem* pb, double u) {
+  if (pb->f_kind == 1) return sin(u);
+  return pb->f_coef[0] + u * (pb->f_coef[1] + u * (pb->f_coef[2] + u * pb->f_coef[3]));
+}
+
+/* Manufactured exact solution and its derivatives. */
+double orc_exact(const orc_problem* pb, const double* x, double t) {
+  int d = pb->dim;
+  double v = 1.0;
+  if (pb->ex_kind == 1) {
+    for (int e = 0; e < d; ++e) v *= sin(ORC_PI * x[e]);
+    return exp(-pb->ex_beta * t) * v;
+  }
+  if (pb->ex_kind == 2) {
+    for (int e = 0; e < d; ++e) v *= cos(0.5 * ORC_PI * x[e]);
+    return exp(-pb->ex_beta * t) * v;
+  }
+  if (pb->ex_kind == 3) {
+    for (int e = 0; e < d; ++e) v *= (1.0 - x[e] * x[e]) * (1.0 + x[e]);
+    return (1.0 + t + t * t) * v;
+  }
+  return 0.0;
+}
+
+/* Source added to f so that the exact solution solves
+ * d_t u + kappa (-Delta) u = f(u) + f_add: f_add = d_t u - kappa Delta u - f(u). */
+double orc_source(const orc_problem* pb, const double* x, double t) {
+  if (pb->ex_kind == 0) return 0.0;
+  int d = pb->dim;
+  double u = orc_exact(pb, x, t);
+  double dtu, mlap;
+  if (pb->ex_kind == 1) { dtu = -pb->ex_beta * u; mlap = d * ORC_PI * ORC_PI * u; }
+  else if (pb->ex_kind == 2) { dtu = -pb->ex_beta * u; mlap = d * 0.25 * ORC_PI * ORC_PI * u; }
+  else {
+    /* u = T(t) prod g(x_e), g = (1-x^2)(1+x) = 1 + x - x^2 - x^3, -g'' = 2 + 6x */
+    double T = 1.0 + t + t * t, g[ORC_MAXD];
+    for (int e = 0; e < d; ++e) g[e] = (1.0 - x[e] * x[e]) * (1.0 + x[e]);
+    double prod = 1.0;
+    for (int e = 0; e < d; ++e) prod *= g[e];
+    dtu = (1.0 + 2.0 * t) * prod;
+    mlap = 0.0;
+    for (int e = 0; e < d; ++e) {
+      double term = 2.0 + 6.0 * x[e];
+      for (int e2 = 0; e2 < d; ++e2) if (e2 != e) term *= g[e2];
+      mlap += term;
+    }
+    mlap *= T;
+  }
+  return dtu + pb->kappa * mlap - orc_f(pb, u);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reconstruction (Eq. u_N and the Remark on tensor products).                */
+/* U[l * S + j]: nodal values, l = 0..Mt time nodes, j spatial linear index   */
+/* with x_1 fastest, S = n^d.  cu[q * S + p], ct[q * S + p]: coefficients of  */
+/* u* in phi_{p_1}..phi_{p_d} L_q and of d_t u* in the same basis.           */
+/* ------------------------------------------------------------------------- */
+void orc_reconstruct(const orc_problem* pb, int Mt, double h, const double* U, double* cu, double* ct) {
+  int d = pb->dim, n = pb->n_space;
+  int64_t S = ipow(n, d);
+  double* A = (double*)malloc(sizeof(double) * n * n);
+  double* B = (double*)malloc(sizeof(double) * (Mt + 1) * (Mt + 1));
+  orc_space_analysis(n, A);
+  orc_time_analysis(pb->time_family, Mt, B);
+  int64_t tot = S * (Mt + 1);
+  double* cur = (double*)malloc(sizeof(double) * tot);
+  double* nxt = (double*)malloc(sizeof(double) * tot);
+  /* time axis: cur[q][j] = sum_k b_qk U[k][j] */
+  for (int q = 0; q <= Mt; ++q)
+    for (int64_t j = 0; j < S; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k <= Mt; ++k) acc += B[q * (Mt + 1) + k] * U[k * S + j];
+      cur[q * S + j] = acc;
+    }
+  /* each spatial axis e: contract j_e with a_{p_e j_e} */
+  for (int e = 0; e < d; ++e) {
+    int64_t stride = ipow(n, e);
+    for (int q = 0; q <= Mt; ++q)
+      for (int64_t idx = 0; idx < S; ++idx) {
+        int pe = (int)((idx / stride) % n);
+        int64_t base = idx - (int64_t)pe * stride;
+        double acc = 0.0;
+        for (int je = 0; je < n; ++je) acc += A[pe * n + je] * cur[q * S + base + je * stride];
+        nxt[q * S + idx] = acc;
+      }
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  memcpy(cu, cur, sizeof(double) * tot);
+  /* d/dt: ct_q = (2/h)(2q+1) sum_{l>q, l+q odd} cu_l  (Legendre derivative identity) */
+  for (int q = 0; q <= Mt; ++q)
+    for (int64_t p = 0; p < S; ++p) {
+      double acc = 0.0;
+      for (int l = q + 1; l <= Mt; l += 2) acc += cu[l * S + p];
+      ct[q * S + p] = (2.0 / h) * (2.0 * q + 1.0) * acc;
+    }
+  free(A); free(B); free(cur); free(nxt);
+}
+
+/* Values of u*, d_t u* and -Delta u* at (x, xi) by the direct sum over all
+ * coefficients (Eq. u_N, with -d^2 phi_p = (p+1)(p+2) P_p^{(1,1)} per axis). */
+void orc_eval(const orc_problem* pb, int Mt, const double* cu, const double* ct, const double* x,
+              double xi, double* u_out, double* dtu_out, double* mlap_out) {
+  int d = pb->dim, n = pb->n_space;
+  int64_t S = ipow(n, d);
+  double phi[ORC_MAXD][ORC_MAXN + 2], P[ORC_MAXD][ORC_MAXN + 2], L[ORC_MAXN + 2];
+  for (int e = 0; e < d; ++e) {
+    orc_jacobi11(n - 1, x[e], P[e]);
+    orc_phi(n - 1, x[e], phi[e]);
+  }
+  orc_legendre(Mt, xi, L);
+  double u = 0.0, dtu = 0.0, mlap = 0.0;
+  for (int q = 0; q <= Mt; ++q)
+    for (int64_t idx = 0; idx < S; ++idx) {
+      int p[ORC_MAXD];
+      int64_t r = idx;
+      for (int e = 0; e < d; ++e) { p[e] = (int)(r % n); r /= n; }
+      double prod = L[q];
+      for (int e = 0; e < d; ++e) prod *= phi[e][p[e]];
+      double lap = 0.0;
+      for (int e = 0; e < d; ++e) {
+        double term = L[q] * (p[e] + 1.0) * (p[e] + 2.0) * P[e][p[e]];
+        for (int e2 = 0; e2 < d; ++e2) if (e2 != e) term *= phi[e2][p[e2]];
+        lap += term;
+      }
+      u += cu[q * S + idx] * prod;
+      dtu += ct[q * S + idx] * prod;
+      mlap += cu[q * S + idx] * lap;
+    }
+  *u_out = u; *dtu_out = dtu; *mlap_out = mlap;
+}
+
+/* Residual of the error equation (Eq. ufg_ep1):
+ * r = f(u*) + f_add - d_t u* + kappa Delta u*. */
+double orc_residual(const orc_problem* pb, int Mt, double t0, double h, const double* cu,
+                    const double* ct, const double* x, double tau) {
+  double xi = (2.0 * tau - t0 - (t0 + h)) / h;
+  double u, dtu, mlap;
+  orc_eval(pb, Mt, cu, ct, x, xi, &u, &dtu, &mlap);
+  return orc_f(pb, u) + orc_source(pb, x, tau) - dtu - pb->kappa * mlap;
+}
+
+/* N_* for a time node at s = t_{n,l} - t_{n-1} in an interval of length h. */
+int orc_nstar(int n_ref, double s, double h) {
+  double v = ceil((double)n_ref * s / h - 1e-9);
+  return v < 1.0 ? 1 : (int)v;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One walk (Lemma Xlocation, Eqs. indexL and interIQ), as the list of its    */
+/* quadrature terms: Q = sum_i w_i r(Y_i, tau_i).                             */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int Mt; double t0, h; const double* cu; const double* ct;
+  int interval, iteration;
+} orc_interval_ctx;
+
+/* The quadrature points of one walk: for term i, the point pts[i*d..], the
+ * time taus[i] and the weight wts[i] (at most cap terms).  Returns L. */
+int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node_lin, uint32_t sample,
+                    const double* x_start, double t_node, int nstar, double* pts, double* taus, double* wts,
+                    int cap, double* x_end) {
+  int d = pb->dim;
+  orc_stream st;
+  stream_init(&st, pb->seed, sample, node_lin, pb->instance, ic->interval, ic->iteration);
+  double s = t_node - ic->t0;
+  double delta = s / nstar;
+  double J = sqrt(2.0 * d * pb->kappa * delta);
+  double X[ORC_MAXD], Xn[ORC_MAXD], theta[ORC_MAXD];
+  for (int e = 0; e < d; ++e) X[e] = x_start[e];
+  int L = 0;
+  if (pb->walk_mode == 1) {
+    /* Fixed radius J; the walk ends at the first step centre outside Omega
+     * (Eq. indexL); the term q counts when X_{q+1} is still inside. */
+    for (int q = 0; q < nstar; ++q) {
+      draw_direction(&st, d, q, theta);
+      int inside = 1;
+      for (int e = 0; e < d; ++e) {
+        Xn[e] = X[e] + J * theta[e];
+        if (!(Xn[e] > -1.0 && Xn[e] < 1.0)) inside = 0;
+      }
+      if (!inside) break;
+      if (L < cap) {
+        for (int e = 0; e < d; ++e) pts[L * d + e] = X[e];
+        taus[L] = t_node - q * delta;
+        wts[L] = delta;
+      }
+      L = q + 1;
+      for (int e = 0; e < d; ++e) X[e] = Xn[e];
+    }
+    if (x_end) for (int e = 0; e < d; ++e) x_end[e] = X[e];
+    return L;
+  }
+  /* Balls inside Omega (walk-on-spheres).  The ball around X_q has radius
+   * r_q = min(J, dist(X_q, boundary)), so it lies in Omega, and weight w_q equal
+   * to its mean exit time: Delta for a full ball, r_q^2/(2 d kappa) for a shrunk
+   * one, cut to the time left.  The per-step integral of the residual is
+   * estimated at one point Y_q of the ball drawn from its Green function G_r
+   * (the per-step representation W E_{Q_r}[f(Y, t_q)] of the error analysis)
+   * and at one of n_sub sub-step midpoints of the step, drawn uniformly: path
+   * time runs on the grid tau_m = t_{n,l} - (m + 1/2) delta, delta = Delta/n_sub.
+   * The clock is (k sub-steps done, fraction f of the next): a full ball
+   * advances k by n_sub; a shrunk ball is evaluated at the sub-step it sits in
+   * and advances f.  The walk is absorbed once dist < shell and ends when the
+   * time s is used up.  Q = sum_q w_q r(Y_q, tau_{m_q}). */
+  int wd = orc_words_per_step(d);
+  int64_t W = orc_ball_words_per_step(d);
+  int G = pb->n_sub;
+  int gbits = 0;
+  while ((1 << gbits) < G) ++gbits;
+  int64_t Ktot = (int64_t)G * nstar;
+  double sub = delta / G;
+  int64_t k = 0;
+  double f = 0.0;
+  for (int q = 0; q < pb->max_steps; ++q) {
+    double dist = 1.0;
+    for (int e = 0; e < d; ++e) {
+      double de = 1.0 - fabs(X[e]);
+      if (de < dist) dist = de;
+    }
+    if (dist < pb->shell) break;
+    int64_t w0 = (int64_t)q * W;
+    uint32_t gword = stream_word(&st, w0 + 2 * wd + ((d == 2) ? 4 : 2));
+    int g = gbits ? (int)(gword >> (32 - gbits)) : 0;
+    double left = (double)(Ktot - k) * sub - f;
+    double w;
+    int64_t m;
+    int last = 0;
+    double r;
+    if (J <= dist) {
+      r = J;
+      w = delta;
+      if (k + G >= Ktot) {
+        /* the last (possibly partial) full step: the sub-points still ahead */
+        int64_t ahead = Ktot - k;
+        m = k + (gbits ? (int64_t)(((uint64_t)gword * (uint64_t)ahead) >> 32) : 0);
+        w = left;
+        last = 1;
+      } else {
+        m = k + g;
+        k += G;
+      }
+    } else {
+      r = dist;
+      w = (r * r) / (2.0 * d * pb->kappa);
+      m = k;
+      if (w >= left) { w = left; last = 1; }
+      else {
+        f += w;
+        while (f >= sub) { f -= sub; ++k; }
+        if (k >= Ktot) last = 1;
+      }
+    }
+    double thg[ORC_MAXD], Y[ORC_MAXD];
+    direction_at(&st, d, w0 + wd, thg);
+    int64_t wr = w0 + 2 * wd;
+    double U1 = orc_u01_pair(stream_word(&st, wr), stream_word(&st, wr + 1));
+    double U2 = (d == 2) ? orc_u01_pair(stream_word(&st, wr + 2), stream_word(&st, wr + 3)) : 0.0;
+    double v = orc_green_radius(d, U1, U2);
+    for (int e = 0; e < d; ++e) Y[e] = X[e] + r * v * thg[e];
+    double tau = t_node - ((double)m + 0.5) * sub;
+    if (L < cap) {
+      for (int e = 0; e < d; ++e) pts[L * d + e] = Y[e];
+      taus[L] = tau;
+      wts[L] = w;
+    }
+    L = q + 1;
+    if (last) break;
+    direction_at(&st, d, w0, theta);
+    for (int e = 0; e < d; ++e) X[e] = X[e] + r * theta[e];
+  }
+  if (x_end) for (int e = 0; e < d; ++e) x_end[e] = X[e];
+  return L;
+}
+
+#define ORC_WALK_CAP 8192
+
+/* One walk's Q = sum_i w_i r(Y_i, tau_i) (integrand 1 when ic->cu == NULL). */
+double orc_walk(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node_lin, uint32_t sample,
+                const double* x_start, double t_node, int nstar, int* L_out, double* x_end) {
+  int d = pb->dim;
+  double* pts = (double*)malloc(sizeof(double) * ORC_WALK_CAP * d);
+  double* taus = (double*)malloc(sizeof(double) * ORC_WALK_CAP);
+  double* wts = (double*)malloc(sizeof(double) * ORC_WALK_CAP);
+  int L = orc_walk_points(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, ORC_WALK_CAP, x_end);
+  double sum = 0.0;
+  for (int i = 0; i < L && i < ORC_WALK_CAP; ++i) {
+    double r = ic->cu ? orc_residual(pb, ic->Mt, ic->t0, ic->h, ic->cu, ic->ct, pts + i * d, taus[i]) : 1.0;
+    sum += wts[i] * r;
+  }
+  free(pts); free(taus); free(wts);
+  if (L_out) *L_out = L;
+  return sum;
+}
+
+/* Spatial node coordinates of linear index j. */
+static void node_coords(int d, int n, const double* xs, int64_t j, double* x) {
+  for (int e = 0; e < d; ++e) { x[e] = xs[j % n]; j /= n; }
+}
+
+/* eps at one node (Eq. varepsilon_1): Neumaier-compensated sum of Q_L over the
+ * samples in order, divided by M. */
+double orc_node_eps(const orc_problem* pb, const orc_interval_ctx* ic, int64_t j, int l) {
+  int d = pb->dim, n = pb->n_space;
+  double xs[ORC_MAXN], ws[ORC_MAXN], xi[ORC_MAXN + 1], wt[ORC_MAXN + 1], x[ORC_MAXD];
+  orc_jg11_nodes(n, xs, ws);
+  orc_time_nodes(pb->time_family, ic->Mt, xi, wt);
+  node_coords(d, n, xs, j, x);
+  double s = (xi[l] + 1.0) * 0.5 * ic->h;
+  double t_node = ic->t0 + s;
+  int nstar = orc_nstar(pb->n_ref, s, ic->h);
+  int64_t S = ipow(n, d);
+  uint32_t node_lin = (uint32_t)(l * S + j);
+  double sum = 0.0, comp = 0.0;
+  for (int64_t i = 0; i < pb->M; ++i) {
+    double Q = orc_walk(pb, ic, node_lin, (uint32_t)i, x, t_node, nstar, NULL, NULL);
+    double t = sum + Q;
+    if (fabs(sum) >= fabs(Q)) comp += (sum - t) + Q; else comp += (Q - t) + sum;
+    sum = t;
+  }
+  return (sum + comp) / (double)pb->M;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Residual iterations on one interval (Algorithm 1, Steps 1-3).             */
+/* U is updated in place; eps_out (optional) receives eps for every node.    */
+/* Returns the number of iterations run; max_eps[k] per iteration.           */
+/* ------------------------------------------------------------------------- */
+int orc_iterate(const orc_problem* pb, int interval, double t0, double t1, int Mt, double* U,
+                int first_iteration, int n_iter, double tol, double* max_eps, double* eps_out) {
+  int d = pb->dim, n = pb->n_space;
+  int64_t S = ipow(n, d);
+  double h = t1 - t0;
+  double* cu = (double*)malloc(sizeof(double) * S * (Mt + 1));
+  double* ct = (double*)malloc(sizeof(double) * S * (Mt + 1));
+  double* eps = (double*)malloc(sizeof(double) * S * (Mt + 1));
+  int done = 0;
+  for (int k = 0; k < n_iter; ++k) {
+    orc_reconstruct(pb, Mt, h, U, cu, ct);
+    orc_interval_ctx ic = {Mt, t0, h, cu, ct, interval, first_iteration + k};
+    int64_t nn = S * Mt;
+#ifdef _OPENMP
+    int nt = pb->n_threads > 0 ? pb->n_threads : 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int64_t a = 0; a < nn; ++a) {
+      int l = 1 + (int)(a / S);
+      int64_t j = a % S;
+      eps[l * S + j] = orc_node_eps(pb, &ic, j, l);
+    }
+    double mx = 0.0;
+    for (int l = 1; l <= Mt; ++l)
+      for (int64_t j = 0; j < S; ++j) {
+        U[l * S + j] += eps[l * S + j];
+        if (fabs(eps[l * S + j]) > mx) mx = fabs(eps[l * S + j]);
+      }
+    if (max_eps) max_eps[k] = mx;
+    if (eps_out) {
+      for (int64_t j = 0; j < S; ++j) eps_out[j] = 0.0;
+      memcpy(eps_out + S, eps + S, sizeof(double) * S * Mt);
+    }
+    ++done;
+    if (tol > 0.0 && mx < tol) break;
+  }
+  free(cu); free(ct); free(eps);
+  return done;
+}
+
+/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:
+ * u*(x_j, t_n) = sum_q sum_k b_qk U[k][j] L_q(1)  (Algorithm 1, Step 4). */
+void orc_handoff(const orc_problem* pb, int Mt, const double* U, double* row) {
+  int64_t S = ipow(pb->n_space, pb->dim);
+  double* B = (double*)malloc(sizeof(double) * (Mt + 1) * (Mt + 1));
+  orc_time_analysis(pb->time_family, Mt, B);
+  for (int64_t j = 0; j < S; ++j) {
+    double acc = 0.0;
+    for (int q = 0; q <= Mt; ++q)
+      for (int k = 0; k <= Mt; ++k) acc += B[q * (Mt + 1) + k] * U[k * S + j];
+    row[j] = acc;
+  }
+  free(B);
+}
+
+/* hp solve (Algorithm 1): n_int intervals with breaks t[0..n_int] and degrees
+ * Mt[0..n_int-1]; u0 holds the initial nodal values (S of them).  U_all
+ * receives, interval after interval, the (Mt+1) x S nodal blocks.  iters_out
+ * (optional) receives the iteration count per interval. */
+void orc_solve(const orc_problem* pb, int n_int, const double* t, const int* Mt, int K, double tol,
+               const double* u0, double* U_all, int* iters_out) {
+  int64_t S = ipow(pb->n_space, pb->dim);
+  double* row = (double*)malloc(sizeof(double) * S);
+  memcpy(row, u0, sizeof(double) * S);
+  int64_t off = 0;
+  for (int m = 0; m < n_int; ++m) {
+    double* U = U_all + off;
+    for (int l = 0; l <= Mt[m]; ++l) memcpy(U + l * S, row, sizeof(double) * S);
+    int it = orc_iterate(pb, m, t[m], t[m + 1], Mt[m], U, 1, K, tol, NULL, NULL);
+    if (iters_out) iters_out[m] = it;
+    orc_handoff(pb, Mt[m], U, row);
+    off += (int64_t)(Mt[m] + 1) * S;
+  }
+  free(row);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Forward-mode tangent of the hp solve, for checking gradients.             */
+/* Direction: ds (reaction scale) and du0 (nodal tangent of u0).  The walks  */
+/* do not depend on the parameters (common random numbers), so the tangent   */
+/* of eps is the sample mean of Delta sum r_dot along the same paths, with   */
+/* r_dot = f'(u*) u_dot* + (df/ds) ds - d_t u_dot* - kappa (-Delta u_dot*).   */
+/* dU_all receives the tangent of U_all (same layout).                        */
+/* ------------------------------------------------------------------------- */
+static double walk_tangent(const orc_problem* pb, const orc_interval_ctx* ic, const double* cdu,
+                           const double* cdt, double ds, uint32_t node_lin, uint32_t sample,
+                           const double* x_start, double t_node, int nstar) {
+  int d = pb->dim;
+  double* pts = (double*)malloc(sizeof(double) * ORC_WALK_CAP * d);
+  double* taus = (double*)malloc(sizeof(double) * ORC_WALK_CAP);
+  double* wts = (double*)malloc(sizeof(double) * ORC_WALK_CAP);
+  int L = orc_walk_points(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, ORC_WALK_CAP, NULL);
+  double sum = 0.0;
+  for (int i = 0; i < L && i < ORC_WALK_CAP; ++i) {
+    double xi = (2.0 * taus[i] - ic->t0 - (ic->t0 + ic->h)) / ic->h;
+    double u, dtu, mlap, ud, dtud, mlapd;
+    orc_eval(pb, ic->Mt, ic->cu, ic->ct, pts + i * d, xi, &u, &dtu, &mlap);
+    orc_eval(pb, ic->Mt, cdu, cdt, pts + i * d, xi, &ud, &dtud, &mlapd);
+    sum += wts[i] * (orc_df(pb, u) * ud + orc_df_ds(pb, u) * ds - dtud - pb->kappa * mlapd);
+  }
+  free(pts); free(taus); free(wts);
+  return sum;
+}
+
+void orc_solve_tangent(const orc_problem* pb, int n_int, const double* t, const int* Mt, int K,
+                       const double* u0, const double* du0, double ds, double* U_all, double* dU_all) {
+  int d = pb->dim, n = pb->n_space;
+  int64_t S = ipow(n, d);
+  double* row = (double*)malloc(sizeof(double) * S);
+  double* drow = (double*)malloc(sizeof(double) * S);
+  memcpy(row, u0, sizeof(double) * S);
+  memcpy(drow, du0, sizeof(double) * S);
+  double xs[ORC_MAXN], ws[ORC_MAXN];
+  orc_jg11_nodes(n, xs, ws);
+  int64_t off = 0;
+  for (int m = 0; m < n_int; ++m) {
+    int M_t = Mt[m];
+    double t0 = t[m], h = t[m + 1] - t[m];
+    double* U = U_all + off;
+    double* dU = dU_all + off;
+    for (int l = 0; l <= M_t; ++l) {
+      memcpy(U + l * S, row, sizeof(double) * S);
+      memcpy(dU + l * S, drow, sizeof(double) * S);
+    }
+    double* cu = (double*)malloc(sizeof(double) * S * (M_t + 1));
+    double* ct = (double*)malloc(sizeof(double) * S * (M_t + 1));
+    double* cdu = (double*)malloc(sizeof(double) * S * (M_t + 1));
+    double* cdt = (double*)malloc(sizeof(double) * S * (M_t + 1));
+    double* eps = (double*)malloc(sizeof(double) * S * (M_t + 1));
+    double* deps = (double*)malloc(sizeof(double) * S * (M_t + 1));
+    double xi[ORC_MAXN + 1], wt[ORC_MAXN + 1];
+    orc_time_nodes(pb->time_family, M_t, xi, wt);
+    for (int k = 0; k < K; ++k) {
+      orc_reconstruct(pb, M_t, h, U, cu, ct);
+      orc_reconstruct(pb, M_t, h, dU, cdu, cdt);
+      orc_interval_ctx ic = {M_t, t0, h, cu, ct, m, 1 + k};
+      int64_t nn = S * M_t;
+#ifdef _OPENMP
+      int nt = pb->n_threads > 0 ? pb->n_threads : 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+      for (int64_t a = 0; a < nn; ++a) {
+        int l = 1 + (int)(a / S);
+        int64_t j = a % S;
+        double x[ORC_MAXD];
+        node_coords(d, n, xs, j, x);
+        double s = (xi[l] + 1.0) * 0.5 * h;
+        int nstar = orc_nstar(pb->n_ref, s, h);
+        uint32_t node_lin = (uint32_t)(l * S + j);
+        double sv = 0.0, sd = 0.0;
+        for (int64_t i = 0; i < pb->M; ++i) {
+          sv += orc_walk(pb, &ic, node_lin, (uint32_t)i, x, t0 + s, nstar, NULL, NULL);
+          sd += walk_tangent(pb, &ic, cdu, cdt, ds, node_lin, (uint32_t)i, x, t0 + s, nstar);
+        }
+        eps[l * S + j] = sv / (double)pb->M;
+        deps[l * S + j] = sd / (double)pb->M;
+      }
+      for (int l = 1; l <= M_t; ++l)
+        for (int64_t j = 0; j < S; ++j) {
+          U[l * S + j] += eps[l * S + j];
+          dU[l * S + j] += deps[l * S + j];
+        }
+    }
+    orc_handoff(pb, M_t, U, row);
+    orc_handoff(pb, M_t, dU, drow);
+    free(cu); free(ct); free(cdu); free(cdt); free(eps); free(deps);
+    off += (int64_t)(M_t + 1) * S;
+  }
+  free(row); free(drow);
+}

@@ -1,0 +1,132 @@
+"""Seeded synthetic workloads shaped like the paper's experiments.
+
+This module holds inputs only: problem shapes, meshes, degrees and the random
+per-instance parameters (reaction scales, interval counts, initial-condition
+coefficients, walk start points).  It contains none of the method's arithmetic
+and serves the CUDA path and the CPU oracle alike.
+
+Workloads (sizes as the benchmarks state them; Section 4 examples they stand in for):
+  w1  1-D, u = e^{-t} sin(pi x), f = -u^3 + source, T = 1, one interval,
+      14 interior JG(1,1) nodes (16 LGL points with the two fixed boundary
+      points) x 16 left Gauss-Radau time nodes, M = 4096, K = 6     (Ex. 1 shape)
+  w2  2-D long time, u = e^{-0.1 t} sin(pi x) sin(pi y), f = sin u + source,
+      T = 20 in 20 intervals of h = 1, 24 x 24 JG x 16 LGL, M = 65536, K = 8
+                                                                  (Ex. 2 shape)
+  w3  1-D initial singularity, u0 = |x|^0.6 (1 - x^2), f = s (u - u^3),
+      geometric mesh t_n = T 0.2^{N-n}, degree p_k = 4 + 2k, 32 JG nodes,
+      M = 32768, K = 8; 256 instances, s ~ U[0.5, 2], N ~ U{8..16}  (Ex. 3 shape)
+  w4  5-D, u = e^{-t} prod cos(pi x_e / 2), f = -u^3 + source, T = 0.5,
+      8 JG nodes per axis x 8 LGL, M = 16384, K = 6              (Ex. 4 shape)
+  w5  adjoint: 2-D u_t = 0.01 Delta u + a (u - u^3), T = 5 in 10 intervals,
+      16 x 16 JG x 12 LGL, M = 16384, u0 = sum_{i,j<8} c_ij phi_i phi_j with
+      c_ij = z_ij / (1+i+j)^2, z ~ N(0,1); 128 instances
+The paper uses no public dataset; these synthetic inputs stand in for its
+examples (its data is only available on request).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import List, Optional
+
+import numpy as np
+
+# enums shared by name with the C-ABI header (values fixed there)
+TIME_LGL, TIME_RADAU_LEFT = 0, 1
+F_POLY3, F_SIN = 0, 1
+EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
+
+
+@dataclass
+class Instance:
+    t_breaks: np.ndarray            # n_intervals + 1 breakpoints
+    degrees: np.ndarray             # time degree M_n per interval (M_n + 1 nodes)
+    f_kind: int = F_POLY3
+    f_coef: tuple = (0.0, 0.0, 0.0, -1.0)
+    f_scale: float = 1.0
+    ex_kind: int = EX_NONE
+    ex_beta: float = 1.0
+    u0_kind: str = "exact"          # "exact" (closed form at t=0), "singular", "phi_coef"
+    u0_coef: Optional[np.ndarray] = None   # phi_i phi_j coefficients (u0_kind == "phi_coef")
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n_space: int
+    time_family: int
+    M: int
+    K: int
+    kappa: float = 1.0
+    seed: int = 0
+    n_ref: int = 80
+    n_sub: int = 4
+    shell: float = 1e-4
+    max_steps: int = 512
+    instances: List[Instance] = field(default_factory=list)
+
+    @property
+    def n_nodes_space(self) -> int:
+        return self.n_space ** self.dim
+
+
+def uniform_mesh(T: float, n: int) -> np.ndarray:
+    return np.linspace(0.0, T, n + 1)
+
+
+def geometric_mesh(T: float, n: int, ratio: float = 0.2) -> np.ndarray:
+    t = np.zeros(n + 1)
+    for k in range(1, n + 1):
+        t[k] = T * ratio ** (n - k)
+    return t
+
+
+def w1(M: int = 4096, K: int = 6, seed: int = 0, n_space: int = 14, degree: int = 15) -> Workload:
+    inst = Instance(t_breaks=uniform_mesh(1.0, 1), degrees=np.array([degree]), f_coef=(0, 0, 0, -1.0),
+                    ex_kind=EX_SIN, ex_beta=1.0)
+    return Workload("w1-1d-single-interval", 1, n_space, TIME_RADAU_LEFT, M, K, seed=seed, instances=[inst])
+
+
+def w2(M: int = 65536, K: int = 8, seed: int = 0, n_space: int = 24, degree: int = 15,
+       n_intervals: int = 20, h: float = 1.0) -> Workload:
+    inst = Instance(t_breaks=uniform_mesh(h * n_intervals, n_intervals), degrees=np.full(n_intervals, degree),
+                    f_kind=F_SIN, f_coef=(0, 0, 0, 0), ex_kind=EX_SIN, ex_beta=0.1)
+    return Workload("w2-2d-long-time", 2, n_space, TIME_LGL, M, K, seed=seed, instances=[inst])
+
+
+def w3(M: int = 32768, K: int = 8, seed: int = 0, batch: int = 256, n_space: int = 32, param_seed: int = 1,
+       fixed_intervals: Optional[int] = None) -> Workload:
+    rng = np.random.default_rng(param_seed)
+    insts = []
+    for b in range(batch):
+        s = float(rng.uniform(0.5, 2.0))
+        n = int(rng.integers(8, 17)) if fixed_intervals is None else fixed_intervals
+        deg = np.array([4 + 2 * k for k in range(n)])
+        insts.append(Instance(t_breaks=geometric_mesh(1.0, n), degrees=deg, f_coef=(0, 1.0, 0, -1.0),
+                              f_scale=s, ex_kind=EX_NONE, u0_kind="singular"))
+    return Workload("w3-1d-initial-singularity-batch", 1, n_space, TIME_LGL, M, K, seed=seed, instances=insts)
+
+
+def w4(M: int = 16384, K: int = 6, seed: int = 0, n_space: int = 8, degree: int = 7) -> Workload:
+    inst = Instance(t_breaks=uniform_mesh(0.5, 1), degrees=np.array([degree]), f_coef=(0, 0, 0, -1.0),
+                    ex_kind=EX_COSHALF, ex_beta=1.0)
+    return Workload("w4-5d", 5, n_space, TIME_LGL, M, K, seed=seed, instances=[inst])
+
+
+def w5(M: int = 16384, K: int = 8, seed: int = 0, batch: int = 128, n_space: int = 16, degree: int = 11,
+       n_intervals: int = 10, T: float = 5.0, param_seed: int = 2, n_coef: int = 8) -> Workload:
+    rng = np.random.default_rng(param_seed)
+    insts = []
+    i = np.arange(n_coef)
+    decay = 1.0 / (1.0 + i[:, None] + i[None, :]) ** 2
+    for b in range(batch):
+        z = rng.standard_normal((n_coef, n_coef))
+        insts.append(Instance(t_breaks=uniform_mesh(T, n_intervals), degrees=np.full(n_intervals, degree),
+                              f_coef=(0, 1.0, 0, -1.0), f_scale=1.0, ex_kind=EX_NONE, u0_kind="phi_coef",
+                              u0_coef=z * decay))
+    return Workload("w5-2d-adjoint-batch", 2, n_space, TIME_LGL, M, K, kappa=0.01, seed=seed, instances=insts)
+
+
+def uniform_points(n: int, dim: int, seed: int) -> np.ndarray:
+    """Start points drawn uniformly in (-1,1)^dim (walk statistics, Table 1)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, dim))
