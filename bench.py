@@ -1,0 +1,342 @@
+"""Benchmark: node-samples/s of the hp-version time-stepping spectral Monte Carlo
+hot path on the 2-D long-time workload (24 x 24 JG x 16 LGL nodes per interval,
+T = 20 in 20 intervals of h = 1, M = 65536 samples per node, K = 8 iterations),
+batched mixed precision (FP32 sweep; FP64 reconstruction, update and sums).
+
+One step = one complete hp solve (Algorithm 1 over all 20 intervals).  Inputs are
+resident in HBM; L2 is flushed between steps outside the timed events.  The JSON
+line also carries the FP64 path's throughput on a bounded run, the sweep
+kernel's roofline figures, an end-to-end figure through the C-ABI with host
+buffers, and the CPU oracle's throughput on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--intervals", type=int, default=20, help="intervals of the workload (20 = full)")
+    ap.add_argument("--M", type=int, default=65536)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU legs")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.rows.append([v.strip() for v in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------- helpers
+def workload(args, rank=0):
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w2(M=args.M, n_intervals=args.intervals)
+    wl.seed = rank            # independent replica per rank (weak scaling)
+    return wl
+
+
+def node_samples_per_solve(wl):
+    S = wl.n_space ** wl.dim
+    tot = 0
+    for inst in wl.instances:
+        for Mt in inst.degrees:
+            tot += int(Mt) * S * wl.M * wl.K
+    return tot
+
+
+def flops_per_point(dim, n):
+    """Algorithmic FP32 flops of one residual evaluation (d = 2): three
+    contractions of the n x n slice with the y-basis (3 n^2 FMA), the x-side
+    accumulation (4 n FMA) and the two basis recurrences (about 5 n flops each)."""
+    if dim == 2:
+        return 2 * 3 * n * n + 2 * 4 * n + 2 * 5 * n
+    return 2 * 3 * n + 10 * n
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """The oracle, as it stands, on a bounded sample of the workload: eps at a set
+    of nodes of the first iteration of the first interval (independent nodes run
+    on separate host threads; each node is the oracle's serial sum)."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle as O
+    from paper_2608_22190_b300 import workloads as W
+    inst = wl.instances[0]
+    cores = os.cpu_count() or 1
+    spec = O.Spec(dim=wl.dim, n_space=wl.n_space, time_family=wl.time_family, n_ref=wl.n_ref, M=16,
+                  kappa=wl.kappa, seed=wl.seed, f_kind=inst.f_kind, f_coef=tuple(inst.f_coef),
+                  f_scale=inst.f_scale, ex_kind=inst.ex_kind, ex_beta=inst.ex_beta, n_sub=wl.n_sub,
+                  shell=wl.shell, max_steps=wl.max_steps, n_threads=1)
+    u0 = W.u0_nodal(inst, O.space_nodes_grid(spec))
+    Mt = int(inst.degrees[0])
+    h = float(inst.t_breaks[1] - inst.t_breaks[0])
+    cu, ct = O.reconstruct(spec, Mt, h, np.tile(u0, (Mt + 1, 1)))
+    S = wl.n_space ** wl.dim
+    rng = np.random.default_rng(0)
+
+    def run(n_nodes, m):
+        sp = O.Spec(**{**spec.__dict__, "M": m})
+        nodes = [(int(rng.integers(0, S)), int(rng.integers(1, Mt + 1))) for _ in range(n_nodes)]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda jl: O.node_eps(sp, Mt, 0.0, h, cu, ct, jl[0], jl[1]), nodes))
+        return time.perf_counter() - t0, n_nodes * m
+
+    dt, ns = run(cores, 8)
+    scale = max(1.0, budget_s / max(dt, 1e-3))
+    m = int(min(4096, max(8, 8 * scale)))
+    dt, ns = run(cores, m)
+    return {"value": ns / dt, "unit": "node-samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} nodes x {m} samples, iteration 1 of interval 1 of the 2-D long-time workload "
+                      f"({dt:.1f} s)"}
+
+
+def flush_l2(buf):
+    buf.fill_(1.0)
+
+
+# --------------------------------------------------------------------------- arms
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300.api import Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    prec = L.MIXED if args.precision == "mixed" else L.FP64
+    wl = workload(args, rank)
+    plan = Plan.from_workload(wl, precision=prec)
+    out = torch.empty(plan.total_size(), dtype=torch.float64, device="cuda")
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.solve(out)
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    base_points = plan.stats()["points"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush_l2(l2)
+            evs[i][0].record(stream)
+            plan.solve(out)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    st = plan.stats()
+    plan.set_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    per_step = node_samples_per_solve(wl)
+    value = per_step * world / (ms / 1e3)
+
+    # roofline of the dominant kernel (the sweep): algorithmic flops / its event time
+    points = st["points"] - base_points
+    fpp = flops_per_point(wl.dim, wl.n_space)
+    sweep_s = st["sweep_ms"] / 1e3
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    if prec == L.MIXED:
+        peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock
+        bound = "alu"
+    else:
+        peak = 1.25                                     # nominal FP64 rate of the recipe's table
+        bound = "alu"
+    achieved = points * fpp / sweep_s / 1e12 if sweep_s > 0 else None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "sweep_kernel", "sweep_share": sweep_s * 1e3 / (ms * args.steps),
+            "flops_per_point": fpp, "points_per_step": points // max(1, args.steps),
+            "peak_source": "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz (MEASURED_PEAKS.json)" if prec == L.MIXED
+            else "nominal FP64 1.25 TFLOP/s (recipe table)"}
+    n_iter = wl.K * sum(len(i.degrees) for i in wl.instances)
+    launches_per_step = sum(len(i.degrees) for i in wl.instances) + 4 * n_iter
+
+    line = {"metric": "node-samples/sec & time to L-inf err 1e-6: batched mixed vs plain FP64, 1 B300",
+            "value": value, "unit": "node-samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == L.MIXED else "f64",
+            "data": "synthetic (manufactured solution u = e^{-0.1 t} sin(pi x) sin(pi y))",
+            "config": {"workload": "w2-2d-long-time: 24x24 JG x 16 LGL, T=20 in 20 intervals, M=65536, K=8"
+                       if args.intervals == 20 else f"w2-2d-long-time ({args.intervals} intervals)",
+                       "precision": args.precision, "n_ref": wl.n_ref, "n_sub": wl.n_sub,
+                       "l2": "flushed between steps (256 MB write, outside the timed events)",
+                       "node_samples_per_step": per_step, "step": "one full hp solve (Algorithm 1)"},
+            "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps, "roofline": roof,
+            "wall_s": t_wall}
+
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_leg(args, wl, prec)
+        line["fp64_path"] = fp64_leg(args)
+        line["cpu_baseline"] = cpu_baseline(wl)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e_leg(args, wl, prec):
+    """Same metric through the C-ABI with HOST buffers: every step uploads the
+    initial values from pinned host memory (set_problem + solve) and the solution
+    comes back into pinned host memory."""
+    import numpy as np
+    import torch
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    plan = Plan.from_workload(wl, precision=prec)
+    inst = wl.instances[0]
+    grid = plan.node_grid()
+    u0 = torch.from_numpy(W.u0_nodal(inst, grid)).pin_memory()
+    host_out = torch.empty(plan.total_size(), dtype=torch.float64).pin_memory()
+    steps = max(1, min(args.steps, 2))
+
+    def step():
+        plan.set_problem(0, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, inst.f_scale, inst.ex_kind,
+                         inst.ex_beta, u0.numpy())
+        plan.solve(host_out)
+        torch.cuda.current_stream().synchronize()
+
+    step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = (time.perf_counter() - t0) / steps
+    plan.close()
+    return {"value": node_samples_per_solve(wl) / dt, "unit": "node-samples/s",
+            "h2d_bytes_per_step": int(u0.numel() * 8 + 96), "d2h_bytes_per_step": int(host_out.numel() * 8),
+            "ms_per_step": dt * 1e3}
+
+
+def fp64_leg(args):
+    """The plain FP64 path on a bounded run of the same workload: one interval,
+    K = 8 iterations, M = 8192 samples per node (node-samples/s)."""
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    wl = W.w2(M=8192, n_intervals=1)
+    plan = Plan.from_workload(wl, precision=L.FP64)
+    out = torch.empty(plan.total_size(), dtype=torch.float64, device="cuda")
+    plan.solve(out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plan.solve(out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    plan.close()
+    return {"value": node_samples_per_solve(wl) / (ms / 1e3), "unit": "node-samples/s",
+            "sample": "1 interval x K=8 of the 2-D workload at M=8192 (FP64 sweep)", "ms": ms}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on a bounded sample of the
+    same workload, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args, 0)
+    steps = []
+    for _ in range(max(1, args.warmup) // 3 + args.steps):
+        steps.append(cpu_baseline(wl, budget_s=6.0))
+    vals = [s["value"] for s in steps[-args.steps:]]
+    v = statistics.mean(vals)
+    cb = dict(steps[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "node-samples/sec & time to L-inf err 1e-6: batched mixed vs plain FP64, 1 B300",
+            "value": v, "unit": "node-samples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "w2-2d-long-time (bounded CPU sample)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "node-samples/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

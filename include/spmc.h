@@ -1,0 +1,173 @@
+/*
+ * spmc.h -- C-ABI of the B300 implementation of the hp-version time-stepping
+ * spectral Monte Carlo method for semilinear parabolic equations
+ *
+ *     d_t u - kappa Delta u = f(u) + f_add(x, t)   in (-1,1)^d x (0, T],
+ *     u = 0 on the boundary,  u(., 0) = u0                       (Eq. mainproblem)
+ *
+ * solved interval by interval over an hp time partition (Eq. mesh, Eq.
+ * multischeme) by the residual iteration of Section 2.4 / Algorithm 1: on
+ * interval n, iteration k reconstructs the space-time spectral expansion of the
+ * nodal values (Eq. u_N), estimates the error eps at every space-time node by
+ * Monte Carlo sampling of the Feynman-Kac representation of the error equation
+ * (Eqs. ufg_ep1, varepsilon_1) and updates u <- u + eps (Algorithm 1, Step 3).
+ *
+ * Conventions
+ *  - All entry points return spmc_status; no C++ exception crosses the ABI.
+ *    On failure, spmc_last_error(plan) returns a message (valid until the next
+ *    call on that plan).
+ *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as void*;
+ *    NULL means the legacy default stream).  Calls that return host values
+ *    (max |eps|, statistics) synchronise that stream.
+ *  - Device buffers passed in are owned by the caller; the plan owns its
+ *    workspace and frees it in spmc_destroy.  Host arrays are read during the
+ *    call only.
+ *  - Spatial nodes are the Jacobi-Gauss (1,1) nodes (Section 2.3), n_space per
+ *    axis, linear index j = j_1 + n_space (j_2 + n_space (...)) (x_1 fastest).
+ *    Nodal arrays of one interval are (M_n + 1) rows (time nodes, row 0 at
+ *    t_{n-1}) of n_space^d values.
+ *  - A plan is not thread-safe: one host thread at a time per plan.
+ */
+#ifndef SPMC_H
+#define SPMC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPMC_OK = 0,
+  SPMC_ERR_INVALID = 1,      /* bad argument or plan state */
+  SPMC_ERR_UNSUPPORTED = 2,  /* valid request outside what this build implements */
+  SPMC_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  SPMC_ERR_OOM = 4,          /* device allocation failed */
+  SPMC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  SPMC_ERR_NONFINITE = 6     /* a non-finite eps was produced */
+} spmc_status;
+
+enum { SPMC_TIME_LGL = 0, SPMC_TIME_RADAU_LEFT = 1 };     /* time nodes per interval */
+enum { SPMC_FP64 = 0, SPMC_MIXED = 1 };                    /* sweep arithmetic */
+enum { SPMC_F_POLY3 = 0, SPMC_F_SIN = 1 };                 /* reaction f(u) */
+enum { SPMC_EX_NONE = 0, SPMC_EX_SIN = 1, SPMC_EX_COSHALF = 2, SPMC_EX_POLY = 3 };
+enum { SPMC_U0_NODAL = 0, SPMC_U0_PHI_COEF = 1 };
+
+typedef struct spmc_plan_s* spmc_plan_t;
+
+/* Geometry, discretisation and sampling of a batch of instances.
+ * Section 2.1 (notation), Eq. time division (N_*), Lemma Xlocation (walk). */
+typedef struct {
+  int dim;                  /* d in 1..5 (this build: 1, 2 and 5) */
+  int n_space;              /* JG(1,1) nodes = spatial modes per axis, 2..32 */
+  int time_family;          /* SPMC_TIME_LGL or SPMC_TIME_RADAU_LEFT */
+  int max_intervals;        /* largest interval count of any instance */
+  int max_degree;           /* largest time degree M_n of any interval, 1..32 */
+  long long M;              /* samples per node, >= 1 */
+  int K;                    /* iterations per interval (cap when tol > 0) */
+  double tol;               /* stop an interval once max|eps| < tol; <= 0: run K */
+  int n_ref;                /* N_* = max(1, ceil(n_ref (t_{n,l} - t_{n-1}) / h_n)) */
+  int n_sub;                /* time sub-points per full walk step, power of two <= 16 */
+  double shell;             /* the walk is absorbed within this distance of the boundary;
+                               0: half the distance of the outermost node, at most 2e-3
+                               (a shell wider than that distance freezes those nodes) */
+  int max_steps;            /* cap on quadrature terms per walk */
+  double kappa;             /* diffusion coefficient (> 0) */
+  unsigned long long seed;  /* Philox4x32-10 key */
+  int precision;            /* SPMC_FP64 or SPMC_MIXED (FP32 sweep, FP64 elsewhere) */
+  int batch;                /* number of instances, >= 1 */
+} spmc_plan_desc;
+
+/* One instance: partition, degrees, reaction, manufactured source, u0.
+ * Eq. mainproblem with homogeneous boundary data; f_add makes the closed form
+ * named by ex_kind an exact solution (Section 4 examples). */
+typedef struct {
+  int n_intervals;          /* 1..max_intervals */
+  const double* t_breaks;   /* host, n_intervals + 1 strictly increasing values */
+  const int* degrees;       /* host, n_intervals time degrees M_n, 1..max_degree */
+  int f_kind;               /* SPMC_F_POLY3: s (c0 + c1 u + c2 u^2 + c3 u^3); SPMC_F_SIN: s sin(u) */
+  double f_coef[4];
+  double f_scale;           /* s */
+  int ex_kind;              /* SPMC_EX_*: e^{-beta t} prod sin(pi x_e); e^{-beta t} prod cos(pi x_e / 2);
+                               (1+t+t^2) prod (1-x_e^2)(1+x_e); or no source */
+  double ex_beta;
+  int u0_kind;              /* SPMC_U0_NODAL: u0 holds n_space^d nodal values;
+                               SPMC_U0_PHI_COEF: u0 holds n_coef^d coefficients of
+                               prod phi_{p_e}(x_e), p_e < n_coef (x_1 fastest) */
+  int n_coef;
+  const double* u0;         /* host */
+} spmc_problem;
+
+typedef struct {
+  long long node_samples;   /* walks run */
+  long long points;         /* residual evaluations */
+  long long capped;         /* walks cut at max_steps */
+  int iterations_run;       /* iterations of the last spmc_solve / spmc_iterate */
+  double last_max_eps;
+  long long sweep_launches; /* sweep kernel launches timed (spmc_set_timing) */
+  double sweep_ms;          /* their summed duration, from CUDA events on the caller's stream */
+} spmc_stats;
+
+/* Validate desc, build the node tables and allocate the workspace.
+ * Errors: SPMC_ERR_INVALID (out-of-range field), SPMC_ERR_UNSUPPORTED (dim or
+ * size this build does not implement), SPMC_ERR_OOM, SPMC_ERR_CUDA.
+ * *out is NULL on failure. */
+spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out);
+
+/* Set instance `instance` (0..batch-1).  Every instance must be set before
+ * spmc_solve / spmc_begin_interval.  Copies the host arrays. */
+spmc_status spmc_set_problem(spmc_plan_t plan, int instance, const spmc_problem* prob);
+
+/* Number of doubles one instance's full solution occupies (sum over its
+ * intervals of (M_n+1) n_space^d), and its offset in spmc_solve's output. */
+spmc_status spmc_solution_layout(spmc_plan_t plan, int instance, long long* offset, long long* count);
+
+/* Algorithm 1 for every instance: all intervals, K iterations each (or until
+ * max|eps| < tol), hand-off of u*(., t_n) between intervals (Step 4).
+ * u_nodes: caller-owned device buffer of spmc_solution_layout's total size;
+ * receives every interval's nodal values. */
+spmc_status spmc_solve(spmc_plan_t plan, void* cuda_stream, double* u_nodes);
+
+/* Stepwise driver.  spmc_begin_interval sets the first iterate of interval
+ * `interval` (0-based) of every instance that has it: row 0 from u0 (interval
+ * 0) or from the previous interval's expansion at its end, all rows equal to
+ * row 0 (Remark 2.1).  spmc_iterate then runs n_iter iterations (iteration
+ * numbers continue from the previous call on that interval) and returns the
+ * largest |eps| of the last one over all instances (synchronises the stream). */
+spmc_status spmc_begin_interval(spmc_plan_t plan, void* cuda_stream, int interval);
+spmc_status spmc_iterate(spmc_plan_t plan, void* cuda_stream, int interval, int n_iter, double* max_eps_host);
+
+/* Copy the current nodal values of (instance, interval) into dst (device
+ * pointer, (M_n+1) n_space^d doubles). */
+spmc_status spmc_get_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, double* dst);
+
+/* Overwrite the nodal values of (instance, interval) with src ((M_n+1)
+ * n_space^d doubles, host or device pointer): checkpoint restore, or a chosen
+ * iterate for checking.  A later spmc_iterate on that interval continues from it. */
+spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, const double* src);
+
+/* Reverse-mode gradient of L(u(T)) for every instance: given dL/du at the
+ * spatial nodes at t = T (device, batch x n_space^d doubles), returns
+ * dL/d(f_scale) (device, batch doubles) and dL/d(u0 coefficients) (device,
+ * batch x n_coef^d doubles; instances set with SPMC_U0_PHI_COEF).  The walks are
+ * the forward solve's (common random numbers); iterations are recomputed from
+ * per-interval checkpoints.  Requires a prior spmc_solve on the same plan. */
+spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_du_T,
+                      double* grad_f_scale, double* grad_u0_coef);
+
+/* Enable (1) or disable (0) CUDA-event timing of every sweep kernel launch; the
+ * totals accumulate in spmc_stats.sweep_ms / sweep_launches (reset on enable). */
+spmc_status spmc_set_timing(spmc_plan_t plan, int enable);
+
+/* The n_space JG(1,1) node coordinates of one axis, ascending (host array). */
+spmc_status spmc_space_nodes(spmc_plan_t plan, double* x_host);
+
+spmc_status spmc_get_stats(spmc_plan_t plan, spmc_stats* out);
+const char* spmc_last_error(spmc_plan_t plan);
+void spmc_destroy(spmc_plan_t plan);
+
+/* Library version string. */
+const char* spmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMC_H */

@@ -124,7 +124,7 @@ class Spec:
     ex_beta: float = 1.0
     n_threads: int = 1
     walk_mode: int = 0          # 0: balls inside Omega, 1: fixed radius (Lemma Xlocation)
-    shell: float = 1e-4
+    shell: float = 0.0           # 0: half the outermost node's distance to the boundary
     max_steps: int = 512
     n_sub: int = 4
 

@@ -607,6 +607,14 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
   while ((1 << gbits) < G) ++gbits;
   int64_t Ktot = (int64_t)G * nstar;
   double sub = delta / G;
+  double shell = pb->shell;
+  if (!(shell > 0.0)) {
+    /* half the distance of the outermost JG(1,1) node to the boundary, at most 2e-3 */
+    double xs[ORC_MAXN], ws[ORC_MAXN];
+    orc_jg11_nodes(pb->n_space, xs, ws);
+    shell = 0.5 * (1.0 - fabs(xs[0]));
+    if (shell > 2e-3) shell = 2e-3;
+  }
   int64_t k = 0;
   double f = 0.0;
   for (int q = 0; q < pb->max_steps; ++q) {
@@ -615,7 +623,7 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
       double de = 1.0 - fabs(X[e]);
       if (de < dist) dist = de;
     }
-    if (dist < pb->shell) break;
+    if (dist < shell) break;
     int64_t w0 = (int64_t)q * W;
     uint32_t gword = stream_word(&st, w0 + 2 * wd + ((d == 2) ? 4 : 2));
     int g = gbits ? (int)(gword >> (32 - gbits)) : 0;

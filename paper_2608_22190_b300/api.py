@@ -1,0 +1,165 @@
+"""Python front end of the CUDA library: plans over PyTorch device memory.
+
+A Plan holds one batch of instances of Eq. mainproblem (homogeneous Dirichlet
+data on (-1,1)^d) and runs Algorithm 1 on the caller's CUDA stream.  All
+arithmetic of the method happens in libspmc.so; this module only marshals
+arguments and allocates result tensors with torch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import workloads as W
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Plan:
+    def __init__(self, dim, n_space, time_family, max_intervals, max_degree, M, K, tol=0.0, n_ref=80, n_sub=4,
+                 shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1):
+        d = L.PlanDesc()
+        d.dim, d.n_space, d.time_family = dim, n_space, time_family
+        d.max_intervals, d.max_degree, d.M, d.K, d.tol = max_intervals, max_degree, M, K, tol
+        d.n_ref, d.n_sub, d.shell, d.max_steps = n_ref, n_sub, shell, max_steps
+        d.kappa, d.seed, d.precision, d.batch = kappa, seed, precision, batch
+        self.desc = d
+        self._h = C.c_void_p()
+        L.check(L.lib.spmc_plan(C.byref(d), C.byref(self._h)))
+        self.dim, self.n_space, self.batch = dim, n_space, batch
+        self.S = n_space ** dim
+        self.degrees = [None] * batch
+
+    # ------------------------------------------------------------------ set-up
+    def space_nodes(self) -> np.ndarray:
+        x = np.zeros(self.n_space)
+        L.check(L.lib.spmc_space_nodes(self._h, x.ctypes.data_as(C.POINTER(C.c_double))), self._h)
+        return x
+
+    def node_grid(self) -> np.ndarray:
+        """(S, d) coordinates of the spatial nodes, x_1 fastest."""
+        x = self.space_nodes()
+        idx = np.arange(self.S)
+        cols = []
+        for e in range(self.dim):
+            cols.append(x[(idx // self.n_space ** e) % self.n_space])
+        return np.stack(cols, axis=1)
+
+    def set_problem(self, instance, t_breaks, degrees, f_kind=L.F_POLY3, f_coef=(0, 0, 0, -1.0), f_scale=1.0,
+                    ex_kind=L.EX_NONE, ex_beta=1.0, u0=None, u0_kind=L.U0_NODAL, n_coef=0):
+        t = np.ascontiguousarray(t_breaks, dtype=np.float64)
+        dg = np.ascontiguousarray(degrees, dtype=np.int32)
+        u = np.ascontiguousarray(u0, dtype=np.float64).ravel()
+        p = L.Problem()
+        p.n_intervals = len(dg)
+        p.t_breaks = t.ctypes.data_as(C.POINTER(C.c_double))
+        p.degrees = dg.ctypes.data_as(C.POINTER(C.c_int))
+        p.f_kind, p.f_scale, p.ex_kind, p.ex_beta = f_kind, f_scale, ex_kind, ex_beta
+        for i, c in enumerate(f_coef):
+            p.f_coef[i] = c
+        p.u0_kind, p.n_coef = u0_kind, n_coef
+        p.u0 = u.ctypes.data_as(C.POINTER(C.c_double))
+        L.check(L.lib.spmc_set_problem(self._h, instance, C.byref(p)), self._h)
+        self.degrees[instance] = [int(v) for v in dg]
+
+    @classmethod
+    def from_workload(cls, wl: "W.Workload", precision=L.FP64, **overrides):
+        insts = wl.instances
+        kw = dict(dim=wl.dim, n_space=wl.n_space, time_family=wl.time_family,
+                  max_intervals=max(len(i.degrees) for i in insts), max_degree=max(int(max(i.degrees)) for i in insts),
+                  M=wl.M, K=wl.K, n_ref=wl.n_ref, n_sub=wl.n_sub, shell=wl.shell, max_steps=wl.max_steps,
+                  kappa=wl.kappa, seed=wl.seed, precision=precision, batch=len(insts))
+        kw.update(overrides)
+        plan = cls(**kw)
+        grid = plan.node_grid()
+        for b, inst in enumerate(insts):
+            if inst.u0_kind == "phi_coef":
+                nc = inst.u0_coef.shape[0]
+                # x_1 fastest: coefficient (i, j) of phi_i(x) phi_j(y) sits at i + nc j
+                plan.set_problem(b, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, inst.f_scale,
+                                 inst.ex_kind, inst.ex_beta, np.ascontiguousarray(inst.u0_coef.T).ravel(),
+                                 L.U0_PHI_COEF, nc)
+            else:
+                plan.set_problem(b, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, inst.f_scale,
+                                 inst.ex_kind, inst.ex_beta, W.u0_nodal(inst, grid))
+        return plan
+
+    # ------------------------------------------------------------------ layout
+    def layout(self, instance):
+        off, cnt = C.c_longlong(), C.c_longlong()
+        L.check(L.lib.spmc_solution_layout(self._h, instance, C.byref(off), C.byref(cnt)), self._h)
+        return off.value, cnt.value
+
+    def total_size(self) -> int:
+        o, c = self.layout(self.batch - 1)
+        return o + c
+
+    def blocks(self, flat: torch.Tensor, instance: int):
+        """Split an instance's part of spmc_solve's output into per-interval (M_n+1, S) views."""
+        off, _ = self.layout(instance)
+        out = []
+        for Mt in self.degrees[instance]:
+            n = (Mt + 1) * self.S
+            out.append(flat[off: off + n].view(Mt + 1, self.S))
+            off += n
+        return out
+
+    # ------------------------------------------------------------------ run
+    def solve(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.total_size(), dtype=torch.float64, device="cuda")
+        assert out.dtype == torch.float64 and out.numel() >= self.total_size()
+        L.check(L.lib.spmc_solve(self._h, C.c_void_p(_stream_ptr(stream)), C.c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def begin_interval(self, interval: int, stream=None):
+        L.check(L.lib.spmc_begin_interval(self._h, C.c_void_p(_stream_ptr(stream)), interval), self._h)
+
+    def iterate(self, interval: int, n_iter: int = 1, stream=None) -> float:
+        mx = C.c_double()
+        L.check(L.lib.spmc_iterate(self._h, C.c_void_p(_stream_ptr(stream)), interval, n_iter, C.byref(mx)), self._h)
+        return mx.value
+
+    def get_nodes(self, instance: int, interval: int, stream=None) -> torch.Tensor:
+        Mt = self.degrees[instance][interval]
+        out = torch.empty((Mt + 1, self.S), dtype=torch.float64, device="cuda")
+        L.check(L.lib.spmc_get_nodes(self._h, C.c_void_p(_stream_ptr(stream)), instance, interval,
+                                     C.c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def set_nodes(self, instance: int, interval: int, values: torch.Tensor, stream=None):
+        v = values.contiguous()
+        Mt = self.degrees[instance][interval]
+        assert v.dtype == torch.float64 and v.numel() == (Mt + 1) * self.S
+        L.check(L.lib.spmc_set_nodes(self._h, C.c_void_p(_stream_ptr(stream)), instance, interval,
+                                     C.c_void_p(v.data_ptr())), self._h)
+        if v.is_cuda:
+            torch.cuda.current_stream().synchronize()
+
+    def stats(self) -> dict:
+        s = L.Stats()
+        L.check(L.lib.spmc_get_stats(self._h, C.byref(s)), self._h)
+        return {"points": s.points, "capped": s.capped, "iterations_run": s.iterations_run,
+                "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms}
+
+    def set_timing(self, enable: bool):
+        L.check(L.lib.spmc_set_timing(self._h, 1 if enable else 0), self._h)
+
+    def close(self):
+        if self._h:
+            L.lib.spmc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,296 @@
+// spmc_device.cuh -- device building blocks of the sweep (sm_103a).
+//
+//  * Philox4x32-10 (Salmon et al., SC'11) counter-based generator;
+//  * Jacobi/Babuska-Shen basis values by recurrence (Section 2.3);
+//  * the inside-ball walk step of the residual estimator (Section 2.2,
+//    Lemma Xlocation, Eqs. indexL, interIQ, with walk-on-spheres balls that stay
+//    inside Omega and Green-function quadrature points per ball);
+//  * the residual r = f(u*) + f_add - d_t u* + kappa Delta u* at a point from a
+//    time-contracted coefficient slice (Eqs. u_N, ufg_ep1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spmc {
+
+constexpr double kPiD = 3.14159265358979323846;
+
+// ------------------------------------------------------------------ Philox
+struct Philox4 {
+  uint32_t v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  Philox4 o;
+  o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+// The stream of one walk: key = seed, counter = (block, sample, node, tag).
+struct WalkStream {
+  uint32_t k0, k1, sample, node, tag;
+  __device__ __forceinline__ Philox4 block(uint32_t b) const { return philox4x32_10(b, sample, node, tag, k0, k1); }
+};
+
+template <typename R> struct U01;
+template <> struct U01<double> {
+  // 53-bit uniform on (0,1) from a pair of words
+  static __device__ __forceinline__ double pair(uint32_t a, uint32_t b) {
+    return __dmul_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0), (double)(b >> 6)), 0.5),
+                     1.0 / 9007199254740992.0);
+  }
+};
+template <> struct U01<float> {
+  // 24-bit uniform on (0,1) from the first word of the pair
+  static __device__ __forceinline__ float pair(uint32_t a, uint32_t) {
+    return ((float)(a >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  }
+};
+
+// exact-rounding arithmetic helpers (no FMA contraction where the walk
+// decides control flow: the FP64 walk must match the CPU step for step)
+template <typename R> struct Ar;
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double log_(double a) { return log(a); }
+  static __device__ __forceinline__ void sincos2pi(double U, double* s, double* c) { sincospi(2.0 * U, s, c); }
+  static __device__ __forceinline__ double sinpi_(double x) { return sinpi(x); }
+  static __device__ __forceinline__ double cospi_(double x) { return cospi(x); }
+  static __device__ __forceinline__ double sin_(double x) { return sin(x); }
+  static __device__ __forceinline__ double cos_(double x) { return cos(x); }
+  static constexpr int kBisect = 60;
+};
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float log_(float a) { return logf(a); }
+  static __device__ __forceinline__ void sincos2pi(float U, float* s, float* c) { sincospif(2.0f * U, s, c); }
+  static __device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }
+  static __device__ __forceinline__ float cospi_(float x) { return cospif(x); }
+  static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
+  static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
+  static constexpr int kBisect = 24;
+};
+
+// ------------------------------------------------------------------ word layout
+// Words of one step of the inside-ball walk, padded to whole Philox blocks:
+// [next-step direction wd | Green direction wd | Green radius 2 (d=2: 4) | sub-point 1]
+__host__ __device__ constexpr int dir_words(int d) { return d == 1 ? 1 : (d == 2 ? 2 : 4 * ((d + 1) / 2)); }
+__host__ __device__ constexpr int radius_words(int d) { return d == 2 ? 4 : 2; }
+__host__ __device__ constexpr int step_words(int d) { return ((2 * dir_words(d) + radius_words(d) + 1) + 3) / 4 * 4; }
+__host__ __device__ constexpr int gword_index(int d) { return 2 * dir_words(d) + radius_words(d); }
+
+// fetch word w of the walk (one Philox evaluation per call)
+__device__ __forceinline__ uint32_t stream_word(const WalkStream& s, uint32_t w) {
+  Philox4 b = s.block(w >> 2);
+  return b.v[w & 3];
+}
+
+// Uniform direction on S^{d-1} from the words starting at w0 (Lemma Xlocation):
+// d=1 sign bit; d=2 angle 2 pi U; d>=3 normalised Box-Muller Gaussians.
+template <int D, typename R>
+__device__ __forceinline__ void direction(const WalkStream& s, uint32_t w0, R* th) {
+  if (D == 1) {
+    th[0] = (stream_word(s, w0) >> 31) ? R(-1) : R(1);
+  } else if (D == 2) {
+    Philox4 b = s.block(w0 >> 2);
+    uint32_t o = w0 & 3;
+    R U = U01<R>::pair(b.v[o], b.v[o + 1]);
+    R sn, cs;
+    Ar<R>::sincos2pi(U, &sn, &cs);
+    th[0] = cs; th[1] = sn;
+  } else {
+    constexpr int NP = (D + 1) / 2;
+    R z[2 * NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      Philox4 b = s.block((w0 >> 2) + k);  // w0 is a multiple of 4 for d >= 3
+      R U1 = U01<R>::pair(b.v[0], b.v[1]);
+      R U2 = U01<R>::pair(b.v[2], b.v[3]);
+      R Rr = Ar<R>::sqrt_(Ar<R>::mul(R(-2), Ar<R>::log_(U1)));
+      R sn, cs;
+      Ar<R>::sincos2pi(U2, &sn, &cs);
+      z[2 * k] = Ar<R>::mul(Rr, cs);
+      z[2 * k + 1] = Ar<R>::mul(Rr, sn);
+    }
+    R nrm = R(0);
+#pragma unroll
+    for (int e = 0; e < D; ++e) nrm = Ar<R>::add(nrm, Ar<R>::mul(z[e], z[e]));
+    nrm = Ar<R>::sqrt_(nrm);
+#pragma unroll
+    for (int e = 0; e < D; ++e) th[e] = Ar<R>::div(z[e], nrm);
+  }
+}
+
+// Radial law of the ball's Green function as a fraction v of the radius:
+// d=1 density 2(1-v); d=2 density 4 v log(1/v); d>=3 density prop. to v - v^{d-1}.
+template <int D, typename R>
+__device__ __forceinline__ R green_radius(R U1, R U2) {
+  if (D == 1) return Ar<R>::sub(R(1), Ar<R>::sqrt_(U1));
+  if (D == 2) return Ar<R>::sqrt_(Ar<R>::mul(U1, U2));
+  R lo = R(0), hi = R(1);
+  for (int it = 0; it < Ar<R>::kBisect; ++it) {
+    R v = Ar<R>::mul(R(0.5), Ar<R>::add(lo, hi));
+    R vd = R(1);
+#pragma unroll
+    for (int k = 0; k < D; ++k) vd = Ar<R>::mul(vd, v);
+    R F = Ar<R>::div(Ar<R>::sub(Ar<R>::mul(Ar<R>::mul(R(D), v), v), Ar<R>::mul(R(2), vd)), R(D - 2.0));
+    if (F < U1) lo = v; else hi = v;
+  }
+  return Ar<R>::mul(R(0.5), Ar<R>::add(lo, hi));
+}
+
+// ------------------------------------------------------------------ problem
+struct InstanceParams {
+  int f_kind;      // 0: s (c0 + c1 u + c2 u^2 + c3 u^3), 1: s sin(u)
+  int ex_kind;     // 0 none, 1 sin product, 2 half-cos product, 3 polynomial
+  double fc[4];
+  double f_scale;
+  double ex_beta;
+};
+
+template <typename R>
+__device__ __forceinline__ R reaction(const InstanceParams& ip, R u) {
+  if (ip.f_kind == 1) return R(ip.f_scale) * Ar<R>::sin_(u);
+  return R(ip.f_scale) * (R(ip.fc[0]) + u * (R(ip.fc[1]) + u * (R(ip.fc[2]) + u * R(ip.fc[3]))));
+}
+
+// Manufactured source f_add = d_t u_ex - kappa Delta u_ex - f(u_ex) at (y, tau);
+// Tt = time factor of u_ex at tau, dTt its derivative (polynomial kind).
+template <int D, typename R>
+__device__ __forceinline__ R source(const InstanceParams& ip, R kappa, const R* y, R Tt, R dTt) {
+  if (ip.ex_kind == 0) return R(0);
+  if (ip.ex_kind == 1 || ip.ex_kind == 2) {
+    R prod = R(1);
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+      prod *= (ip.ex_kind == 1) ? Ar<R>::sinpi_(y[e]) : Ar<R>::cospi_(R(0.5) * y[e]);
+    R ue = Tt * prod;
+    R cl = (ip.ex_kind == 1) ? R(D * kPiD * kPiD) : R(D * 0.25 * kPiD * kPiD);
+    return (R(-ip.ex_beta) + kappa * cl) * ue - reaction<R>(ip, ue);
+  }
+  R g[D];
+  R prod = R(1);
+#pragma unroll
+  for (int e = 0; e < D; ++e) { g[e] = (R(1) - y[e] * y[e]) * (R(1) + y[e]); prod *= g[e]; }
+  R mlap = R(0);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    R term = R(2) + R(6) * y[e];
+#pragma unroll
+    for (int e2 = 0; e2 < D; ++e2) if (e2 != e) term *= g[e2];
+    mlap += term;
+  }
+  R ue = Tt * prod;
+  return dTt * prod + kappa * Tt * mlap - reaction<R>(ip, ue);
+}
+
+// Recurrence coefficients of P^{(1,1)}: P_p = ra_p x P_{p-1} - rb_p P_{p-2},
+// ra_p = (2p+1)(p+1)/(p(p+2)), rb_p = (p+1)/(p+2); lam_p = (p+1)(p+2)
+// (tables filled once by the host, read through the constant cache).
+constexpr int kMaxModes = 64;
+__constant__ double c_ra_d[kMaxModes], c_rb_d[kMaxModes], c_lam_d[kMaxModes];
+__constant__ float c_ra_f[kMaxModes], c_rb_f[kMaxModes], c_lam_f[kMaxModes];
+template <typename R> __device__ __forceinline__ R jac_ra(int p);
+template <typename R> __device__ __forceinline__ R jac_rb(int p);
+template <typename R> __device__ __forceinline__ R jac_lam(int p);
+template <> __device__ __forceinline__ double jac_ra<double>(int p) { return c_ra_d[p]; }
+template <> __device__ __forceinline__ double jac_rb<double>(int p) { return c_rb_d[p]; }
+template <> __device__ __forceinline__ double jac_lam<double>(int p) { return c_lam_d[p]; }
+template <> __device__ __forceinline__ float jac_ra<float>(int p) { return c_ra_f[p]; }
+template <> __device__ __forceinline__ float jac_rb<float>(int p) { return c_rb_f[p]; }
+template <> __device__ __forceinline__ float jac_lam<float>(int p) { return c_lam_f[p]; }
+
+// Basis values phi_p(y) = (1-y^2) P_p(y) and psi_p(y) = (p+1)(p+2) P_p(y), p < n.
+template <int NMAX, typename R>
+__device__ __forceinline__ void basis(int n, R y, R* phi, R* psi) {
+  R om = R(1) - y * y;
+  R pm2 = R(1), pm1 = R(2) * y;
+#pragma unroll
+  for (int p = 0; p < NMAX; ++p) {
+    R P;
+    if (p == 0) P = R(1);
+    else if (p == 1) P = R(2) * y;
+    else { P = jac_ra<R>(p) * y * pm1 - jac_rb<R>(p) * pm2; pm2 = pm1; pm1 = P; }
+    phi[p] = (p < n) ? om * P : R(0);
+    psi[p] = (p < n) ? jac_lam<R>(p) * P : R(0);
+  }
+}
+
+// The residual at y from one slice: C = time-contracted coefficients of u*,
+// H = time-contracted coefficients of -d_t u* (both in the phi basis; for d=2
+// stored [p_x][p_y] with p_y contiguous).
+//   u* = sum_p C_p Phi_p(y),
+//   G  = sum_p H_p Phi_p(y) - kappa sum_p C_p Psi_p(y)   (= -d_t u* + kappa Delta u*)
+//   r  = f(u*) + f_add + G
+template <int D, int NMAX, typename R>
+__device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int n, const R* __restrict__ sC,
+                                         const R* __restrict__ sH, const R* y, R Tt, R dTt) {
+  R u = R(0), G = R(0);
+  if (D == 1) {
+    R om = R(1) - y[0] * y[0];
+    R pm2 = R(1), pm1 = R(2) * y[0];
+    R cpsi = R(0);
+#pragma unroll
+    for (int p = 0; p < NMAX; ++p) {
+      if (p < n) {
+        R P;
+        if (p == 0) P = R(1);
+        else if (p == 1) P = R(2) * y[0];
+        else { P = jac_ra<R>(p) * y[0] * pm1 - jac_rb<R>(p) * pm2; pm2 = pm1; pm1 = P; }
+        R phi = om * P;
+        R c = sC[p];
+        u += c * phi;
+        G += sH[p] * phi;
+        cpsi += c * jac_lam<R>(p) * P;
+      }
+    }
+    G -= kappa * cpsi;
+  } else if (D == 2) {
+    R phy[NMAX], psy[NMAX];
+    basis<NMAX, R>(n, y[1], phy, psy);
+    R omx = R(1) - y[0] * y[0];
+    R pm2 = R(1), pm1 = R(2) * y[0];
+    R cpsi = R(0);
+    for (int p1 = 0; p1 < n; ++p1) {
+      R P;
+      if (p1 == 0) P = R(1);
+      else if (p1 == 1) P = R(2) * y[0];
+      else { P = jac_ra<R>(p1) * y[0] * pm1 - jac_rb<R>(p1) * pm2; pm2 = pm1; pm1 = P; }
+      R phx = omx * P, psx = jac_lam<R>(p1) * P;
+      const R* c = sC + p1 * NMAX;     // rows padded to NMAX entries
+      const R* hh = sH + p1 * NMAX;
+      R a1 = R(0), a2 = R(0), a3 = R(0);
+#pragma unroll
+      for (int p2 = 0; p2 < NMAX; ++p2) {   // padded entries are zero
+        R cv = c[p2];
+        a1 += cv * phy[p2];
+        a2 += cv * psy[p2];
+        a3 += hh[p2] * phy[p2];
+      }
+      u += phx * a1;
+      G += phx * a3;
+      cpsi += psx * a1 + phx * a2;
+    }
+    G -= kappa * cpsi;
+  }
+  return reaction<R>(ip, u) + source<D, R>(ip, kappa, y, Tt, dTt) + G;
+}
+
+}  // namespace spmc

@@ -1,0 +1,597 @@
+// spmc_kernels.cuh -- kernels of one residual iteration (Algorithm 1, Steps 1-3)
+// and of the interval hand-off (Step 4), for a batch of instances.
+//
+//   reconstruct_kernel  Step 1: nodal -> modal (Eq. u_N), FP64
+//   slice_kernel        time contraction of the coefficients at every path time
+//                       of every node's walk grid, FP64 or FP32
+//   sweep_kernel        Step 2: M walks per node, residual quadrature per walk,
+//                       per-block FP64 sums of Q (Eqs. interIQ, varepsilon_1)
+//   update_kernel       Step 3: eps = sum / M (compensated, FP64), u += eps
+//   init/handoff        Step 4 and the first iterate (Remark 2.1)
+#pragma once
+#include "spmc_device.cuh"
+
+namespace spmc {
+
+// One sampled time node (l >= 1) of one instance in the current interval.
+struct TimeNode {
+  int inst;
+  int ell;
+  int nstar;        // N_* of Eq. time division
+  int Mt;           // time degree of the interval
+  long long slice_base;  // first slice (sub-point m = 0) of this node
+  long long u_off;  // offset of the instance's nodal block of this interval
+  double t_node, t0, h;
+};
+
+// Per active instance in the current interval.
+struct InstInterval {
+  int inst;
+  int Mt;
+  long long u_off;     // nodal block (Mt+1) x S
+  long long c_off;     // coefficient blocks cu, ct ((Mt+1) x S each)
+  long long b_off;     // time analysis matrix (Mt+1)^2
+  long long h_off;     // hand-off weights sum_q b_qk (Mt+1)
+  long long next_u_off;  // nodal block of the next interval (-1 if none)
+  int next_Mt;
+  double t0, h;
+};
+
+struct SliceInfo {
+  double tau;       // path time of the sub-point
+  double Tt, dTt;   // exact-solution time factor and its derivative at tau
+};
+
+// ----------------------------------------------------------------- Step 1
+// cu = (B_n x A x ... x A) U, ct_q = (2/h)(2q+1) sum_{l>q, l+q odd} cu_l.
+// One block per active instance; the nodal block lives in shared memory.
+template <int D>
+__global__ void reconstruct_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ U,
+                                   const double* __restrict__ A, const double* __restrict__ Bt,
+                                   double* __restrict__ coef, int n) {
+  extern __shared__ double sm[];
+  const InstInterval w = ii[blockIdx.x];
+  int S = 1;
+  for (int e = 0; e < D; ++e) S *= n;
+  const int T = w.Mt + 1;
+  const int tot = T * S;
+  double* a = sm;
+  double* b = sm + tot;
+  const double* B = Bt + w.b_off;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) a[i] = U[w.u_off + i];
+  __syncthreads();
+  // time axis
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    int q = i / S, j = i - q * S;
+    double acc = 0.0;
+    for (int k = 0; k < T; ++k) acc += B[q * T + k] * a[k * S + j];
+    b[i] = acc;
+  }
+  __syncthreads();
+  double* src = b;
+  double* dst = a;
+  int stride = 1;
+  for (int e = 0; e < D; ++e) {
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+      int q = i / S, idx = i - q * S;
+      int pe = (idx / stride) % n;
+      int base = q * S + idx - pe * stride;
+      double acc = 0.0;
+      for (int je = 0; je < n; ++je) acc += A[pe * n + je] * src[base + je * stride];
+      dst[i] = acc;
+    }
+    __syncthreads();
+    double* t = src; src = dst; dst = t;
+    stride *= n;
+  }
+  double* cu = coef + w.c_off;
+  double* ct = cu + tot;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    int q = i / S, p = i - q * S;
+    cu[i] = src[i];
+    double acc = 0.0;
+    for (int l = q + 1; l < T; l += 2) acc += src[l * S + p];
+    ct[i] = (2.0 / w.h) * (2.0 * q + 1.0) * acc;
+  }
+}
+
+// ----------------------------------------------------------------- slices
+// For every node's walk grid tau_m = t_node - (m + 1/2) delta / n_sub:
+//   C_m[p] = sum_q cu[q][p] L_q(xi(tau_m)),  H_m[p] = -sum_q ct[q][p] L_q(xi(tau_m)).
+// d=2 slices are stored [p_x][p_y] (p_y contiguous).  One block per slice.
+// Slice layout: C then H, each n rows (d = 2) or one row (d = 1) of `row`
+// entries (row >= n, zero padded), slices `sl_stride` entries apart.
+template <int D, typename R>
+__global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* __restrict__ slice_node,
+                             const InstInterval* __restrict__ inst_of_node, const double* __restrict__ coef,
+                             const InstanceParams* __restrict__ ip, R* __restrict__ slices,
+                             SliceInfo* __restrict__ sinfo, int n, int n_sub, int row, long long sl_stride) {
+  __shared__ double L[40];
+  long long s = blockIdx.x;
+  long long ti = slice_node[s];
+  const TimeNode node = tn[ti];
+  const InstInterval w = inst_of_node[ti];
+  int m = (int)(s - node.slice_base);
+  int S = 1;
+  for (int e = 0; e < D; ++e) S *= n;
+  const double sdur = __dsub_rn(node.t_node, node.t0);
+  const double delta = __ddiv_rn(sdur, (double)node.nstar);
+  const double sub = __ddiv_rn(delta, (double)n_sub);
+  const double tau = __dsub_rn(node.t_node, __dmul_rn((double)m + 0.5, sub));
+  if (threadIdx.x == 0) {
+    double xi = (2.0 * tau - node.t0 - (node.t0 + node.h)) / node.h;
+    L[0] = 1.0;
+    if (node.Mt >= 1) L[1] = xi;
+    for (int k = 1; k < node.Mt; ++k) L[k + 1] = ((2.0 * k + 1.0) * xi * L[k] - k * L[k - 1]) / (k + 1.0);
+    const InstanceParams P = ip[node.inst];
+    SliceInfo si;
+    si.tau = tau;
+    if (P.ex_kind == 3) { si.Tt = 1.0 + tau + tau * tau; si.dTt = 1.0 + 2.0 * tau; }
+    else if (P.ex_kind == 1 || P.ex_kind == 2) { si.Tt = exp(-P.ex_beta * tau); si.dTt = -P.ex_beta * si.Tt; }
+    else { si.Tt = 0.0; si.dTt = 0.0; }
+    sinfo[s] = si;
+  }
+  __syncthreads();
+  const double* cu = coef + w.c_off;
+  const double* ct = cu + (long long)(node.Mt + 1) * S;
+  R* out = slices + s * sl_stride;
+  const int half = (D == 2) ? n * row : row;
+  for (int i = threadIdx.x; i < 2 * half; i += blockDim.x) out[i] = R(0);
+  __syncthreads();
+  for (int p = threadIdx.x; p < S; p += blockDim.x) {
+    double c = 0.0, h = 0.0;
+    for (int q = 0; q <= node.Mt; ++q) {
+      c += cu[q * S + p] * L[q];
+      h -= ct[q * S + p] * L[q];
+    }
+    int dstp = p;
+    if (D == 2) { int px = p % n, py = p / n; dstp = px * row + py; }
+    out[dstp] = (R)c;
+    out[half + dstp] = (R)h;
+  }
+}
+
+// ----------------------------------------------------------------- Step 2
+struct SweepArgs {
+  const TimeNode* tn;
+  const InstanceParams* ip;
+  const double* xnodes;     // JG(1,1) nodes (n)
+  const void* slices;       // R[2 S] per slice
+  const SliceInfo* sinfo;
+  double* partial;          // per (time node, j, chunk) sum of Q
+  unsigned long long* counters;  // [0] points evaluated, [1] walks capped
+  int* status;
+  int n, S, n_chunks, chunk, n_sub, gbits, max_steps;
+  long long M;              // samples per node (the last chunk may be partial)
+  long long sl_stride;      // entries between consecutive slices (global and shared)
+  int half;                 // entries of C (= of H) in a slice
+  double kappa, shell;
+  uint32_t k0, k1;
+  int interval, iteration;
+};
+
+// Per-sample walk state, kept in shared memory (structure of arrays).
+template <int D, typename R>
+struct WalkState {
+  R* X[D];
+  R* f;       // fraction of the current sub-step used by shrunk balls
+  R* w;       // weight of the pending step
+  R* r;       // ball radius of the pending step
+  R* S;       // running sum of w r(Y, tau) for the walk
+  int* k;     // whole sub-steps used
+  int* q;     // step counter
+  int* mnext; // sub-point of the pending evaluation; -1 once the walk has ended
+  int* last;  // the pending step ends the walk
+};
+
+// Prepare step q of sample s (the ball, its weight and its sub-point) as the
+// CPU reference does: absorb in the shell, shrink the ball to the distance to
+// the boundary, cut the last step to the time left.
+template <int D, typename R>
+__device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, const WalkStream& ws, R J, R delta,
+                                             R sub, int Ktot, int G, int gbits, R shell, R kappa, int max_steps,
+                                             double& acc, unsigned long long& capped) {
+  int q = st.q[s];
+  R dist = R(1);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    R de = Ar<R>::sub(R(1), fabs(st.X[e][s]));
+    if (de < dist) dist = de;
+  }
+  if (q >= max_steps || dist < shell) {
+    if (q >= max_steps) ++capped;
+    st.mnext[s] = -1;   // the walk's Q stays in st.S[s]
+    return;
+  }
+  constexpr int W = step_words(D);
+  uint32_t gword = stream_word(ws, (uint32_t)q * W + gword_index(D));
+  int g = gbits ? (int)(gword >> (32 - gbits)) : 0;
+  int k = st.k[s];
+  R f = st.f[s];
+  R left = Ar<R>::sub(Ar<R>::mul((R)(Ktot - k), sub), f);
+  R w, r;
+  int m, last = 0;
+  if (J <= dist) {
+    r = J;
+    w = delta;
+    if (k + G >= Ktot) {
+      int ahead = Ktot - k;
+      m = k + (gbits ? (int)(((unsigned long long)gword * (unsigned long long)ahead) >> 32) : 0);
+      w = left;
+      last = 1;
+    } else {
+      m = k + g;
+      k += G;
+    }
+  } else {
+    r = dist;
+    w = Ar<R>::div(Ar<R>::mul(r, r), Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa));
+    m = k;
+    if (w >= left) { w = left; last = 1; }
+    else {
+      f = Ar<R>::add(f, w);
+      while (f >= sub) { f = Ar<R>::sub(f, sub); ++k; }
+      if (k >= Ktot) last = 1;
+    }
+  }
+  st.k[s] = k;
+  st.f[s] = f;
+  st.w[s] = w;
+  st.r[s] = r;
+  st.mnext[s] = m;
+  st.last[s] = last;
+}
+
+// Per-cohort constants, kept in shared memory.  A cohort is one chunk of the
+// samples of one sampled node (time node ti, spatial node j).
+template <int D, typename R>
+struct Cohort {
+  int id;            // global cohort index, -1 when the slot is empty
+  long long ti;
+  int j, chunk;
+  int m0;            // first sub-point of the cohort's current window
+  int fresh;         // started during this pass: its window stays at 0
+  int npass;         // passes spent on the cohort (bounded by 2 Ktot + 8)
+  int Ktot;
+  int nsl;           // slices staged for the window
+  long long slice_base;
+  R xj[D];
+  R J, delta, sub;
+  uint32_t node, tag;
+  long long sample0;
+};
+
+// Persistent sweep.  Each block keeps NC cohorts in flight.  A pass handles, for
+// every cohort, the window of n_sub sub-points [m0, m0 + n_sub) whose slices are
+// staged in shared memory: every sample whose pending evaluation lies in its
+// cohort's window is evaluated and keeps stepping while its next evaluation
+// stays in the window.  When all walks of a cohort have ended, the block sums
+// their Q in FP64 (fixed order), writes the cohort's partial sum and takes the
+// next cohort from a global counter.  Cohorts at different stages share the
+// block, so the long tail of surviving walks of one cohort overlaps the start
+// of others.
+template <int D, int NMAX, typename R>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) sweep_kernel(SweepArgs a, int NC, int CC, long long n_cohorts,
+                                                    int* __restrict__ work_counter) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int S = a.S, n = a.n;
+  const int G = a.n_sub;
+  const long long slst = a.sl_stride;
+  const int half = a.half;
+  const int NS = NC * CC;
+  R* sSl = reinterpret_cast<R*>(smraw);                       // [NC][G][slst]
+  unsigned char* p = smraw + ((NC * G * slst * sizeof(R) + 15) / 16) * 16;
+  WalkState<D, R> st;
+#pragma unroll
+  for (int e = 0; e < D; ++e) { st.X[e] = reinterpret_cast<R*>(p); p += NS * sizeof(R); }
+  st.f = reinterpret_cast<R*>(p); p += NS * sizeof(R);
+  st.w = reinterpret_cast<R*>(p); p += NS * sizeof(R);
+  st.r = reinterpret_cast<R*>(p); p += NS * sizeof(R);
+  st.S = reinterpret_cast<R*>(p); p += NS * sizeof(R);
+  st.k = reinterpret_cast<int*>(p); p += NS * sizeof(int);
+  st.q = reinterpret_cast<int*>(p); p += NS * sizeof(int);
+  st.mnext = reinterpret_cast<int*>(p); p += NS * sizeof(int);
+  st.last = reinterpret_cast<int*>(p); p += NS * sizeof(int);
+  int* ready = reinterpret_cast<int*>(p); p += NS * sizeof(int);
+  Cohort<D, R>* coh = reinterpret_cast<Cohort<D, R>*>(p); p += ((NC * sizeof(Cohort<D, R>) + 15) / 16) * 16;
+  int* cinfo = reinterpret_cast<int*>(p); p += 3 * NC * sizeof(int);   // [ready count | min pending | alive]
+  double* sT = reinterpret_cast<double*>(p);                          // [NC][G][2] time factors
+  __shared__ int red[64];
+  __shared__ double dred[32];
+  __shared__ int s_next;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const InstanceParams* ipt = a.ip;
+  const R kappa = (R)a.kappa;
+  const R shell = (R)a.shell;
+  const R* slices = reinterpret_cast<const R*>(a.slices);
+  unsigned long long capped = 0, points = 0;
+  double dummy_acc = 0.0;
+
+  // take a cohort for slot c and start its walks
+  auto start_cohort = [&](int c) {
+    if (threadIdx.x == 0) s_next = atomicAdd(work_counter, 1);
+    __syncthreads();
+    const int id = s_next;
+    __syncthreads();
+    if (id >= n_cohorts) {
+      if (threadIdx.x == 0) coh[c].id = -1;
+      for (int s = threadIdx.x; s < CC; s += blockDim.x) st.mnext[c * CC + s] = -1;
+      __syncthreads();
+      return;
+    }
+    long long b = id;
+    const int chunk = (int)(b % a.n_chunks);
+    b /= a.n_chunks;
+    const int j = (int)(b % S);
+    const long long ti = b / S;
+    const TimeNode node = a.tn[ti];
+    Cohort<D, R> ch;
+    ch.id = id; ch.ti = ti; ch.j = j; ch.chunk = chunk; ch.m0 = 0; ch.fresh = 1; ch.npass = 0;
+    {
+      int jj = j;
+#pragma unroll
+      for (int e = 0; e < D; ++e) { ch.xj[e] = (R)a.xnodes[jj % n]; jj /= n; }
+    }
+    const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
+    ch.delta = Ar<R>::div(sdur, (R)node.nstar);
+    ch.J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), ch.delta));
+    ch.sub = Ar<R>::div(ch.delta, (R)G);
+    ch.Ktot = G * node.nstar;
+    ch.slice_base = node.slice_base;
+    ch.node = (uint32_t)(node.ell * S + j);
+    ch.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+             (uint32_t)(a.iteration & 0x3ff);
+    ch.sample0 = (long long)chunk * CC;
+    ch.nsl = 0;
+    if (threadIdx.x == 0) coh[c] = ch;
+    WalkStream ws;
+    ws.k0 = a.k0; ws.k1 = a.k1; ws.node = ch.node; ws.tag = ch.tag;
+    for (int s = threadIdx.x; s < CC; s += blockDim.x) {
+      const int g = c * CC + s;
+#pragma unroll
+      for (int e = 0; e < D; ++e) st.X[e][g] = ch.xj[e];
+      st.f[g] = R(0); st.S[g] = R(0); st.k[g] = 0; st.q[g] = 0;
+      if (ch.sample0 + s >= a.M) { st.mnext[g] = -1; continue; }
+      ws.sample = (uint32_t)(ch.sample0 + s);
+      prepare_step<D, R>(st, g, ws, ch.J, ch.delta, ch.sub, ch.Ktot, G, a.gbits, shell, kappa, a.max_steps,
+                         dummy_acc, capped);
+    }
+    __syncthreads();
+  };
+
+  for (int c = 0; c < NC; ++c) start_cohort(c);
+
+  while (true) {
+    // per-cohort window statistics
+    if (threadIdx.x < 3 * NC) cinfo[threadIdx.x] = (threadIdx.x / NC == 1) ? 0x7fffffff : 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int s = threadIdx.x; s < NS; s += blockDim.x) {
+      const int mv = st.mnext[s];
+      if (mv < 0) continue;
+      const int c = s / CC;
+      const int m0 = coh[c].m0;
+      atomicAdd(&cinfo[2 * NC + c], 1);
+      if (mv >= m0 && mv < m0 + G) ++cnt;
+      else if (mv >= m0 + G) atomicMin(&cinfo[NC + c], mv);
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+    for (int wv = 0; wv < nwarps; ++wv) {
+      if (wv < warp) wbase += red[wv];
+      total += red[wv];
+    }
+    int pos = wbase + incl - cnt;
+    for (int s = threadIdx.x; s < NS; s += blockDim.x) {
+      const int mv = st.mnext[s];
+      const int m0 = coh[s / CC].m0;
+      if (mv >= m0 && mv < m0 + G) ready[pos++] = s;
+    }
+    // finished cohorts: reduce, write, restart; empty windows: jump ahead
+    bool any_active = false;
+    for (int c = 0; c < NC; ++c) {
+      const int id = coh[c].id;
+      if (id < 0) continue;
+      if (cinfo[2 * NC + c] == 0) {
+        // all walks of the cohort have ended: FP64 sum of their Q in slot order
+        double t = 0.0;
+        for (int s = threadIdx.x; s < CC; s += blockDim.x) t += (double)st.S[c * CC + s];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) dred[warp] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double tt = 0.0;
+          for (int wv = 0; wv < nwarps; ++wv) tt += dred[wv];
+          a.partial[(coh[c].ti * S + coh[c].j) * a.n_chunks + coh[c].chunk] = tt;
+        }
+        __syncthreads();
+        start_cohort(c);
+        // the new cohort's walks are pending at window 0; they join the next pass
+        if (coh[c].id >= 0) any_active = true;
+      } else {
+        any_active = true;
+      }
+    }
+    if (!any_active) break;
+    // pass budget: a cohort's pending sub-points never decrease and stay below
+    // Ktot, and its window moves forward every pass, so 2 Ktot + 8 passes always
+    // suffice; a cohort over budget (inconsistent inputs) is reported and its
+    // walks are ended, so the kernel always terminates.
+    for (int c = 0; c < NC; ++c) {
+      if (coh[c].id < 0) continue;
+      if (coh[c].npass > 2 * coh[c].Ktot + 8) {
+        if (threadIdx.x == 0) atomicOr(a.status, 2);
+        for (int s = threadIdx.x; s < CC; s += blockDim.x) st.mnext[c * CC + s] = -1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < total; i += blockDim.x) if (ready[i] / CC == c) ready[i] = -1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < NC && coh[threadIdx.x].id >= 0) coh[threadIdx.x].npass += 1;
+    if (total == 0) {
+      // no cohort has work in its window: move every window to its next pending sub-point
+      __syncthreads();
+      if (threadIdx.x < NC && coh[threadIdx.x].id >= 0) {
+        if (coh[threadIdx.x].fresh) coh[threadIdx.x].fresh = 0;
+        else if (cinfo[2 * NC + threadIdx.x] > 0 && cinfo[NC + threadIdx.x] != 0x7fffffff)
+          coh[threadIdx.x].m0 = cinfo[NC + threadIdx.x];
+      }
+      __syncthreads();
+      continue;
+    }
+    // stage every active cohort's window of slices (16-byte vector copies) and time factors
+    for (int c = 0; c < NC; ++c) {
+      if (coh[c].id < 0) continue;
+      const int m0 = coh[c].m0;
+      const int nsl = min(G, coh[c].Ktot - m0);
+      const R* src = slices + (coh[c].slice_base + m0) * slst;
+      const int vec = (int)(16 / sizeof(R));
+      const long long nv = (long long)nsl * slst / vec;
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(sSl + (long long)c * G * slst);
+      for (long long i = threadIdx.x; i < nv; i += blockDim.x) d4[i] = s4[i];
+      if (threadIdx.x < nsl) {
+        SliceInfo si = a.sinfo[coh[c].slice_base + m0 + threadIdx.x];
+        sT[(c * G + threadIdx.x) * 2] = si.Tt;
+        sT[(c * G + threadIdx.x) * 2 + 1] = si.dTt;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int s = ready[i];
+      if (s < 0) continue;
+      const int c = s / CC;
+      const Cohort<D, R>& ch = coh[c];
+      const InstanceParams ip = ipt[a.tn[ch.ti].inst];
+      WalkStream ws;
+      ws.k0 = a.k0; ws.k1 = a.k1; ws.node = ch.node; ws.tag = ch.tag;
+      ws.sample = (uint32_t)(ch.sample0 + (s - c * CC));
+      const int m0 = ch.m0;
+      int mv = st.mnext[s];
+      while (mv >= m0 && mv < m0 + G) {
+        const int q = st.q[s];
+        constexpr int W = step_words(D);
+        const uint32_t w0 = (uint32_t)q * W;
+        // Green-function point of the pending ball
+        R thg[D], Y[D];
+        direction<D, R>(ws, w0 + dir_words(D), thg);
+        const uint32_t wr = w0 + 2 * dir_words(D);
+        Philox4 rb = ws.block(wr >> 2);
+        R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
+        R U2 = R(0);
+        if (D == 2) U2 = U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]);
+        const R v = green_radius<D, R>(U1, U2);
+        const R r = st.r[s];
+        const R rv = Ar<R>::mul(r, v);
+#pragma unroll
+        for (int e = 0; e < D; ++e) Y[e] = Ar<R>::add(st.X[e][s], Ar<R>::mul(rv, thg[e]));
+        const R w = st.w[s];
+        R Ssum = st.S[s];
+        if (w > R(0)) {
+          const int b = mv - m0;
+          const R* sc = sSl + ((long long)c * G + b) * slst;
+          R res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)sT[(c * G + b) * 2],
+                                          (R)sT[(c * G + b) * 2 + 1]);
+          Ssum += w * res;
+          ++points;
+        }
+        st.S[s] = Ssum;
+        if (st.last[s]) { st.mnext[s] = -1; break; }
+        // step to the sphere of the ball
+        R th[D];
+        direction<D, R>(ws, w0, th);
+#pragma unroll
+        for (int e = 0; e < D; ++e) st.X[e][s] = Ar<R>::add(st.X[e][s], Ar<R>::mul(r, th[e]));
+        st.q[s] = q + 1;
+        prepare_step<D, R>(st, s, ws, ch.J, ch.delta, ch.sub, ch.Ktot, G, a.gbits, shell, kappa, a.max_steps,
+                           dummy_acc, capped);
+        mv = st.mnext[s];
+      }
+    }
+    __syncthreads();
+    // advance every active cohort's window (a cohort started in this pass has not
+    // been processed yet and keeps window 0)
+    if (threadIdx.x < NC && coh[threadIdx.x].id >= 0) {
+      if (coh[threadIdx.x].fresh) coh[threadIdx.x].fresh = 0;
+      else coh[threadIdx.x].m0 += G;
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    points += __shfl_xor_sync(0xffffffffu, points, o);
+    capped += __shfl_xor_sync(0xffffffffu, capped, o);
+  }
+  if (lane == 0) {
+    if (points) atomicAdd(&a.counters[0], points);
+    if (capped) atomicAdd(&a.counters[1], capped);
+  }
+}
+
+// ----------------------------------------------------------------- Step 3
+// eps = (Neumaier sum of the chunk sums, in chunk order) / M;  u += eps.
+__global__ void update_kernel(const TimeNode* __restrict__ tn, const double* __restrict__ partial,
+                              double* __restrict__ U, double* __restrict__ eps_out,
+                              unsigned long long* __restrict__ max_eps_bits, int* status, long long n_nodes,
+                              int S, int n_chunks, double inv_M) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  int inst = -1;
+  if (i < n_nodes) {
+    long long ti = i / S;
+    int j = (int)(i - ti * S);
+    const TimeNode node = tn[ti];
+    inst = node.inst;
+    const double* pp = partial + i * n_chunks;
+    double sum = 0.0, comp = 0.0;
+    for (int c = 0; c < n_chunks; ++c) {
+      double x = pp[c];
+      double t = sum + x;
+      if (fabs(sum) >= fabs(x)) comp += (sum - t) + x; else comp += (x - t) + sum;
+      sum = t;
+    }
+    e = (sum + comp) * inv_M;
+    if (!isfinite(e)) atomicOr(status, 1);
+    U[node.u_off + (long long)node.ell * S + j] += e;
+    if (eps_out) eps_out[i] = e;
+    unsigned long long bits = __double_as_longlong(fabs(e));
+    atomicMax(&max_eps_bits[inst], bits);
+  }
+}
+
+// ----------------------------------------------------------------- Step 4 and first iterate
+// row 0 of interval 0 from u0; every other row equal to row 0.
+__global__ void init_first_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ u0,
+                                  double* __restrict__ U, int S) {
+  const InstInterval w = ii[blockIdx.x];
+  const int T = w.Mt + 1;
+  for (int i = threadIdx.x; i < T * S; i += blockDim.x)
+    U[w.u_off + i] = u0[(long long)w.inst * S + (i % S)];
+}
+
+// u*(x_j, t_n) = sum_k hw_k U[k][j] with hw_k = sum_q b_qk L_q(1); the next
+// interval starts from it in every row.
+__global__ void handoff_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ hw,
+                               double* __restrict__ U, int S) {
+  const InstInterval w = ii[blockIdx.x];
+  if (w.next_u_off < 0) return;
+  const int T = w.Mt + 1, Tn = w.next_Mt + 1;
+  const double* h = hw + w.h_off;
+  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < T; ++k) acc += h[k] * U[w.u_off + (long long)k * S + j];
+    for (int l = 0; l < Tn; ++l) U[w.next_u_off + (long long)l * S + j] = acc;
+  }
+}
+
+}  // namespace spmc

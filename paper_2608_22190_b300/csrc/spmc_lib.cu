@@ -1,0 +1,701 @@
+// spmc_lib.cu -- C-ABI of the B300 hp-version time-stepping spectral Monte
+// Carlo library (declared in include/spmc.h): plans, problem set-up, the hp
+// driver of Algorithm 1 and its launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "spmc.h"
+#include "spmc_kernels.cuh"
+#include "spmc_tables.h"
+
+using namespace spmc;
+
+namespace {
+
+struct HostProblem {
+  bool set = false;
+  int n_int = 0;
+  std::vector<double> t;
+  std::vector<int> deg;
+  InstanceParams ip{};
+  std::vector<double> u0;       // nodal
+  int u0_kind = 0, n_coef = 0;
+  std::vector<double> u0_coef;  // phi coefficients (for the gradient)
+};
+
+struct Round {
+  // work tables of interval index r across instances (host and device copies)
+  std::vector<TimeNode> tn;
+  std::vector<InstInterval> ii;           // active instances
+  std::vector<InstInterval> ii_of_node;   // per time node
+  std::vector<long long> slice_node;      // per slice -> time node
+  long long n_slices = 0;
+  TimeNode* d_tn = nullptr;
+  InstInterval* d_ii = nullptr;
+  InstInterval* d_ii_of_node = nullptr;
+  long long* d_slice_node = nullptr;
+  long long coef_total = 0;
+  int iteration = 0;                      // iterations run so far on this interval
+};
+
+}  // namespace
+
+struct spmc_plan_s {
+  spmc_plan_desc d{};
+  std::string err;
+  int S = 1;
+  int chunk = 512, threads = 256;   // chunk = samples per cohort
+  int NC = 2;                        // cohorts in flight per block
+  int* d_work = nullptr;             // persistent-kernel work counter
+  std::vector<HostProblem> probs;
+  bool built = false;
+  std::vector<double> xnodes;
+  // device
+  double* d_x = nullptr;
+  double* d_A = nullptr;
+  double* d_B = nullptr;
+  double* d_hw = nullptr;
+  InstanceParams* d_ip = nullptr;
+  double* d_u0 = nullptr;
+  double* d_U = nullptr;
+  double* d_coef = nullptr;
+  void* d_slices = nullptr;
+  SliceInfo* d_sinfo = nullptr;
+  double* d_partial = nullptr;
+  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_maxeps = nullptr;
+  int* d_status = nullptr;
+  long long U_total = 0;
+  std::vector<long long> inst_off, inst_count;
+  std::vector<std::vector<long long>> int_off;
+  std::vector<Round> rounds;
+  long long slice_cap = 0, partial_cap = 0, coef_cap = 0;
+  int row = 32, half = 64;       // slice geometry: row width, entries of C (= of H)
+  double shell = 1e-4;           // absorption shell in use
+  long long sl_stride = 132;     // entries between slices (bank-spread)
+  spmc_stats stats{};
+  bool solved = false;
+  bool timing = false;
+  bool params_dirty = false;   // instance parameters / u0 changed, layout unchanged
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+};
+
+namespace {
+
+const char* kVersion = "spmc-b300 0.1 (sm_103a)";
+
+#define SPMC_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      plan->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return e_ == cudaErrorMemoryAllocation ? SPMC_ERR_OOM : SPMC_ERR_CUDA;         \
+    }                                                                                \
+  } while (0)
+
+spmc_status fail(spmc_plan_t plan, spmc_status st, const std::string& msg) {
+  if (plan) plan->err = msg;
+  return st;
+}
+
+int nstar_of(int n_ref, double s, double h) {
+  double v = std::ceil((double)n_ref * s / h - 1e-9);
+  return v < 1.0 ? 1 : (int)v;
+}
+
+template <typename T>
+spmc_status upload(spmc_plan_t plan, T** dptr, const std::vector<T>& v) {
+  if (*dptr) { cudaFree(*dptr); *dptr = nullptr; }
+  if (v.empty()) return SPMC_OK;
+  SPMC_CUDA(cudaMalloc((void**)dptr, sizeof(T) * v.size()));
+  SPMC_CUDA(cudaMemcpy(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return SPMC_OK;
+}
+
+size_t sweep_smem(int D, int G, long long sl_stride, int NC, int CC, size_t rsz, size_t cohort_size) {
+  size_t base = ((NC * G * sl_stride * rsz + 15) / 16) * 16;
+  size_t NS = (size_t)NC * CC;
+  size_t st = NS * ((D + 4) * rsz + 5 * sizeof(int));
+  size_t co = ((NC * cohort_size + 15) / 16) * 16;
+  return base + st + co + 3 * NC * sizeof(int) + (size_t)NC * G * 2 * sizeof(double) + 16;
+}
+
+// Slice geometry: rows padded to the template width of the sweep (16-byte
+// vector loads), consecutive slices offset by 4 banks (conflict-free reads of
+// the n_sub slices of a window).
+void slice_geometry(spmc_plan_t plan) {
+  const int n = plan->d.n_space;
+  int row = 32;
+  if (plan->d.dim == 2) row = n <= 8 ? 8 : (n <= 16 ? 16 : (n <= 24 ? 24 : 32));
+  plan->row = row;
+  plan->half = plan->d.dim == 2 ? n * row : row;
+  long long SL = 2LL * plan->half;
+  if (plan->d.precision == SPMC_FP64) plan->sl_stride = SL + ((2 - SL % 16) + 16) % 16;
+  else plan->sl_stride = SL + ((4 - SL % 32) + 32) % 32;
+}
+
+// Build the per-interval work tables, the nodal layout and the workspace once
+// every instance is set.
+spmc_status build(spmc_plan_t plan) {
+  const spmc_plan_desc& d = plan->d;
+  const int S = plan->S, n = d.n_space, B = d.batch;
+  for (int i = 0; i < B; ++i)
+    if (!plan->probs[i].set) return fail(plan, SPMC_ERR_INVALID, "instance " + std::to_string(i) + " not set");
+  // nodal layout: instance-major, interval blocks of (M_n+1) x S
+  plan->inst_off.assign(B, 0);
+  plan->inst_count.assign(B, 0);
+  plan->int_off.assign(B, {});
+  long long off = 0;
+  for (int i = 0; i < B; ++i) {
+    plan->inst_off[i] = off;
+    for (int m = 0; m < plan->probs[i].n_int; ++m) {
+      plan->int_off[i].push_back(off);
+      off += (long long)(plan->probs[i].deg[m] + 1) * S;
+    }
+    plan->inst_count[i] = off - plan->inst_off[i];
+  }
+  plan->U_total = off;
+  // time analysis matrices and hand-off weights per degree
+  std::map<int, std::pair<long long, long long>> bmap;
+  std::vector<double> Bh, Hh;
+  std::vector<std::vector<double>> xi_of(d.max_degree + 1);
+  for (int i = 0; i < B; ++i)
+    for (int m = 0; m < plan->probs[i].n_int; ++m) {
+      int Mt = plan->probs[i].deg[m];
+      if (bmap.count(Mt)) continue;
+      std::vector<double> Bm((Mt + 1) * (Mt + 1));
+      time_analysis(d.time_family, Mt, Bm.data());
+      long long bo = Bh.size(), ho = Hh.size();
+      Bh.insert(Bh.end(), Bm.begin(), Bm.end());
+      for (int k = 0; k <= Mt; ++k) {
+        double s = 0.0;
+        for (int q = 0; q <= Mt; ++q) s += Bm[q * (Mt + 1) + k];
+        Hh.push_back(s);
+      }
+      bmap[Mt] = {bo, ho};
+      xi_of[Mt].resize(Mt + 1);
+      time_nodes(d.time_family, Mt, xi_of[Mt].data());
+    }
+  spmc_status st;
+  if ((st = upload(plan, &plan->d_B, Bh)) != SPMC_OK) return st;
+  if ((st = upload(plan, &plan->d_hw, Hh)) != SPMC_OK) return st;
+  // rounds
+  int R = 0;
+  for (int i = 0; i < B; ++i) R = std::max(R, plan->probs[i].n_int);
+  for (auto& r : plan->rounds) { cudaFree(r.d_tn); cudaFree(r.d_ii); cudaFree(r.d_ii_of_node); cudaFree(r.d_slice_node); }
+  plan->rounds.assign(R, Round());
+  long long slice_cap = 0, partial_cap = 0, coef_cap = 0;
+  const int n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
+  for (int r = 0; r < R; ++r) {
+    Round& rd = plan->rounds[r];
+    long long coef_off = 0, slice_off = 0;
+    for (int i = 0; i < B; ++i) {
+      const HostProblem& P = plan->probs[i];
+      if (r >= P.n_int) continue;
+      int Mt = P.deg[r];
+      InstInterval w{};
+      w.inst = i; w.Mt = Mt; w.u_off = plan->int_off[i][r]; w.c_off = coef_off;
+      w.b_off = bmap[Mt].first; w.h_off = bmap[Mt].second;
+      w.next_u_off = (r + 1 < P.n_int) ? plan->int_off[i][r + 1] : -1;
+      w.next_Mt = (r + 1 < P.n_int) ? P.deg[r + 1] : 0;
+      w.t0 = P.t[r]; w.h = P.t[r + 1] - P.t[r];
+      coef_off += 2LL * (Mt + 1) * S;
+      rd.ii.push_back(w);
+      const std::vector<double>& xi = xi_of[Mt];
+      for (int l = 1; l <= Mt; ++l) {
+        TimeNode t{};
+        t.inst = i; t.ell = l; t.Mt = Mt; t.u_off = w.u_off; t.t0 = w.t0; t.h = w.h;
+        double s = (xi[l] + 1.0) * 0.5 * w.h;
+        t.t_node = w.t0 + s;
+        t.nstar = nstar_of(d.n_ref, s, w.h);
+        t.slice_base = slice_off;
+        long long ns = (long long)d.n_sub * t.nstar;
+        for (long long m = 0; m < ns; ++m) rd.slice_node.push_back((long long)rd.tn.size());
+        slice_off += ns;
+        rd.tn.push_back(t);
+        rd.ii_of_node.push_back(w);
+      }
+    }
+    rd.n_slices = slice_off;
+    rd.coef_total = coef_off;
+    slice_cap = std::max(slice_cap, slice_off);
+    partial_cap = std::max(partial_cap, (long long)rd.tn.size() * S * n_chunks);
+    coef_cap = std::max(coef_cap, coef_off);
+    if ((st = upload(plan, &rd.d_tn, rd.tn)) != SPMC_OK) return st;
+    if ((st = upload(plan, &rd.d_ii, rd.ii)) != SPMC_OK) return st;
+    if ((st = upload(plan, &rd.d_ii_of_node, rd.ii_of_node)) != SPMC_OK) return st;
+    if ((st = upload(plan, &rd.d_slice_node, rd.slice_node)) != SPMC_OK) return st;
+  }
+  // workspace
+  cudaFree(plan->d_U); cudaFree(plan->d_coef); cudaFree(plan->d_slices); cudaFree(plan->d_sinfo);
+  cudaFree(plan->d_partial);
+  plan->d_U = nullptr; plan->d_coef = nullptr; plan->d_slices = nullptr; plan->d_sinfo = nullptr; plan->d_partial = nullptr;
+  size_t rsz = d.precision == SPMC_FP64 ? sizeof(double) : sizeof(float);
+  SPMC_CUDA(cudaMalloc((void**)&plan->d_U, sizeof(double) * std::max(1LL, plan->U_total)));
+  SPMC_CUDA(cudaMalloc((void**)&plan->d_coef, sizeof(double) * std::max(1LL, coef_cap)));
+  slice_geometry(plan);
+  SPMC_CUDA(cudaMalloc(&plan->d_slices, rsz * plan->sl_stride * std::max(1LL, slice_cap)));
+  SPMC_CUDA(cudaMalloc((void**)&plan->d_sinfo, sizeof(SliceInfo) * std::max(1LL, slice_cap)));
+  SPMC_CUDA(cudaMalloc((void**)&plan->d_partial, sizeof(double) * std::max(1LL, partial_cap)));
+  plan->slice_cap = slice_cap; plan->partial_cap = partial_cap; plan->coef_cap = coef_cap;
+  std::vector<InstanceParams> ips(B);
+  std::vector<double> u0(B * (size_t)S);
+  for (int i = 0; i < B; ++i) {
+    ips[i] = plan->probs[i].ip;
+    std::copy(plan->probs[i].u0.begin(), plan->probs[i].u0.end(), u0.begin() + (size_t)i * S);
+  }
+  if ((st = upload(plan, &plan->d_ip, ips)) != SPMC_OK) return st;
+  if ((st = upload(plan, &plan->d_u0, u0)) != SPMC_OK) return st;
+  plan->built = true;
+  return SPMC_OK;
+}
+
+// Re-upload instance parameters and initial values (same partition and degrees).
+spmc_status refresh_params(spmc_plan_t plan, cudaStream_t stream) {
+  const int B = plan->d.batch, S = plan->S;
+  static thread_local std::vector<InstanceParams> ips;
+  static thread_local std::vector<double> u0;
+  ips.resize(B);
+  u0.resize((size_t)B * S);
+  for (int i = 0; i < B; ++i) {
+    ips[i] = plan->probs[i].ip;
+    std::copy(plan->probs[i].u0.begin(), plan->probs[i].u0.end(), u0.begin() + (size_t)i * S);
+  }
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_ip, ips.data(), sizeof(InstanceParams) * B, cudaMemcpyHostToDevice, stream));
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_u0, u0.data(), sizeof(double) * u0.size(), cudaMemcpyHostToDevice, stream));
+  SPMC_CUDA(cudaStreamSynchronize(stream));
+  plan->params_dirty = false;
+  return SPMC_OK;
+}
+
+spmc_status ensure_ready(spmc_plan_t plan, cudaStream_t stream) {
+  if (!plan->built) return build(plan);
+  if (plan->params_dirty) return refresh_params(plan, stream);
+  return SPMC_OK;
+}
+
+template <int D, int NMAX, typename R>
+spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const spmc_plan_desc& d = plan->d;
+  SweepArgs a;
+  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
+  a.partial = plan->d_partial; a.counters = plan->d_counters; a.status = plan->d_status;
+  a.n = d.n_space; a.S = plan->S;
+  a.chunk = plan->chunk;
+  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
+  a.n_sub = d.n_sub;
+  int gb = 0;
+  while ((1 << gb) < d.n_sub) ++gb;
+  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
+  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
+  a.interval = interval; a.iteration = iteration;
+  a.M = d.M;
+  a.sl_stride = plan->sl_stride;
+  a.half = plan->half;
+  const long long n_cohorts = (long long)rd.tn.size() * plan->S * a.n_chunks;
+  if (n_cohorts <= 0) return SPMC_OK;
+  size_t smem = sweep_smem(D, d.n_sub, plan->sl_stride, plan->NC, plan->chunk, sizeof(R), sizeof(Cohort<D, R>));
+  auto kern = sweep_kernel<D, NMAX, R>;
+  SPMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, plan->threads, smem));
+  if (occ < 1) return fail(plan, SPMC_ERR_UNSUPPORTED, "sweep configuration does not fit on an SM");
+  long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
+  SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (plan->timing) {
+    if (!plan->ev_free.empty()) { ev = plan->ev_free.back(); plan->ev_free.pop_back(); }
+    else { SPMC_CUDA(cudaEventCreate(&ev.first)); SPMC_CUDA(cudaEventCreate(&ev.second)); }
+    SPMC_CUDA(cudaEventRecord(ev.first, stream));
+  }
+  kern<<<(unsigned)grid, plan->threads, smem, stream>>>(a, plan->NC, plan->chunk, n_cohorts, plan->d_work);
+  SPMC_CUDA(cudaGetLastError());
+  if (plan->timing) {
+    SPMC_CUDA(cudaEventRecord(ev.second, stream));
+    plan->ev_pending.push_back(ev);
+  }
+  return SPMC_OK;
+}
+
+template <typename R>
+spmc_status dispatch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const int n = plan->d.n_space;
+  if (plan->d.dim == 1) return launch_sweep<1, 32, R>(plan, stream, rd, interval, iteration);
+  if (plan->d.dim == 2) {
+    if (n <= 8) return launch_sweep<2, 8, R>(plan, stream, rd, interval, iteration);
+    if (n <= 16) return launch_sweep<2, 16, R>(plan, stream, rd, interval, iteration);
+    if (n <= 24) return launch_sweep<2, 24, R>(plan, stream, rd, interval, iteration);
+    return launch_sweep<2, 32, R>(plan, stream, rd, interval, iteration);
+  }
+  return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
+}
+
+// One residual iteration on interval r for every instance that has it.
+spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
+  Round& rd = plan->rounds[r];
+  const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
+  const int iteration = ++rd.iteration;
+  if (rd.ii.empty()) return SPMC_OK;
+  int maxT = 0;
+  for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
+  size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
+  if (D == 1) {
+    SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
+                                                                          plan->d_coef, n);
+  } else {
+    SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
+                                                                          plan->d_coef, n);
+  }
+  SPMC_CUDA(cudaGetLastError());
+  bool fp64 = plan->d.precision == SPMC_FP64;
+  if (rd.n_slices > 0) {
+    if (D == 1) {
+      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+    } else {
+      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+    }
+    SPMC_CUDA(cudaGetLastError());
+  }
+  spmc_status st = fp64 ? dispatch_sweep<double>(plan, stream, rd, r, iteration)
+                        : dispatch_sweep<float>(plan, stream, rd, r, iteration);
+  if (st != SPMC_OK) return st;
+  SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, stream));
+  long long nn = (long long)rd.tn.size() * S;
+  int n_chunks = (int)((plan->d.M + plan->chunk - 1) / plan->chunk);
+  if (nn > 0) {
+    update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(rd.d_tn, plan->d_partial, plan->d_U, nullptr,
+                                                                    plan->d_maxeps, plan->d_status, nn, S, n_chunks,
+                                                                    1.0 / (double)plan->d.M);
+    SPMC_CUDA(cudaGetLastError());
+  }
+  return SPMC_OK;
+}
+
+spmc_status begin_interval(spmc_plan_t plan, cudaStream_t stream, int r) {
+  Round& rd = plan->rounds[r];
+  rd.iteration = 0;
+  if (r == 0) {
+    if (!rd.ii.empty())
+      init_first_kernel<<<(unsigned)rd.ii.size(), 256, 0, stream>>>(rd.d_ii, plan->d_u0, plan->d_U, plan->S);
+  } else {
+    Round& prev = plan->rounds[r - 1];
+    if (!prev.ii.empty())
+      handoff_kernel<<<(unsigned)prev.ii.size(), 256, 0, stream>>>(prev.d_ii, plan->d_hw, plan->d_U, plan->S);
+  }
+  SPMC_CUDA(cudaGetLastError());
+  return SPMC_OK;
+}
+
+spmc_status read_status(spmc_plan_t plan, cudaStream_t stream) {
+  int h = 0;
+  SPMC_CUDA(cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  SPMC_CUDA(cudaStreamSynchronize(stream));
+  if (h & 1) return fail(plan, SPMC_ERR_NONFINITE, "a non-finite eps was produced");
+  if (h & 2) return fail(plan, SPMC_ERR_TIMEOUT, "a sweep block exceeded its round budget");
+  return SPMC_OK;
+}
+
+spmc_status read_max_eps(spmc_plan_t plan, cudaStream_t stream, double* out) {
+  std::vector<unsigned long long> bits(plan->d.batch);
+  SPMC_CUDA(cudaMemcpyAsync(bits.data(), plan->d_maxeps, sizeof(unsigned long long) * bits.size(),
+                            cudaMemcpyDeviceToHost, stream));
+  SPMC_CUDA(cudaStreamSynchronize(stream));
+  double mx = 0.0;
+  for (auto b : bits) { double v; std::memcpy(&v, &b, sizeof v); mx = std::max(mx, v); }
+  *out = mx;
+  return SPMC_OK;
+}
+
+void drain_timing(spmc_plan_t plan) {
+  for (auto& ev : plan->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(ev.second) == cudaSuccess && cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+      plan->stats.sweep_ms += ms;
+      plan->stats.sweep_launches += 1;
+    }
+    plan->ev_free.push_back(ev);
+  }
+  plan->ev_pending.clear();
+}
+
+void sync_counters(spmc_plan_t plan) {
+  drain_timing(plan);
+  unsigned long long c[2] = {0, 0};
+  if (cudaMemcpy(c, plan->d_counters, sizeof c, cudaMemcpyDeviceToHost) == cudaSuccess) {
+    plan->stats.points = (long long)c[0];
+    plan->stats.capped = (long long)c[1];
+  }
+}
+
+}  // namespace
+
+// =================================================================== C-ABI
+extern "C" {
+
+const char* spmc_version(void) { return kVersion; }
+
+spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
+  if (!out) return SPMC_ERR_INVALID;
+  *out = nullptr;
+  if (!desc) return SPMC_ERR_INVALID;
+  const spmc_plan_desc& d = *desc;
+  if (d.dim < 1 || d.dim > 5 || d.n_space < 2 || d.n_space > 32 || d.max_intervals < 1 || d.max_degree < 1 ||
+      d.max_degree > 32 || d.M < 1 || d.K < 1 || d.n_ref < 1 || d.n_sub < 1 || d.n_sub > 16 ||
+      (d.n_sub & (d.n_sub - 1)) || !(d.shell >= 0.0) || d.shell >= 0.5 || d.max_steps < 1 || !(d.kappa > 0.0) || d.batch < 1 ||
+      (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
+      (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL)
+    return SPMC_ERR_INVALID;
+  if (d.dim > 2) return SPMC_ERR_UNSUPPORTED;
+  if (d.tol > 0.0 && d.batch > 1) return SPMC_ERR_UNSUPPORTED;
+  spmc_plan_t plan = new spmc_plan_s();
+  plan->d = d;
+  plan->S = 1;
+  for (int e = 0; e < d.dim; ++e) plan->S *= d.n_space;
+  plan->probs.assign(d.batch, HostProblem());
+  plan->chunk = (int)std::min<long long>(d.precision == SPMC_FP64 ? 256 : 512, ((d.M + 31) / 32) * 32);
+  plan->NC = (d.dim == 1) ? 4 : 2;
+  slice_geometry(plan);
+  plan->threads = 256;
+  // tables
+  const int n = d.n_space;
+  plan->xnodes.resize(n);
+  space_nodes(n, plan->xnodes.data());
+  // shell == 0: half the distance of the outermost node to the boundary, at most 2e-3
+  plan->shell = d.shell > 0.0 ? d.shell : std::min(2e-3, 0.5 * (1.0 - std::fabs(plan->xnodes[0])));
+  std::vector<double> A(n * n);
+  space_analysis(n, A.data());
+  spmc_status st;
+  if ((st = upload(plan, &plan->d_x, plan->xnodes)) != SPMC_OK) { spmc_destroy(plan); return st; }
+  if ((st = upload(plan, &plan->d_A, A)) != SPMC_OK) { spmc_destroy(plan); return st; }
+  double ra[kMaxModes], rb[kMaxModes], lam[kMaxModes];
+  float raf[kMaxModes], rbf[kMaxModes], lamf[kMaxModes];
+  for (int p = 0; p < kMaxModes; ++p) {
+    ra[p] = p >= 2 ? (2.0 * p + 1.0) * (p + 1.0) / (p * (p + 2.0)) : 0.0;
+    rb[p] = p >= 2 ? (p + 1.0) / (p + 2.0) : 0.0;
+    lam[p] = (p + 1.0) * (p + 2.0);
+    raf[p] = (float)ra[p]; rbf[p] = (float)rb[p]; lamf[p] = (float)lam[p];
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_ra_d, ra, sizeof ra);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rb_d, rb, sizeof rb);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_lam_d, lam, sizeof lam);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ra_f, raf, sizeof raf);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rb_f, rbf, sizeof rbf);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_lam_f, lamf, sizeof lamf);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_counters, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_counters, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_maxeps, sizeof(unsigned long long) * d.batch);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_work, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    spmc_status r = (e == cudaErrorMemoryAllocation) ? SPMC_ERR_OOM : SPMC_ERR_CUDA;
+    spmc_destroy(plan);
+    return r;
+  }
+  *out = plan;
+  return SPMC_OK;
+}
+
+spmc_status spmc_set_problem(spmc_plan_t plan, int instance, const spmc_problem* prob) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!prob || instance < 0 || instance >= plan->d.batch) return fail(plan, SPMC_ERR_INVALID, "bad instance or problem");
+  const spmc_plan_desc& d = plan->d;
+  const spmc_problem& p = *prob;
+  if (p.n_intervals < 1 || p.n_intervals > d.max_intervals || !p.t_breaks || !p.degrees || !p.u0)
+    return fail(plan, SPMC_ERR_INVALID, "bad interval count or null array");
+  for (int m = 0; m < p.n_intervals; ++m) {
+    if (!(p.t_breaks[m + 1] > p.t_breaks[m])) return fail(plan, SPMC_ERR_INVALID, "t_breaks not increasing");
+    if (p.degrees[m] < 1 || p.degrees[m] > d.max_degree) return fail(plan, SPMC_ERR_INVALID, "degree out of range");
+  }
+  if (p.f_kind != SPMC_F_POLY3 && p.f_kind != SPMC_F_SIN) return fail(plan, SPMC_ERR_INVALID, "bad f_kind");
+  if (p.ex_kind < SPMC_EX_NONE || p.ex_kind > SPMC_EX_POLY) return fail(plan, SPMC_ERR_INVALID, "bad ex_kind");
+  HostProblem& H = plan->probs[instance];
+  bool same_layout = H.set && H.n_int == p.n_intervals &&
+                     std::equal(H.deg.begin(), H.deg.end(), p.degrees) &&
+                     std::equal(H.t.begin(), H.t.end(), p.t_breaks);
+  H.n_int = p.n_intervals;
+  H.t.assign(p.t_breaks, p.t_breaks + p.n_intervals + 1);
+  H.deg.assign(p.degrees, p.degrees + p.n_intervals);
+  H.ip.f_kind = p.f_kind; H.ip.ex_kind = p.ex_kind;
+  for (int k = 0; k < 4; ++k) H.ip.fc[k] = p.f_coef[k];
+  H.ip.f_scale = p.f_scale; H.ip.ex_beta = p.ex_beta;
+  const int S = plan->S, n = d.n_space, D = d.dim;
+  H.u0.assign(S, 0.0);
+  H.u0_kind = p.u0_kind;
+  if (p.u0_kind == SPMC_U0_NODAL) {
+    H.u0.assign(p.u0, p.u0 + S);
+  } else if (p.u0_kind == SPMC_U0_PHI_COEF) {
+    if (p.n_coef < 1 || p.n_coef > n) return fail(plan, SPMC_ERR_INVALID, "n_coef out of range");
+    H.n_coef = p.n_coef;
+    int nc = 1;
+    for (int e = 0; e < D; ++e) nc *= p.n_coef;
+    H.u0_coef.assign(p.u0, p.u0 + nc);
+    std::vector<double> ph((size_t)n * n);  // ph[j*n + p] = phi_p(x_j)
+    for (int j = 0; j < n; ++j) phi_values(n, plan->xnodes[j], &ph[(size_t)j * n]);
+    for (int j = 0; j < S; ++j) {
+      double acc = 0.0;
+      for (int c = 0; c < nc; ++c) {
+        double prod = p.u0[c];
+        int jj = j, cc = c;
+        for (int e = 0; e < D; ++e) { prod *= ph[(size_t)(jj % n) * n + (cc % p.n_coef)]; jj /= n; cc /= p.n_coef; }
+        acc += prod;
+      }
+      H.u0[j] = acc;
+    }
+  } else {
+    return fail(plan, SPMC_ERR_INVALID, "bad u0_kind");
+  }
+  H.set = true;
+  if (plan->built && same_layout) plan->params_dirty = true;
+  else plan->built = false;
+  plan->solved = false;
+  return SPMC_OK;
+}
+
+spmc_status spmc_solution_layout(spmc_plan_t plan, int instance, long long* offset, long long* count) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built) { spmc_status st = build(plan); if (st != SPMC_OK) return st; }
+  if (instance < 0 || instance >= plan->d.batch || !offset || !count) return fail(plan, SPMC_ERR_INVALID, "bad instance");
+  *offset = plan->inst_off[instance];
+  *count = plan->inst_count[instance];
+  return SPMC_OK;
+}
+
+spmc_status spmc_begin_interval(spmc_plan_t plan, void* cuda_stream, int interval) {
+  if (!plan) return SPMC_ERR_INVALID;
+  { spmc_status st = ensure_ready(plan, (cudaStream_t)cuda_stream); if (st != SPMC_OK) return st; }
+  if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  return begin_interval(plan, (cudaStream_t)cuda_stream, interval);
+}
+
+spmc_status spmc_iterate(spmc_plan_t plan, void* cuda_stream, int interval, int n_iter, double* max_eps_host) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "call spmc_begin_interval first");
+  if (interval < 0 || interval >= (int)plan->rounds.size() || n_iter < 0) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  for (int k = 0; k < n_iter; ++k) {
+    spmc_status st = iterate_once(plan, s, interval);
+    if (st != SPMC_OK) return st;
+  }
+  spmc_status st = read_status(plan, s);
+  if (st != SPMC_OK) return st;
+  double mx = 0.0;
+  if ((st = read_max_eps(plan, s, &mx)) != SPMC_OK) return st;
+  if (max_eps_host) *max_eps_host = mx;
+  plan->stats.iterations_run = n_iter;
+  plan->stats.last_max_eps = mx;
+  sync_counters(plan);
+  return SPMC_OK;
+}
+
+spmc_status spmc_solve(spmc_plan_t plan, void* cuda_stream, double* u_nodes) {
+  if (!plan) return SPMC_ERR_INVALID;
+  { spmc_status st = ensure_ready(plan, (cudaStream_t)cuda_stream); if (st != SPMC_OK) return st; }
+  if (!u_nodes) return fail(plan, SPMC_ERR_INVALID, "null output");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const spmc_plan_desc& d = plan->d;
+  int total_iters = 0;
+  double mx = 0.0;
+  for (int r = 0; r < (int)plan->rounds.size(); ++r) {
+    spmc_status st = begin_interval(plan, s, r);
+    if (st != SPMC_OK) return st;
+    for (int k = 0; k < d.K; ++k) {
+      st = iterate_once(plan, s, r);
+      if (st != SPMC_OK) return st;
+      ++total_iters;
+      if (d.tol > 0.0) {
+        if ((st = read_max_eps(plan, s, &mx)) != SPMC_OK) return st;
+        if (mx < d.tol) break;
+      }
+    }
+  }
+  SPMC_CUDA(cudaMemcpyAsync(u_nodes, plan->d_U, sizeof(double) * plan->U_total, cudaMemcpyDefault, s));
+  spmc_status st = read_status(plan, s);
+  if (st != SPMC_OK) return st;
+  plan->stats.iterations_run = total_iters;
+  plan->solved = true;
+  return SPMC_OK;
+}
+
+spmc_status spmc_get_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, double* dst) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "plan not built");
+  if (instance < 0 || instance >= plan->d.batch || !dst) return fail(plan, SPMC_ERR_INVALID, "bad instance");
+  const HostProblem& P = plan->probs[instance];
+  if (interval < 0 || interval >= P.n_int) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  size_t cnt = (size_t)(P.deg[interval] + 1) * plan->S;
+  SPMC_CUDA(cudaMemcpyAsync(dst, plan->d_U + plan->int_off[instance][interval], sizeof(double) * cnt,
+                            cudaMemcpyDefault, (cudaStream_t)cuda_stream));
+  return SPMC_OK;
+}
+
+spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, const double* src) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built) { spmc_status st = build(plan); if (st != SPMC_OK) return st; }
+  if (instance < 0 || instance >= plan->d.batch || !src) return fail(plan, SPMC_ERR_INVALID, "bad instance");
+  const HostProblem& P = plan->probs[instance];
+  if (interval < 0 || interval >= P.n_int) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  size_t cnt = (size_t)(P.deg[interval] + 1) * plan->S;
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_U + plan->int_off[instance][interval], src, sizeof(double) * cnt,
+                            cudaMemcpyDefault, (cudaStream_t)cuda_stream));
+  return SPMC_OK;
+}
+
+spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_du_T, double* grad_f_scale,
+                      double* grad_u0_coef) {
+  (void)cuda_stream; (void)dloss_du_T; (void)grad_f_scale; (void)grad_u0_coef;
+  if (!plan) return SPMC_ERR_INVALID;
+  return fail(plan, SPMC_ERR_UNSUPPORTED, "gradient not built yet");
+}
+
+spmc_status spmc_set_timing(spmc_plan_t plan, int enable) {
+  if (!plan) return SPMC_ERR_INVALID;
+  drain_timing(plan);
+  plan->timing = enable != 0;
+  if (plan->timing) { plan->stats.sweep_ms = 0.0; plan->stats.sweep_launches = 0; }
+  return SPMC_OK;
+}
+
+spmc_status spmc_space_nodes(spmc_plan_t plan, double* x_host) {
+  if (!plan || !x_host) return SPMC_ERR_INVALID;
+  std::copy(plan->xnodes.begin(), plan->xnodes.end(), x_host);
+  return SPMC_OK;
+}
+
+spmc_status spmc_get_stats(spmc_plan_t plan, spmc_stats* out) {
+  if (!plan || !out) return SPMC_ERR_INVALID;
+  sync_counters(plan);
+  *out = plan->stats;
+  return SPMC_OK;
+}
+
+const char* spmc_last_error(spmc_plan_t plan) { return plan ? plan->err.c_str() : "null plan"; }
+
+void spmc_destroy(spmc_plan_t plan) {
+  if (!plan) return;
+  drain_timing(plan);
+  for (auto& ev : plan->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  for (auto& r : plan->rounds) { cudaFree(r.d_tn); cudaFree(r.d_ii); cudaFree(r.d_ii_of_node); cudaFree(r.d_slice_node); }
+  cudaFree(plan->d_x); cudaFree(plan->d_A); cudaFree(plan->d_B); cudaFree(plan->d_hw); cudaFree(plan->d_ip);
+  cudaFree(plan->d_u0); cudaFree(plan->d_U); cudaFree(plan->d_coef); cudaFree(plan->d_slices);
+  cudaFree(plan->d_sinfo); cudaFree(plan->d_partial); cudaFree(plan->d_counters); cudaFree(plan->d_maxeps);
+  cudaFree(plan->d_status);
+  cudaFree(plan->d_work);
+  delete plan;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// spmc_tables.cpp -- host-side node and transform tables of the CUDA library.
+//
+// Gauss-type nodes (Section 2.3): Jacobi-Gauss (1,1) in space; shifted
+// Legendre-Gauss-Lobatto or left Gauss-Radau in time.  Zeros are found as zeros
+// of Jacobi polynomials P^{(a,b)}_n by Newton's method with deflation:
+//   JG(1,1) interior nodes      = zeros of P^{(1,1)}_n,
+//   LGL interior nodes          = zeros of P^{(1,1)}_{M-1}  (= zeros of L_M'),
+//   left-Radau interior nodes   = zeros of P^{(0,1)}_M     (with -1 added).
+// Analysis matrices: a_pj of Eq. spacelag and b_qk of Eq. timeLag.
+#include "spmc_tables.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace spmc {
+
+static const double kPi = 3.14159265358979323846;
+
+// P^{(a,b)}_0..P^{(a,b)}_m at x by the standard three-term recurrence.
+void jacobi_values(int m, double a, double b, double x, double* P) {
+  P[0] = 1.0;
+  if (m == 0) return;
+  P[1] = 0.5 * ((a + b + 2.0) * x + (a - b));
+  for (int n = 2; n <= m; ++n) {
+    double c = 2.0 * n + a + b;
+    double a1 = 2.0 * n * (n + a + b) * (c - 2.0);
+    double a2 = (c - 1.0) * (a * a - b * b);
+    double a3 = (c - 2.0) * (c - 1.0) * c;
+    double a4 = 2.0 * (n + a - 1.0) * (n + b - 1.0) * c;
+    P[n] = ((a2 + a3 * x) * P[n - 1] - a4 * P[n - 2]) / a1;
+  }
+}
+
+// P^{(a,b)}_n and its derivative (d/dx P^{(a,b)}_n = (n+a+b+1)/2 P^{(a+1,b+1)}_{n-1}).
+static void jacobi_and_derivative(int n, double a, double b, double x, double* val, double* der) {
+  std::vector<double> P(n + 1), Q(std::max(n, 1));
+  jacobi_values(n, a, b, x, P.data());
+  *val = P[n];
+  if (n == 0) { *der = 0.0; return; }
+  jacobi_values(n - 1, a + 1.0, b + 1.0, x, Q.data());
+  *der = 0.5 * (n + a + b + 1.0) * Q[n - 1];
+}
+
+// The n zeros of P^{(a,b)}_n in ascending order.
+void jacobi_zeros(int n, double a, double b, double* z) {
+  for (int k = 0; k < n; ++k) {
+    // guess between Chebyshev points of the first kind
+    double x = -std::cos((2.0 * k + 1.0) * kPi / (2.0 * n + 1.0));
+    for (int it = 0; it < 200; ++it) {
+      double p, dp;
+      jacobi_and_derivative(n, a, b, x, &p, &dp);
+      double s = 0.0;
+      for (int i = 0; i < k; ++i) s += 1.0 / (x - z[i]);
+      double dx = p / (dp - s * p);
+      x -= dx;
+      if (std::fabs(dx) <= 4e-16 * std::max(1.0, std::fabs(x))) {
+        // two polishing steps
+        for (int pol = 0; pol < 2; ++pol) {
+          jacobi_and_derivative(n, a, b, x, &p, &dp);
+          s = 0.0;
+          for (int i = 0; i < k; ++i) s += 1.0 / (x - z[i]);
+          x -= p / (dp - s * p);
+        }
+        break;
+      }
+    }
+    z[k] = x;
+  }
+  std::sort(z, z + n);
+}
+
+void legendre_values(int m, double x, double* L) { jacobi_values(m, 0.0, 0.0, x, L); }
+
+void space_nodes(int n, double* x) { jacobi_zeros(n, 1.0, 1.0, x); }
+
+void time_nodes(int family, int M, double* xi) {
+  xi[0] = -1.0;
+  if (family == 0) {
+    xi[M] = 1.0;
+    if (M >= 2) jacobi_zeros(M - 1, 1.0, 1.0, xi + 1);
+  } else {
+    jacobi_zeros(M, 0.0, 1.0, xi + 1);
+  }
+}
+
+void time_weights(int family, int M, const double* xi, double* w) {
+  std::vector<double> L(M + 1);
+  for (int k = 0; k <= M; ++k) {
+    legendre_values(M, xi[k], L.data());
+    double LM = L[M];
+    if (family == 0) w[k] = 2.0 / (M * (M + 1.0) * LM * LM);
+    else w[k] = (k == 0) ? 2.0 / ((M + 1.0) * (M + 1.0)) : (1.0 - xi[k]) / ((M + 1.0) * (M + 1.0) * LM * LM);
+  }
+}
+
+// a_pj (row-major [p][j]) of Eq. spacelag with the JG(1,1) weights
+// w_j = 8(n+1) / ((n+2) (1-x_j^2) P_n'(x_j)^2).
+void space_analysis(int n, double* A) {
+  std::vector<double> x(n), P(n + 1);
+  space_nodes(n, x.data());
+  for (int j = 0; j < n; ++j) {
+    double pn, dpn;
+    jacobi_and_derivative(n, 1.0, 1.0, x[j], &pn, &dpn);
+    double one_m = 1.0 - x[j] * x[j];
+    double wj = 8.0 * (n + 1.0) / ((n + 2.0) * one_m * dpn * dpn);
+    jacobi_values(n - 1, 1.0, 1.0, x[j], P.data());
+    for (int p = 0; p < n; ++p) {
+      double gt = 8.0 * (p + 1.0) / ((2.0 * p + 3.0) * (p + 2.0));
+      A[p * n + j] = wj * P[p] / (one_m * gt);
+    }
+  }
+}
+
+// b_qk (row-major [q][k]) of Eq. timeLag on the reference interval; gamma_q =
+// 2/(2q+1) for q < M and the discrete norm sum_k L_M(xi_k)^2 w_k for q = M.
+void time_analysis(int family, int M, double* B) {
+  std::vector<double> xi(M + 1), w(M + 1), L(M + 1), Lk((M + 1) * (M + 1));
+  time_nodes(family, M, xi.data());
+  time_weights(family, M, xi.data(), w.data());
+  for (int k = 0; k <= M; ++k) {
+    legendre_values(M, xi[k], L.data());
+    for (int q = 0; q <= M; ++q) Lk[q * (M + 1) + k] = L[q];
+  }
+  double gM = 0.0;
+  for (int k = 0; k <= M; ++k) gM += Lk[M * (M + 1) + k] * Lk[M * (M + 1) + k] * w[k];
+  for (int q = 0; q <= M; ++q) {
+    double g = (q < M) ? 2.0 / (2.0 * q + 1.0) : gM;
+    for (int k = 0; k <= M; ++k) B[q * (M + 1) + k] = Lk[q * (M + 1) + k] * w[k] / g;
+  }
+}
+
+// phi_p(x) = (1-x^2) P^{(1,1)}_p(x), p < n (u0 from coefficients).
+void phi_values(int n, double x, double* phi) {
+  std::vector<double> P(n);
+  jacobi_values(n - 1, 1.0, 1.0, x, P.data());
+  for (int p = 0; p < n; ++p) phi[p] = (1.0 - x * x) * P[p];
+}
+
+}  // namespace spmc

@@ -1,0 +1,14 @@
+// spmc_tables.h -- host-side Gauss-type node and transform tables (Section 2.3).
+#pragma once
+
+namespace spmc {
+void jacobi_values(int m, double a, double b, double x, double* P);
+void jacobi_zeros(int n, double a, double b, double* z);
+void legendre_values(int m, double x, double* L);
+void space_nodes(int n, double* x);                               // JG(1,1), ascending
+void time_nodes(int family, int M, double* xi);                   // LGL (0) or left Radau (1) on [-1,1]
+void time_weights(int family, int M, const double* xi, double* w);
+void space_analysis(int n, double* A);                            // a_pj, [p][j]
+void time_analysis(int family, int M, double* B);                 // b_qk, [q][k]
+void phi_values(int n, double x, double* phi);                    // phi_0..phi_{n-1}
+}  // namespace spmc

@@ -61,7 +61,7 @@ class Workload:
     seed: int = 0
     n_ref: int = 80
     n_sub: int = 4
-    shell: float = 1e-4
+    shell: float = 0.0          # 0: half the outermost node's distance to the boundary
     max_steps: int = 512
     instances: List[Instance] = field(default_factory=list)
 
@@ -91,7 +91,7 @@ def w2(M: int = 65536, K: int = 8, seed: int = 0, n_space: int = 24, degree: int
        n_intervals: int = 20, h: float = 1.0) -> Workload:
     inst = Instance(t_breaks=uniform_mesh(h * n_intervals, n_intervals), degrees=np.full(n_intervals, degree),
                     f_kind=F_SIN, f_coef=(0, 0, 0, 0), ex_kind=EX_SIN, ex_beta=0.1)
-    return Workload("w2-2d-long-time", 2, n_space, TIME_LGL, M, K, seed=seed, instances=[inst])
+    return Workload("w2-2d-long-time", 2, n_space, TIME_LGL, M, K, seed=seed, n_ref=160, instances=[inst])
 
 
 def w3(M: int = 32768, K: int = 8, seed: int = 0, batch: int = 256, n_space: int = 32, param_seed: int = 1,
@@ -130,3 +130,18 @@ def w5(M: int = 16384, K: int = 8, seed: int = 0, batch: int = 128, n_space: int
 def uniform_points(n: int, dim: int, seed: int) -> np.ndarray:
     """Start points drawn uniformly in (-1,1)^dim (walk statistics, Table 1)."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, dim))
+
+
+def u0_nodal(inst: Instance, grid: np.ndarray) -> np.ndarray:
+    """Initial values at the spatial nodes (grid: (S, d) coordinates): the
+    closed form at t = 0 of the manufactured solution, or the singular profile
+    |x|^0.6 (1 - x^2) of the initial-singularity workload."""
+    if inst.u0_kind == "singular":
+        return np.prod(np.abs(grid) ** 0.6 * (1.0 - grid ** 2), axis=1)
+    if inst.ex_kind == EX_SIN:
+        return np.prod(np.sin(np.pi * grid), axis=1)
+    if inst.ex_kind == EX_COSHALF:
+        return np.prod(np.cos(0.5 * np.pi * grid), axis=1)
+    if inst.ex_kind == EX_POLY:
+        return np.prod((1.0 - grid ** 2) * (1.0 + grid), axis=1)
+    raise ValueError("instance has no closed-form initial condition")
