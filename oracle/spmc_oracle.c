@@ -157,11 +157,12 @@ static void draw_direction(orc_stream* s, int d, int64_t step_index, double* the
 
 /* Inside-ball walk (walk_mode 0): the words of one step, padded to whole
  * Philox blocks: [next-step direction | Green point direction | Green radius
- * uniform(s), a pair of words each | one word choosing the time sub-point]. */
+ * uniform(s), a pair of words each | one word choosing the time sub-point |
+ * one word for the evaluation roulette of shrunk balls]. */
 int orc_ball_words_per_step(int d) {
   int wd = orc_words_per_step(d);
   int wr = (d == 2) ? 4 : 2;
-  int w = 2 * wd + wr + 1;
+  int w = 2 * wd + wr + 2;
   return (w + 3) / 4 * 4;
 }
 
@@ -664,10 +665,20 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
     double v = orc_green_radius(d, U1, U2);
     for (int e = 0; e < d; ++e) Y[e] = X[e] + r * v * thg[e];
     double tau = t_node - ((double)m + 0.5) * sub;
+    /* A shrunk ball's term (weight w < Delta) is evaluated with probability
+     * w/Delta and then weighted Delta (unbiased Russian roulette): most of the
+     * many small steps that approach the boundary cost no evaluation. */
+    double wq = w;
+    if (r < J && w > 0.0) {
+      uint32_t rword = stream_word(&st, w0 + 2 * wd + ((d == 2) ? 4 : 2) + 1);
+      double Ur = ((double)(rword >> 8) + 0.5) * (1.0 / 16777216.0);
+      double pi = w / delta;
+      wq = (Ur < pi) ? delta : 0.0;
+    }
     if (L < cap) {
       for (int e = 0; e < d; ++e) pts[L * d + e] = Y[e];
       taus[L] = tau;
-      wts[L] = w;
+      wts[L] = wq;
     }
     L = q + 1;
     if (last) break;
@@ -690,6 +701,7 @@ double orc_walk(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node
   int L = orc_walk_points(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, ORC_WALK_CAP, x_end);
   double sum = 0.0;
   for (int i = 0; i < L && i < ORC_WALK_CAP; ++i) {
+    if (wts[i] == 0.0) continue;
     double r = ic->cu ? orc_residual(pb, ic->Mt, ic->t0, ic->h, ic->cu, ic->ct, pts + i * d, taus[i]) : 1.0;
     sum += wts[i] * r;
   }
@@ -825,6 +837,7 @@ static double walk_tangent(const orc_problem* pb, const orc_interval_ctx* ic, co
   int L = orc_walk_points(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, ORC_WALK_CAP, NULL);
   double sum = 0.0;
   for (int i = 0; i < L && i < ORC_WALK_CAP; ++i) {
+    if (wts[i] == 0.0) continue;
     double xi = (2.0 * taus[i] - ic->t0 - (ic->t0 + ic->h)) / ic->h;
     double u, dtu, mlap, ud, dtud, mlapd;
     orc_eval(pb, ic->Mt, ic->cu, ic->ct, pts + i * d, xi, &u, &dtu, &mlap);

@@ -135,6 +135,14 @@ class Plan:
                                      C.c_void_p(out.data_ptr())), self._h)
         return out
 
+    def get_nodes_into(self, instance: int, interval: int, dst: torch.Tensor, stream=None):
+        """Copy (instance, interval)'s nodal values into dst (device or pinned host tensor)."""
+        Mt = self.degrees[instance][interval]
+        assert dst.dtype == torch.float64 and dst.is_contiguous() and dst.numel() >= (Mt + 1) * self.S
+        L.check(L.lib.spmc_get_nodes(self._h, C.c_void_p(_stream_ptr(stream)), instance, interval,
+                                     C.c_void_p(dst.data_ptr())), self._h)
+        return dst
+
     def set_nodes(self, instance: int, interval: int, values: torch.Tensor, stream=None):
         v = values.contiguous()
         Mt = self.degrees[instance][interval]

@@ -90,11 +90,13 @@ template <> struct Ar<float> {
 
 // ------------------------------------------------------------------ word layout
 // Words of one step of the inside-ball walk, padded to whole Philox blocks:
-// [next-step direction wd | Green direction wd | Green radius 2 (d=2: 4) | sub-point 1]
+// [next-step direction wd | Green direction wd | Green radius 2 (d=2: 4) |
+//  sub-point 1 | evaluation roulette 1]
 __host__ __device__ constexpr int dir_words(int d) { return d == 1 ? 1 : (d == 2 ? 2 : 4 * ((d + 1) / 2)); }
 __host__ __device__ constexpr int radius_words(int d) { return d == 2 ? 4 : 2; }
-__host__ __device__ constexpr int step_words(int d) { return ((2 * dir_words(d) + radius_words(d) + 1) + 3) / 4 * 4; }
+__host__ __device__ constexpr int step_words(int d) { return ((2 * dir_words(d) + radius_words(d) + 2) + 3) / 4 * 4; }
 __host__ __device__ constexpr int gword_index(int d) { return 2 * dir_words(d) + radius_words(d); }
+__host__ __device__ constexpr int rword_index(int d) { return gword_index(d) + 1; }
 
 // fetch word w of the walk (one Philox evaluation per call)
 __device__ __forceinline__ uint32_t stream_word(const WalkStream& s, uint32_t w) {

@@ -242,140 +242,68 @@ __device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, c
   st.last[s] = last;
 }
 
-// Per-cohort constants, kept in shared memory.  A cohort is one chunk of the
-// samples of one sampled node (time node ti, spatial node j).
+// Persistent sweep.  A cohort is a tile of JT spatial nodes of one sampled time
+// node times one chunk of CC samples per node: W = JT CC walks that share the
+// time node's slices.  Each block takes cohorts from a global counter and runs
+// them pass by pass: a pass handles the window of n_sub sub-points
+// [m0, m0 + n_sub) whose slices are staged in shared memory; every walk whose
+// pending evaluation lies in the window is evaluated and keeps stepping while
+// its next evaluation stays in the window.  Walk state lives in a block-private
+// global region (L2 resident); the pending sub-points and the active and ready
+// lists live in shared memory.  When every walk of the cohort has ended, the
+// block sums each node's walks in sample order (FP64) into the node's chunk sum.
 template <int D, typename R>
-struct Cohort {
-  int id;            // global cohort index, -1 when the slot is empty
-  long long ti;
-  int j, chunk;
-  int m0;            // first sub-point of the cohort's current window
-  int fresh;         // started during this pass: its window stays at 0
-  int npass;         // passes spent on the cohort (bounded by 2 Ktot + 8)
-  int Ktot;
-  int nsl;           // slices staged for the window
-  long long slice_base;
-  R xj[D];
-  R J, delta, sub;
-  uint32_t node, tag;
-  long long sample0;
+struct StateRegion {
+  // block-private global arrays of W entries each
+  R* X[D];
+  R *f, *w, *r, *S;
+  int *k, *q, *last;
 };
 
-// Persistent sweep.  Each block keeps NC cohorts in flight.  A pass handles, for
-// every cohort, the window of n_sub sub-points [m0, m0 + n_sub) whose slices are
-// staged in shared memory: every sample whose pending evaluation lies in its
-// cohort's window is evaluated and keeps stepping while its next evaluation
-// stays in the window.  When all walks of a cohort have ended, the block sums
-// their Q in FP64 (fixed order), writes the cohort's partial sum and takes the
-// next cohort from a global counter.  Cohorts at different stages share the
-// block, so the long tail of surviving walks of one cohort overlaps the start
-// of others.
 template <int D, int NMAX, typename R>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) sweep_kernel(SweepArgs a, int NC, int CC, long long n_cohorts,
-                                                    int* __restrict__ work_counter) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1)
+sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__ work_counter,
+             void* __restrict__ state_base, long long state_stride) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int S = a.S, n = a.n;
   const int G = a.n_sub;
   const long long slst = a.sl_stride;
   const int half = a.half;
-  const int NS = NC * CC;
-  R* sSl = reinterpret_cast<R*>(smraw);                       // [NC][G][slst]
-  unsigned char* p = smraw + ((NC * G * slst * sizeof(R) + 15) / 16) * 16;
-  WalkState<D, R> st;
-#pragma unroll
-  for (int e = 0; e < D; ++e) { st.X[e] = reinterpret_cast<R*>(p); p += NS * sizeof(R); }
-  st.f = reinterpret_cast<R*>(p); p += NS * sizeof(R);
-  st.w = reinterpret_cast<R*>(p); p += NS * sizeof(R);
-  st.r = reinterpret_cast<R*>(p); p += NS * sizeof(R);
-  st.S = reinterpret_cast<R*>(p); p += NS * sizeof(R);
-  st.k = reinterpret_cast<int*>(p); p += NS * sizeof(int);
-  st.q = reinterpret_cast<int*>(p); p += NS * sizeof(int);
-  st.mnext = reinterpret_cast<int*>(p); p += NS * sizeof(int);
-  st.last = reinterpret_cast<int*>(p); p += NS * sizeof(int);
-  int* ready = reinterpret_cast<int*>(p); p += NS * sizeof(int);
-  Cohort<D, R>* coh = reinterpret_cast<Cohort<D, R>*>(p); p += ((NC * sizeof(Cohort<D, R>) + 15) / 16) * 16;
-  int* cinfo = reinterpret_cast<int*>(p); p += 3 * NC * sizeof(int);   // [ready count | min pending | alive]
-  double* sT = reinterpret_cast<double*>(p);                          // [NC][G][2] time factors
+  const int W = JT * CC;
+  const int n_jt = (S + JT - 1) / JT;
+  R* sSl = reinterpret_cast<R*>(smraw);                       // [G][slst]
+  unsigned char* p = smraw + ((G * slst * sizeof(R) + 15) / 16) * 16;
+  int* mnext = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  int* act = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  int* ready = reinterpret_cast<int*>(p); p += W * sizeof(int);
   __shared__ int red[64];
   __shared__ double dred[32];
-  __shared__ int s_next;
+  __shared__ int s_next, s_nact;
+  __shared__ double s_Tt[16], s_dTt[16];
+
+  // block-private walk state (structure of arrays)
+  unsigned char* gb = reinterpret_cast<unsigned char*>(state_base) + (long long)blockIdx.x * state_stride;
+  WalkState<D, R> st;
+#pragma unroll
+  for (int e = 0; e < D; ++e) { st.X[e] = reinterpret_cast<R*>(gb); gb += W * sizeof(R); }
+  st.f = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.w = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.r = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.S = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.k = reinterpret_cast<int*>(gb); gb += W * sizeof(int);
+  st.q = reinterpret_cast<int*>(gb); gb += W * sizeof(int);
+  st.last = reinterpret_cast<int*>(gb); gb += W * sizeof(int);
+  st.mnext = mnext;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const InstanceParams* ipt = a.ip;
   const R kappa = (R)a.kappa;
   const R shell = (R)a.shell;
   const R* slices = reinterpret_cast<const R*>(a.slices);
   unsigned long long capped = 0, points = 0;
   double dummy_acc = 0.0;
 
-  // take a cohort for slot c and start its walks
-  auto start_cohort = [&](int c) {
-    if (threadIdx.x == 0) s_next = atomicAdd(work_counter, 1);
-    __syncthreads();
-    const int id = s_next;
-    __syncthreads();
-    if (id >= n_cohorts) {
-      if (threadIdx.x == 0) coh[c].id = -1;
-      for (int s = threadIdx.x; s < CC; s += blockDim.x) st.mnext[c * CC + s] = -1;
-      __syncthreads();
-      return;
-    }
-    long long b = id;
-    const int chunk = (int)(b % a.n_chunks);
-    b /= a.n_chunks;
-    const int j = (int)(b % S);
-    const long long ti = b / S;
-    const TimeNode node = a.tn[ti];
-    Cohort<D, R> ch;
-    ch.id = id; ch.ti = ti; ch.j = j; ch.chunk = chunk; ch.m0 = 0; ch.fresh = 1; ch.npass = 0;
-    {
-      int jj = j;
-#pragma unroll
-      for (int e = 0; e < D; ++e) { ch.xj[e] = (R)a.xnodes[jj % n]; jj /= n; }
-    }
-    const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
-    ch.delta = Ar<R>::div(sdur, (R)node.nstar);
-    ch.J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), ch.delta));
-    ch.sub = Ar<R>::div(ch.delta, (R)G);
-    ch.Ktot = G * node.nstar;
-    ch.slice_base = node.slice_base;
-    ch.node = (uint32_t)(node.ell * S + j);
-    ch.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
-             (uint32_t)(a.iteration & 0x3ff);
-    ch.sample0 = (long long)chunk * CC;
-    ch.nsl = 0;
-    if (threadIdx.x == 0) coh[c] = ch;
-    WalkStream ws;
-    ws.k0 = a.k0; ws.k1 = a.k1; ws.node = ch.node; ws.tag = ch.tag;
-    for (int s = threadIdx.x; s < CC; s += blockDim.x) {
-      const int g = c * CC + s;
-#pragma unroll
-      for (int e = 0; e < D; ++e) st.X[e][g] = ch.xj[e];
-      st.f[g] = R(0); st.S[g] = R(0); st.k[g] = 0; st.q[g] = 0;
-      if (ch.sample0 + s >= a.M) { st.mnext[g] = -1; continue; }
-      ws.sample = (uint32_t)(ch.sample0 + s);
-      prepare_step<D, R>(st, g, ws, ch.J, ch.delta, ch.sub, ch.Ktot, G, a.gbits, shell, kappa, a.max_steps,
-                         dummy_acc, capped);
-    }
-    __syncthreads();
-  };
-
-  for (int c = 0; c < NC; ++c) start_cohort(c);
-
-  while (true) {
-    // per-cohort window statistics
-    if (threadIdx.x < 3 * NC) cinfo[threadIdx.x] = (threadIdx.x / NC == 1) ? 0x7fffffff : 0;
-    __syncthreads();
-    int cnt = 0;
-    for (int s = threadIdx.x; s < NS; s += blockDim.x) {
-      const int mv = st.mnext[s];
-      if (mv < 0) continue;
-      const int c = s / CC;
-      const int m0 = coh[c].m0;
-      atomicAdd(&cinfo[2 * NC + c], 1);
-      if (mv >= m0 && mv < m0 + G) ++cnt;
-      else if (mv >= m0 + G) atomicMin(&cinfo[NC + c], mv);
-    }
+  // block-wide exclusive scan of one count per thread; returns the total
+  auto block_scan = [&](int cnt, int& base) -> int {
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -389,142 +317,193 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1) sweep_kernel(Sw
       if (wv < warp) wbase += red[wv];
       total += red[wv];
     }
-    int pos = wbase + incl - cnt;
-    for (int s = threadIdx.x; s < NS; s += blockDim.x) {
-      const int mv = st.mnext[s];
-      const int m0 = coh[s / CC].m0;
-      if (mv >= m0 && mv < m0 + G) ready[pos++] = s;
-    }
-    // finished cohorts: reduce, write, restart; empty windows: jump ahead
-    bool any_active = false;
-    for (int c = 0; c < NC; ++c) {
-      const int id = coh[c].id;
-      if (id < 0) continue;
-      if (cinfo[2 * NC + c] == 0) {
-        // all walks of the cohort have ended: FP64 sum of their Q in slot order
-        double t = 0.0;
-        for (int s = threadIdx.x; s < CC; s += blockDim.x) t += (double)st.S[c * CC + s];
+    __syncthreads();
+    base = wbase + incl - cnt;
+    return total;
+  };
+
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(work_counter, 1);
+    __syncthreads();
+    const long long id = s_next;
+    __syncthreads();
+    if (id >= n_cohorts) break;
+    long long b = id;
+    const int chunk = (int)(b % a.n_chunks);
+    b /= a.n_chunks;
+    const int jt = (int)(b % n_jt);
+    const long long ti = b / n_jt;
+    const TimeNode node = a.tn[ti];
+    const InstanceParams ip = a.ip[node.inst];
+    const int j0 = jt * JT;
+    const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
+    const R delta = Ar<R>::div(sdur, (R)node.nstar);
+    const R J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
+    const R sub = Ar<R>::div(delta, (R)G);
+    const int Ktot = G * node.nstar;
+    const uint32_t tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+                         (uint32_t)(a.iteration & 0x3ff);
+    const long long sample0 = (long long)chunk * CC;
+    WalkStream ws;
+    ws.k0 = a.k0; ws.k1 = a.k1; ws.tag = tag;
+
+    // start the cohort's walks
+    int cnt = 0;
+    for (int wk = threadIdx.x; wk < W; wk += blockDim.x) {
+      const int jj = wk / CC, s = wk - jj * CC;
+      const int j = j0 + jj;
+      st.S[wk] = R(0);
+      if (j >= S || sample0 + s >= a.M) { mnext[wk] = -1; continue; }
+      int jr = j;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) dred[warp] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double tt = 0.0;
-          for (int wv = 0; wv < nwarps; ++wv) tt += dred[wv];
-          a.partial[(coh[c].ti * S + coh[c].j) * a.n_chunks + coh[c].chunk] = tt;
-        }
-        __syncthreads();
-        start_cohort(c);
-        // the new cohort's walks are pending at window 0; they join the next pass
-        if (coh[c].id >= 0) any_active = true;
-      } else {
-        any_active = true;
-      }
-    }
-    if (!any_active) break;
-    // pass budget: a cohort's pending sub-points never decrease and stay below
-    // Ktot, and its window moves forward every pass, so 2 Ktot + 8 passes always
-    // suffice; a cohort over budget (inconsistent inputs) is reported and its
-    // walks are ended, so the kernel always terminates.
-    for (int c = 0; c < NC; ++c) {
-      if (coh[c].id < 0) continue;
-      if (coh[c].npass > 2 * coh[c].Ktot + 8) {
-        if (threadIdx.x == 0) atomicOr(a.status, 2);
-        for (int s = threadIdx.x; s < CC; s += blockDim.x) st.mnext[c * CC + s] = -1;
-        __syncthreads();
-        for (int i = threadIdx.x; i < total; i += blockDim.x) if (ready[i] / CC == c) ready[i] = -1;
-      }
+      for (int e = 0; e < D; ++e) { st.X[e][wk] = (R)a.xnodes[jr % n]; jr /= n; }
+      st.f[wk] = R(0); st.k[wk] = 0; st.q[wk] = 0;
+      ws.node = (uint32_t)(node.ell * S + j);
+      ws.sample = (uint32_t)(sample0 + s);
+      prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps, dummy_acc, capped);
+      if (mnext[wk] >= 0) ++cnt;
     }
     __syncthreads();
-    if (threadIdx.x < NC && coh[threadIdx.x].id >= 0) coh[threadIdx.x].npass += 1;
-    if (total == 0) {
-      // no cohort has work in its window: move every window to its next pending sub-point
+    {
+      int base;
+      const int tot = block_scan(cnt, base);
+      for (int wk = threadIdx.x; wk < W; wk += blockDim.x)
+        if (mnext[wk] >= 0) act[base++] = wk;
+      if (threadIdx.x == 0) s_nact = tot;
       __syncthreads();
-      if (threadIdx.x < NC && coh[threadIdx.x].id >= 0) {
-        if (coh[threadIdx.x].fresh) coh[threadIdx.x].fresh = 0;
-        else if (cinfo[2 * NC + threadIdx.x] > 0 && cinfo[NC + threadIdx.x] != 0x7fffffff)
-          coh[threadIdx.x].m0 = cinfo[NC + threadIdx.x];
+    }
+    int m0 = 0;
+    const int max_passes = 2 * Ktot + 8;
+    int passes = 0;
+    while (s_nact > 0) {
+      const int nact = s_nact;
+      if (++passes > max_passes) {  // cannot happen for consistent inputs: report and end the walks
+        if (threadIdx.x == 0) { atomicOr(a.status, 2); s_nact = 0; }
+        for (int i = threadIdx.x; i < nact; i += blockDim.x) mnext[act[i]] = -1;
+        __syncthreads();
+        break;
+      }
+      // ready list: active walks pending in the window; smallest pending beyond it
+      int rc = 0, mn = 0x7fffffff;
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) {
+        const int mv = mnext[act[i]];
+        if (mv < m0 + G) ++rc; else mn = min(mn, mv);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      if (lane == 0) red[32 + warp] = mn;
+      int rbase;
+      const int nready = block_scan(rc, rbase);
+      int gmin = 0x7fffffff;
+      for (int wv = 0; wv < nwarps; ++wv) gmin = min(gmin, red[32 + wv]);
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) {
+        const int wk = act[i];
+        if (mnext[wk] < m0 + G) ready[rbase++] = wk;
+      }
+      if (nready == 0) {
+        __syncthreads();
+        m0 = gmin;
+        continue;
+      }
+      // stage the window's slices (16-byte vector copies) and time factors
+      {
+        const int nsl = min(G, Ktot - m0);
+        const R* src = slices + (node.slice_base + m0) * slst;
+        const int vec = (int)(16 / sizeof(R));
+        const long long nv = (long long)nsl * slst / vec;
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(sSl);
+        for (long long i = threadIdx.x; i < nv; i += blockDim.x) d4[i] = s4[i];
+        if (threadIdx.x < nsl) {
+          SliceInfo si = a.sinfo[node.slice_base + m0 + threadIdx.x];
+          s_Tt[threadIdx.x] = si.Tt; s_dTt[threadIdx.x] = si.dTt;
+        }
       }
       __syncthreads();
-      continue;
-    }
-    // stage every active cohort's window of slices (16-byte vector copies) and time factors
-    for (int c = 0; c < NC; ++c) {
-      if (coh[c].id < 0) continue;
-      const int m0 = coh[c].m0;
-      const int nsl = min(G, coh[c].Ktot - m0);
-      const R* src = slices + (coh[c].slice_base + m0) * slst;
-      const int vec = (int)(16 / sizeof(R));
-      const long long nv = (long long)nsl * slst / vec;
-      const float4* s4 = reinterpret_cast<const float4*>(src);
-      float4* d4 = reinterpret_cast<float4*>(sSl + (long long)c * G * slst);
-      for (long long i = threadIdx.x; i < nv; i += blockDim.x) d4[i] = s4[i];
-      if (threadIdx.x < nsl) {
-        SliceInfo si = a.sinfo[coh[c].slice_base + m0 + threadIdx.x];
-        sT[(c * G + threadIdx.x) * 2] = si.Tt;
-        sT[(c * G + threadIdx.x) * 2 + 1] = si.dTt;
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int s = ready[i];
-      if (s < 0) continue;
-      const int c = s / CC;
-      const Cohort<D, R>& ch = coh[c];
-      const InstanceParams ip = ipt[a.tn[ch.ti].inst];
-      WalkStream ws;
-      ws.k0 = a.k0; ws.k1 = a.k1; ws.node = ch.node; ws.tag = ch.tag;
-      ws.sample = (uint32_t)(ch.sample0 + (s - c * CC));
-      const int m0 = ch.m0;
-      int mv = st.mnext[s];
-      while (mv >= m0 && mv < m0 + G) {
-        const int q = st.q[s];
-        constexpr int W = step_words(D);
-        const uint32_t w0 = (uint32_t)q * W;
-        // Green-function point of the pending ball
-        R thg[D], Y[D];
-        direction<D, R>(ws, w0 + dir_words(D), thg);
-        const uint32_t wr = w0 + 2 * dir_words(D);
-        Philox4 rb = ws.block(wr >> 2);
-        R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
-        R U2 = R(0);
-        if (D == 2) U2 = U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]);
-        const R v = green_radius<D, R>(U1, U2);
-        const R r = st.r[s];
-        const R rv = Ar<R>::mul(r, v);
+      for (int i = threadIdx.x; i < nready; i += blockDim.x) {
+        const int wk = ready[i];
+        const int jj = wk / CC;
+        ws.node = (uint32_t)(node.ell * S + j0 + jj);
+        ws.sample = (uint32_t)(sample0 + (wk - jj * CC));
+        int mv = mnext[wk];
+        while (mv >= m0 && mv < m0 + G) {
+          const int q = st.q[wk];
+          constexpr int WS = step_words(D);
+          const uint32_t w0 = (uint32_t)q * WS;
+          // Green-function point of the pending ball
+          R thg[D], Y[D];
+          direction<D, R>(ws, w0 + dir_words(D), thg);
+          const uint32_t wr = w0 + 2 * dir_words(D);
+          Philox4 rb = ws.block(wr >> 2);
+          R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
+          R U2 = R(0);
+          if (D == 2) U2 = U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]);
+          const R v = green_radius<D, R>(U1, U2);
+          const R r = st.r[wk];
+          const R rv = Ar<R>::mul(r, v);
 #pragma unroll
-        for (int e = 0; e < D; ++e) Y[e] = Ar<R>::add(st.X[e][s], Ar<R>::mul(rv, thg[e]));
-        const R w = st.w[s];
-        R Ssum = st.S[s];
-        if (w > R(0)) {
-          const int b = mv - m0;
-          const R* sc = sSl + ((long long)c * G + b) * slst;
-          R res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)sT[(c * G + b) * 2],
-                                          (R)sT[(c * G + b) * 2 + 1]);
-          Ssum += w * res;
-          ++points;
+          for (int e = 0; e < D; ++e) Y[e] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(rv, thg[e]));
+          // a shrunk ball's term is evaluated with probability w / Delta and
+          // then weighted Delta (unbiased Russian roulette)
+          R w = st.w[wk];
+          if (r < J && w > R(0)) {
+            const uint32_t rw = stream_word(ws, w0 + rword_index(D));
+            const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
+            w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
+          }
+          if (w > R(0)) {
+            const int bsl = mv - m0;
+            const R* sc = sSl + bsl * slst;
+            R res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)s_Tt[bsl], (R)s_dTt[bsl]);
+            st.S[wk] += w * res;
+            ++points;
+          }
+          if (st.last[wk]) { mnext[wk] = -1; break; }
+          // step to the sphere of the ball
+          R th[D];
+          direction<D, R>(ws, w0, th);
+#pragma unroll
+          for (int e = 0; e < D; ++e) st.X[e][wk] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(r, th[e]));
+          st.q[wk] = q + 1;
+          prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps,
+                             dummy_acc, capped);
+          mv = mnext[wk];
         }
-        st.S[s] = Ssum;
-        if (st.last[s]) { st.mnext[s] = -1; break; }
-        // step to the sphere of the ball
-        R th[D];
-        direction<D, R>(ws, w0, th);
-#pragma unroll
-        for (int e = 0; e < D; ++e) st.X[e][s] = Ar<R>::add(st.X[e][s], Ar<R>::mul(r, th[e]));
-        st.q[s] = q + 1;
-        prepare_step<D, R>(st, s, ws, ch.J, ch.delta, ch.sub, ch.Ktot, G, a.gbits, shell, kappa, a.max_steps,
-                           dummy_acc, capped);
-        mv = st.mnext[s];
       }
+      __syncthreads();
+      // compact the active list
+      int kc = 0;
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) kc += (mnext[act[i]] >= 0);
+      int kbase;
+      const int nkeep = block_scan(kc, kbase);
+      // stable compaction through the ready buffer
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) {
+        const int wk = act[i];
+        if (mnext[wk] >= 0) ready[kbase++] = wk;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < nkeep; i += blockDim.x) act[i] = ready[i];
+      if (threadIdx.x == 0) s_nact = nkeep;
+      __syncthreads();
+      m0 += G;
     }
-    __syncthreads();
-    // advance every active cohort's window (a cohort started in this pass has not
-    // been processed yet and keeps window 0)
-    if (threadIdx.x < NC && coh[threadIdx.x].id >= 0) {
-      if (coh[threadIdx.x].fresh) coh[threadIdx.x].fresh = 0;
-      else coh[threadIdx.x].m0 += G;
+    // every walk of the cohort has ended: each node's chunk sum in sample order
+    for (int jj = 0; jj < JT; ++jj) {
+      const int j = j0 + jj;
+      if (j >= S) break;
+      double t = 0.0;
+      for (int s = threadIdx.x; s < CC; s += blockDim.x) t += (double)st.S[jj * CC + s];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) dred[warp] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tt = 0.0;
+        for (int wv = 0; wv < nwarps; ++wv) tt += dred[wv];
+        a.partial[(ti * S + j) * a.n_chunks + chunk] = tt;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
 #pragma unroll

@@ -51,9 +51,11 @@ struct spmc_plan_s {
   spmc_plan_desc d{};
   std::string err;
   int S = 1;
-  int chunk = 512, threads = 256;   // chunk = samples per cohort
-  int NC = 2;                        // cohorts in flight per block
+  int chunk = 512, threads = 256;   // chunk = samples per node in a cohort
+  int JT = 12;                       // spatial nodes per cohort
   int* d_work = nullptr;             // persistent-kernel work counter
+  void* d_state = nullptr;           // block-private walk state regions
+  size_t state_bytes = 0;
   std::vector<HostProblem> probs;
   bool built = false;
   std::vector<double> xnodes;
@@ -120,12 +122,13 @@ spmc_status upload(spmc_plan_t plan, T** dptr, const std::vector<T>& v) {
   return SPMC_OK;
 }
 
-size_t sweep_smem(int D, int G, long long sl_stride, int NC, int CC, size_t rsz, size_t cohort_size) {
-  size_t base = ((NC * G * sl_stride * rsz + 15) / 16) * 16;
-  size_t NS = (size_t)NC * CC;
-  size_t st = NS * ((D + 4) * rsz + 5 * sizeof(int));
-  size_t co = ((NC * cohort_size + 15) / 16) * 16;
-  return base + st + co + 3 * NC * sizeof(int) + (size_t)NC * G * 2 * sizeof(double) + 16;
+size_t sweep_smem(int G, long long sl_stride, int W, size_t rsz) {
+  return ((G * sl_stride * rsz + 15) / 16) * 16 + 3 * (size_t)W * sizeof(int);
+}
+
+size_t state_stride_bytes(int D, int W, size_t rsz) {
+  size_t b = (size_t)W * ((D + 4) * rsz + 3 * sizeof(int));
+  return (b + 255) / 256 * 256;
 }
 
 // Slice geometry: rows padded to the template width of the sweep (16-byte
@@ -300,9 +303,12 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
   a.M = d.M;
   a.sl_stride = plan->sl_stride;
   a.half = plan->half;
-  const long long n_cohorts = (long long)rd.tn.size() * plan->S * a.n_chunks;
+  const int JT = std::min(plan->JT, plan->S);
+  const int W = JT * plan->chunk;
+  const long long n_jt = (plan->S + JT - 1) / JT;
+  const long long n_cohorts = (long long)rd.tn.size() * n_jt * a.n_chunks;
   if (n_cohorts <= 0) return SPMC_OK;
-  size_t smem = sweep_smem(D, d.n_sub, plan->sl_stride, plan->NC, plan->chunk, sizeof(R), sizeof(Cohort<D, R>));
+  size_t smem = sweep_smem(d.n_sub, plan->sl_stride, W, sizeof(R));
   auto kern = sweep_kernel<D, NMAX, R>;
   SPMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, occ = 0;
@@ -311,6 +317,14 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
   SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, plan->threads, smem));
   if (occ < 1) return fail(plan, SPMC_ERR_UNSUPPORTED, "sweep configuration does not fit on an SM");
   long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
+  const size_t stride = state_stride_bytes(D, W, sizeof(R));
+  if (plan->state_bytes < stride * grid) {
+    cudaFree(plan->d_state);
+    plan->d_state = nullptr;
+    plan->state_bytes = 0;
+    SPMC_CUDA(cudaMalloc(&plan->d_state, stride * grid));
+    plan->state_bytes = stride * grid;
+  }
   SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (plan->timing) {
@@ -318,7 +332,8 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
     else { SPMC_CUDA(cudaEventCreate(&ev.first)); SPMC_CUDA(cudaEventCreate(&ev.second)); }
     SPMC_CUDA(cudaEventRecord(ev.first, stream));
   }
-  kern<<<(unsigned)grid, plan->threads, smem, stream>>>(a, plan->NC, plan->chunk, n_cohorts, plan->d_work);
+  kern<<<(unsigned)grid, plan->threads, smem, stream>>>(a, JT, plan->chunk, n_cohorts, plan->d_work, plan->d_state,
+                                                         (long long)stride);
   SPMC_CUDA(cudaGetLastError());
   if (plan->timing) {
     SPMC_CUDA(cudaEventRecord(ev.second, stream));
@@ -467,7 +482,7 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   for (int e = 0; e < d.dim; ++e) plan->S *= d.n_space;
   plan->probs.assign(d.batch, HostProblem());
   plan->chunk = (int)std::min<long long>(d.precision == SPMC_FP64 ? 256 : 512, ((d.M + 31) / 32) * 32);
-  plan->NC = (d.dim == 1) ? 4 : 2;
+  plan->JT = (d.precision == SPMC_FP64 ? 4096 : 6144) / plan->chunk;
   slice_geometry(plan);
   plan->threads = 256;
   // tables
@@ -695,6 +710,7 @@ void spmc_destroy(spmc_plan_t plan) {
   cudaFree(plan->d_sinfo); cudaFree(plan->d_partial); cudaFree(plan->d_counters); cudaFree(plan->d_maxeps);
   cudaFree(plan->d_status);
   cudaFree(plan->d_work);
+  cudaFree(plan->d_state);
   delete plan;
 }
 
