@@ -144,6 +144,28 @@ spmc_status spmc_get_nodes(spmc_plan_t plan, void* cuda_stream, int instance, in
  * iterate for checking.  A later spmc_iterate on that interval continues from it. */
 spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, const double* src);
 
+/* One residual iteration on `interval` (like spmc_iterate with n_iter = 1) that
+ * allocates nothing.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory at the point of the call, e.g.
+ * code running between the set-up of a real-time loop and its teardown, or a
+ * host thread inside a region where cudaMalloc would synchronise the device or
+ * is forbidden by the surrounding allocator policy.  The sweep kernel's scratch
+ * (walk state, work counter, per-node chunk sums) lives in a file-scope device
+ * array of SPMC_STATIC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
+ * holds until exit; nodal values, coefficients and slices stay in the plan,
+ * which must already be built (spmc_begin_interval on it has run).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) for the current device; make that first call before
+ *    any stream capture.
+ *  - Every call shares the array and leaves its last contents there; the call
+ *    clears what must start at zero.  Calls that overlap on the GPU (other
+ *    streams, other plans, other host threads) race on it: serialise them.
+ *  - A problem whose chunk sums and minimal walk state do not fit in the array
+ *    is rejected with SPMC_ERR_UNSUPPORTED and a message naming the limit.
+ * max_eps_host receives the largest |eps| (the stream is synchronised). */
+#define SPMC_STATIC_SCRATCH_BYTES (16u << 20)
+spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interval, double* max_eps_host);
+
 /* Reverse-mode gradient of L(u(T)) for every instance: given dL/du at the
  * spatial nodes at t = T (device, batch x n_space^d doubles), returns
  * dL/d(f_scale) (device, batch doubles) and dL/d(u0 coefficients) (device,

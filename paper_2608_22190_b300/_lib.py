@@ -57,6 +57,7 @@ _SIGNATURES = {
     "spmc_iterate": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "spmc_get_nodes": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "spmc_set_nodes": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "spmc_iterate_static": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spmc_set_timing": (C.c_int, [_PLAN, C.c_int]),
     "spmc_space_nodes": (C.c_int, [_PLAN, C.POINTER(C.c_double)]),

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -458,6 +459,99 @@ void sync_counters(spmc_plan_t plan) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ static scratch
+// Device scratch of spmc_iterate_static: one array per GPU, for callers that
+// cannot allocate at the call.  Host code must not use g_static_scratch as an
+// address (it is a host-side stand-in); its device address is looked up once per
+// device with cudaGetSymbolAddress, with that device current.
+static __device__ __align__(256) unsigned char g_static_scratch[SPMC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+spmc_status static_scratch(spmc_plan_t plan, void** out) {
+  int dev = -1;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(plan, SPMC_ERR_UNSUPPORTED, "device index beyond 63");
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      plan->err = std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e);
+      return SPMC_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return SPMC_OK;
+}
+
+// The sweep of one iteration with its scratch in the static array: one cohort of
+// one node x chunk per block, as many resident blocks as the array holds.
+template <int D, int NMAX, typename R>
+spmc_status launch_sweep_static(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval,
+                                int iteration, unsigned char* scratch, double* partial, size_t partial_bytes) {
+  const spmc_plan_desc& d = plan->d;
+  SweepArgs a;
+  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
+  a.partial = partial; a.counters = plan->d_counters; a.status = plan->d_status;
+  a.n = d.n_space; a.S = plan->S;
+  a.chunk = plan->chunk;
+  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
+  a.n_sub = d.n_sub;
+  int gb = 0;
+  while ((1 << gb) < d.n_sub) ++gb;
+  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
+  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
+  a.interval = interval; a.iteration = iteration;
+  a.M = d.M;
+  a.sl_stride = plan->sl_stride;
+  a.half = plan->half;
+  const int JT = 1;
+  const int W = plan->chunk;
+  const long long n_cohorts = (long long)rd.tn.size() * plan->S * a.n_chunks;
+  if (n_cohorts <= 0) return SPMC_OK;
+  size_t smem = sweep_smem(d.n_sub, plan->sl_stride, W, sizeof(R));
+  auto kern = sweep_kernel<D, NMAX, R>;
+  SPMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, plan->threads, smem));
+  if (occ < 1) return fail(plan, SPMC_ERR_UNSUPPORTED, "sweep configuration does not fit on an SM");
+  const size_t stride = state_stride_bytes(D, W, sizeof(R));
+  const size_t head = 256 + partial_bytes;                    // counter, then chunk sums, then walk state
+  const long long fit = (long long)((SPMC_STATIC_SCRATCH_BYTES - head) / stride);
+  long long grid = std::min<long long>(n_cohorts, std::min<long long>((long long)sms * occ, fit));
+  if (grid < 1) return fail(plan, SPMC_ERR_UNSUPPORTED, "static scratch too small for one block's walk state");
+  int* work = reinterpret_cast<int*>(scratch);
+  SPMC_CUDA(cudaMemsetAsync(work, 0, sizeof(int), stream));
+  kern<<<(unsigned)grid, plan->threads, smem, stream>>>(a, JT, plan->chunk, n_cohorts, work, scratch + head,
+                                                         (long long)stride);
+  SPMC_CUDA(cudaGetLastError());
+  return SPMC_OK;
+}
+
+template <typename R>
+spmc_status dispatch_sweep_static(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval,
+                                  int iteration, unsigned char* scratch, double* partial, size_t pb) {
+  const int n = plan->d.n_space;
+  if (plan->d.dim == 1) return launch_sweep_static<1, 32, R>(plan, stream, rd, interval, iteration, scratch, partial, pb);
+  if (plan->d.dim == 2) {
+    if (n <= 8) return launch_sweep_static<2, 8, R>(plan, stream, rd, interval, iteration, scratch, partial, pb);
+    if (n <= 16) return launch_sweep_static<2, 16, R>(plan, stream, rd, interval, iteration, scratch, partial, pb);
+    if (n <= 24) return launch_sweep_static<2, 24, R>(plan, stream, rd, interval, iteration, scratch, partial, pb);
+    return launch_sweep_static<2, 32, R>(plan, stream, rd, interval, iteration, scratch, partial, pb);
+  }
+  return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
+}
+
+}  // namespace
+
 // =================================================================== C-ABI
 extern "C" {
 
@@ -667,6 +761,81 @@ spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, in
   size_t cnt = (size_t)(P.deg[interval] + 1) * plan->S;
   SPMC_CUDA(cudaMemcpyAsync(plan->d_U + plan->int_off[instance][interval], src, sizeof(double) * cnt,
                             cudaMemcpyDefault, (cudaStream_t)cuda_stream));
+  return SPMC_OK;
+}
+
+spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interval, double* max_eps_host) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built || plan->params_dirty)
+    return fail(plan, SPMC_ERR_INVALID, "spmc_iterate_static needs a built plan: call spmc_begin_interval first");
+  if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  Round& rd = plan->rounds[interval];
+  const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
+  const int n_chunks = (int)((plan->d.M + plan->chunk - 1) / plan->chunk);
+  const long long nn = (long long)rd.tn.size() * S;
+  const size_t partial_bytes = ((size_t)nn * n_chunks * sizeof(double) + 255) / 256 * 256;
+  if (partial_bytes + 256 >= SPMC_STATIC_SCRATCH_BYTES)
+    return fail(plan, SPMC_ERR_UNSUPPORTED,
+                "spmc_iterate_static: the chunk sums of this problem exceed the 16 MiB static scratch");
+  void* base = nullptr;
+  spmc_status st = static_scratch(plan, &base);
+  if (st != SPMC_OK) return st;
+  unsigned char* scratch = reinterpret_cast<unsigned char*>(base);
+  double* partial = reinterpret_cast<double*>(scratch + 256);
+  const int iteration = rd.iteration + 1;
+  if (!rd.ii.empty()) {
+    int maxT = 0;
+    for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
+    size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
+    if (D == 1) {
+      SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
+                                                                            plan->d_coef, n);
+    } else {
+      SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
+                                                                            plan->d_coef, n);
+    }
+    SPMC_CUDA(cudaGetLastError());
+    const bool fp64 = plan->d.precision == SPMC_FP64;
+    if (rd.n_slices > 0) {
+      if (D == 1) {
+        if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+        else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      } else {
+        if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+        else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      }
+      SPMC_CUDA(cudaGetLastError());
+    }
+    st = fp64 ? dispatch_sweep_static<double>(plan, stream, rd, interval, iteration, scratch, partial, partial_bytes)
+              : dispatch_sweep_static<float>(plan, stream, rd, interval, iteration, scratch, partial, partial_bytes);
+    if (st != SPMC_OK) return st;
+    SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, stream));
+    if (nn > 0) {
+      update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(rd.d_tn, partial, plan->d_U, nullptr,
+                                                                      plan->d_maxeps, plan->d_status, nn, S,
+                                                                      n_chunks, 1.0 / (double)plan->d.M);
+      SPMC_CUDA(cudaGetLastError());
+    }
+  }
+  rd.iteration = iteration;
+  // status and max |eps| through fixed host buffers (no allocation)
+  int hs = 0;
+  SPMC_CUDA(cudaMemcpyAsync(&hs, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  double mx = 0.0;
+  unsigned long long bits[64];
+  for (int b0 = 0; b0 < plan->d.batch; b0 += 64) {
+    const int cnt = std::min(64, plan->d.batch - b0);
+    SPMC_CUDA(cudaMemcpyAsync(bits, plan->d_maxeps + b0, sizeof(unsigned long long) * cnt, cudaMemcpyDeviceToHost,
+                              stream));
+    SPMC_CUDA(cudaStreamSynchronize(stream));
+    for (int i = 0; i < cnt; ++i) { double v; std::memcpy(&v, &bits[i], sizeof v); mx = std::max(mx, v); }
+  }
+  if (hs & 1) return fail(plan, SPMC_ERR_NONFINITE, "a non-finite eps was produced");
+  if (hs & 2) return fail(plan, SPMC_ERR_TIMEOUT, "a sweep block exceeded its pass budget");
+  if (max_eps_host) *max_eps_host = mx;
   return SPMC_OK;
 }
 
