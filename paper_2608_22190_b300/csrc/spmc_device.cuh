@@ -278,14 +278,33 @@ __device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int 
       R phx = omx * P, psx = jac_lam<R>(p1) * P;
       const R* c = sC + p1 * NMAX;     // rows padded to NMAX entries
       const R* hh = sH + p1 * NMAX;
-      R a1 = R(0), a2 = R(0), a3 = R(0);
+      // rows are 16-byte aligned and padded to NMAX: vector loads, two partial
+      // sums per quantity (independent FMA chains)
+      R a1 = R(0), a2 = R(0), a3 = R(0), b1 = R(0), b2 = R(0), b3 = R(0);
+      if (sizeof(R) == 4) {
+        const float4* c4 = reinterpret_cast<const float4*>(c);
+        const float4* h4 = reinterpret_cast<const float4*>(hh);
 #pragma unroll
-      for (int p2 = 0; p2 < NMAX; ++p2) {   // padded entries are zero
-        R cv = c[p2];
-        a1 += cv * phy[p2];
-        a2 += cv * psy[p2];
-        a3 += hh[p2] * phy[p2];
+        for (int v = 0; v < NMAX / 4; ++v) {
+          const float4 cv = c4[v], hv = h4[v];
+          const int p2 = 4 * v;
+          a1 += (R)cv.x * phy[p2];     a2 += (R)cv.x * psy[p2];     a3 += (R)hv.x * phy[p2];
+          b1 += (R)cv.y * phy[p2 + 1]; b2 += (R)cv.y * psy[p2 + 1]; b3 += (R)hv.y * phy[p2 + 1];
+          a1 += (R)cv.z * phy[p2 + 2]; a2 += (R)cv.z * psy[p2 + 2]; a3 += (R)hv.z * phy[p2 + 2];
+          b1 += (R)cv.w * phy[p2 + 3]; b2 += (R)cv.w * psy[p2 + 3]; b3 += (R)hv.w * phy[p2 + 3];
+        }
+      } else {
+        const double2* c2 = reinterpret_cast<const double2*>(c);
+        const double2* h2 = reinterpret_cast<const double2*>(hh);
+#pragma unroll
+        for (int v = 0; v < NMAX / 2; ++v) {
+          const double2 cv = c2[v], hv = h2[v];
+          const int p2 = 2 * v;
+          a1 += (R)cv.x * phy[p2];     a2 += (R)cv.x * psy[p2];     a3 += (R)hv.x * phy[p2];
+          b1 += (R)cv.y * phy[p2 + 1]; b2 += (R)cv.y * psy[p2 + 1]; b3 += (R)hv.y * phy[p2 + 1];
+        }
       }
+      a1 += b1; a2 += b2; a3 += b3;
       u += phx * a1;
       G += phx * a3;
       cpsi += psx * a1 + phx * a2;
