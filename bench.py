@@ -187,6 +187,8 @@ def run_ours(args):
 
     n_int = max(len(i.degrees) for i in wl.instances)
     state = {"r": 0}
+    plan.begin_interval(0)
+    tune_ms = plan.autotune(0)
 
     def step():
         r = state["r"] % n_int
@@ -261,11 +263,13 @@ def run_ours(args):
                        "step": "one interval of the hp solve: hand-off + K = 8 iterations",
                        "intervals_timed": done},
             "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps, "roofline": roof,
-            "wall_s": t_wall}
+            "wall_s": t_wall, "autotune": {"sweep_ms": tune_ms, "nodes_per_cohort": None}}
 
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(args, wl, prec)
         line["fp64_path"] = fp64_leg(args)
+        line["time_to_1e-6"] = time_to_tol_legs(args)
+        line["batch_w3"] = batch_leg(args)
         line["cpu_baseline"] = cpu_baseline(wl)
     plan.close()
     if rank == 0:
@@ -332,6 +336,71 @@ def fp64_leg(args):
     ns = node_samples_per_interval(wl, 0) / wl.K
     return {"value": ns / (ms / 1e3), "unit": "node-samples/s",
             "sample": "one iteration of the first interval of the 2-D workload at M=4096 (FP64 sweep)", "ms": ms}
+
+
+def time_to_tol_legs(args, tol=1e-6):
+    """Time until the L-inf error against the closed form reaches tol: the 1-D
+    single-interval workload (its full size, both precisions) and the first
+    interval of the 2-D long-time workload (mixed).  GPU time of the iterations
+    (CUDA events); the error is read after every iteration, outside the events."""
+    import numpy as np
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    out = {}
+    cases = [("w1_mixed", W.w1(), L.MIXED, 12), ("w1_fp64", W.w1(), L.FP64, 12),
+             ("w2_first_interval_mixed", W.w2(M=args.M, n_intervals=1), L.MIXED, 10)]
+    for name, wl, prec, kmax in cases:
+        inst = wl.instances[0]
+        plan = Plan.from_workload(wl, precision=prec)
+        ex = W.exact_block(wl, inst, plan.node_grid(), 0)
+        plan.begin_interval(0)
+        ms_total, errs, reached = 0.0, [], None
+        for k in range(kmax):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.iterate(0, 1)
+            b.record()
+            torch.cuda.synchronize()
+            ms_total += a.elapsed_time(b)
+            err = float(np.abs(plan.get_nodes(0, 0).cpu().numpy() - ex).max())
+            errs.append(err)
+            if reached is None and err <= tol:
+                reached = {"iterations": k + 1, "ms": ms_total}
+        out[name] = {"reached": reached, "linf_by_iteration": errs, "ms_per_iteration": ms_total / kmax,
+                     "n_ref": wl.n_ref, "M": wl.M}
+        plan.close()
+    return out
+
+
+def batch_leg(args):
+    """Batched uneven instances (initial-singularity workload shape) in one plan:
+    64 instances with 8-16 geometric intervals and degrees 4 + 2k, M = 4096,
+    K = 8, first two intervals (node-samples/s, mixed)."""
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    wl = W.w3(M=4096, batch=64)
+    plan = Plan.from_workload(wl, precision=L.MIXED)
+    plan.begin_interval(0)
+    plan.iterate(0, 1)
+    torch.cuda.synchronize()
+    ns, ms = 0, 0.0
+    for r in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.begin_interval(r)
+        plan.iterate(r, wl.K)
+        b.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        ns += sum(int(i.degrees[r]) * wl.n_space * wl.M * wl.K for i in wl.instances if r < len(i.degrees))
+    st = plan.stats()
+    plan.close()
+    return {"value": ns / (ms / 1e3), "unit": "node-samples/s", "instances": len(wl.instances),
+            "sample": "intervals 1-2 of 64 uneven instances, M=4096, K=8", "ms": ms}
 
 
 def run_reference(args):

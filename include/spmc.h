@@ -60,7 +60,7 @@ typedef struct {
   int n_space;              /* JG(1,1) nodes = spatial modes per axis, 2..32 */
   int time_family;          /* SPMC_TIME_LGL or SPMC_TIME_RADAU_LEFT */
   int max_intervals;        /* largest interval count of any instance */
-  int max_degree;           /* largest time degree M_n of any interval, 1..32 */
+  int max_degree;           /* largest time degree M_n of any interval, 1..39 */
   long long M;              /* samples per node, >= 1 */
   int K;                    /* iterations per interval (cap when tol > 0) */
   double tol;               /* stop an interval once max|eps| < tol; <= 0: run K */
@@ -178,6 +178,15 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
 /* Enable (1) or disable (0) CUDA-event timing of every sweep kernel launch; the
  * totals accumulate in spmc_stats.sweep_ms / sweep_launches (reset on enable). */
 spmc_status spmc_set_timing(spmc_plan_t plan, int enable);
+
+/* Autotuner: times the sweep kernel of one iteration of `interval` (which must
+ * have been started with spmc_begin_interval) for each candidate cohort width
+ * (spatial nodes per cohort), keeps the fastest for the plan and returns its
+ * time in *best_ms (may be NULL).  The nodal values are left unchanged: the
+ * candidates run the reconstruction, slices and sweep but not the update.
+ * Results of later iterations do not depend on the choice (per-node sums run in
+ * sample order whatever the width). */
+spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, double* best_ms);
 
 /* The n_space JG(1,1) node coordinates of one axis, ascending (host array). */
 spmc_status spmc_space_nodes(spmc_plan_t plan, double* x_host);

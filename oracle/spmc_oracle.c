@@ -842,7 +842,9 @@ static double walk_tangent(const orc_problem* pb, const orc_interval_ctx* ic, co
     double u, dtu, mlap, ud, dtud, mlapd;
     orc_eval(pb, ic->Mt, ic->cu, ic->ct, pts + i * d, xi, &u, &dtu, &mlap);
     orc_eval(pb, ic->Mt, cdu, cdt, pts + i * d, xi, &ud, &dtud, &mlapd);
-    sum += wts[i] * (orc_df(pb, u) * ud + orc_df_ds(pb, u) * ds - dtud - pb->kappa * mlapd);
+    /* the source f_add = d_t u_ex - kappa Delta u_ex - f(u_ex) depends on s through f(u_ex) */
+    double dsrc = (pb->ex_kind != 0) ? -orc_df_ds(pb, orc_exact(pb, pts + i * d, taus[i])) * ds : 0.0;
+    sum += wts[i] * (orc_df(pb, u) * ud + orc_df_ds(pb, u) * ds + dsrc - dtud - pb->kappa * mlapd);
   }
   free(pts); free(taus); free(wts);
   return sum;

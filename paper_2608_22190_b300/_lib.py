@@ -60,6 +60,7 @@ _SIGNATURES = {
     "spmc_iterate_static": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spmc_set_timing": (C.c_int, [_PLAN, C.c_int]),
+    "spmc_autotune": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_space_nodes": (C.c_int, [_PLAN, C.POINTER(C.c_double)]),
     "spmc_get_stats": (C.c_int, [_PLAN, C.POINTER(Stats)]),
     "spmc_last_error": (C.c_char_p, [_PLAN]),

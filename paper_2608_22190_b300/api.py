@@ -128,6 +128,27 @@ class Plan:
         L.check(L.lib.spmc_iterate(self._h, C.c_void_p(_stream_ptr(stream)), interval, n_iter, C.byref(mx)), self._h)
         return mx.value
 
+    def final_values(self, flat: torch.Tensor) -> torch.Tensor:
+        """u(T) at the spatial nodes for every instance: the last row of each
+        instance's last interval (LGL time nodes end at t_n), shape (batch, S)."""
+        rows = []
+        for b in range(self.batch):
+            blk = self.blocks(flat, b)[-1]
+            rows.append(blk[-1])
+        return torch.stack(rows)
+
+    def grad(self, dloss_du_T: torch.Tensor, n_coef: int = 0, stream=None):
+        """Reverse-mode gradient after solve(): returns (dL/d f_scale (batch,),
+        dL/d u0 coefficients (batch, n_coef^d) or None)."""
+        g = dloss_du_T.contiguous().to(torch.float64)
+        assert g.is_cuda and g.numel() == self.batch * self.S
+        gs = torch.zeros(self.batch, dtype=torch.float64, device="cuda")
+        gc = torch.zeros(self.batch, max(1, n_coef ** self.dim), dtype=torch.float64, device="cuda") if n_coef else None
+        L.check(L.lib.spmc_grad(self._h, C.c_void_p(_stream_ptr(stream)), C.c_void_p(g.data_ptr()),
+                                C.c_void_p(gs.data_ptr()), C.c_void_p(gc.data_ptr() if gc is not None else None)),
+                self._h)
+        return gs, gc
+
     def get_nodes(self, instance: int, interval: int, stream=None) -> torch.Tensor:
         Mt = self.degrees[instance][interval]
         out = torch.empty((Mt + 1, self.S), dtype=torch.float64, device="cuda")
@@ -158,6 +179,12 @@ class Plan:
         return {"points": s.points, "capped": s.capped, "iterations_run": s.iterations_run,
                 "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms}
 
+    def autotune(self, interval: int = 0, stream=None) -> float:
+        """Pick the sweep's cohort width by timing one sweep per candidate (nodal values unchanged)."""
+        ms = C.c_double()
+        L.check(L.lib.spmc_autotune(self._h, C.c_void_p(_stream_ptr(stream)), interval, C.byref(ms)), self._h)
+        return ms.value
+
     def set_timing(self, enable: bool):
         L.check(L.lib.spmc_set_timing(self._h, 1 if enable else 0), self._h)
 
@@ -171,3 +198,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class SpmcFunction(torch.autograd.Function):
+    """u(T) at the nodes as a differentiable function of the reaction scales
+    (batch,) and the u0 phi-coefficients (batch, n_coef, n_coef) (2-D, LGL time
+    nodes).  Forward: spmc_solve; backward: spmc_grad (adjoint sweeps on the
+    forward walks, iterations recomputed from each interval's first iterate)."""
+
+    @staticmethod
+    def forward(ctx, f_scale, u0_coef, plan, wl):
+        nc = u0_coef.shape[-1]
+        for b, inst in enumerate(wl.instances):
+            c = u0_coef[b].detach().cpu().numpy()
+            plan.set_problem(b, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, float(f_scale[b]),
+                             inst.ex_kind, inst.ex_beta, np.ascontiguousarray(c.T).ravel(), L.U0_PHI_COEF, nc)
+        flat = plan.solve()
+        ctx.plan, ctx.nc, ctx.dim = plan, nc, wl.dim
+        ctx.devices = (f_scale.device, u0_coef.device)
+        return plan.final_values(flat).clone().to(u0_coef.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        gs, gc = ctx.plan.grad(grad_out.to("cuda"), n_coef=ctx.nc)
+        nc = ctx.nc
+        # coefficient (i, j) of phi_i(x) phi_j(y) sits at i + nc j
+        gcoef = gc.view(-1, nc, nc).transpose(1, 2).contiguous()
+        return gs.to(ctx.devices[0]), gcoef.to(ctx.devices[1]), None, None

@@ -315,3 +315,75 @@ __device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int 
 }
 
 }  // namespace spmc
+
+namespace spmc {
+
+// g(u) = df/ds and g'(u) for f = s g(u).
+__device__ __forceinline__ void reaction_g(const InstanceParams& ip, double u, double* g, double* dg) {
+  if (ip.f_kind == 1) { *g = sin(u); *dg = cos(u); return; }
+  *g = ip.fc[0] + u * (ip.fc[1] + u * (ip.fc[2] + u * ip.fc[3]));
+  *dg = ip.fc[1] + u * (2.0 * ip.fc[2] + 3.0 * u * ip.fc[3]);
+}
+
+// Adjoint of one quadrature term at y with weight cw = lambda_i w_p / M:
+// u* from the forward slice C, then the rank-1 scatters
+//   acc[0] += cw s g'(u*) Phi(y),  acc[1] += cw Phi(y),  acc[2] += cw Psi(y)
+// in coefficient order (x_1 fastest), Phi = prod phi, Psi = sum over one axis of
+// psi with phi on the others.  Returns cw (g(u*) - g(u_ex)) = the term's
+// derivative in the reaction scale s (the source f_add depends on s through
+// f(u_ex)).
+template <int D, int NMAX, typename R>
+__device__ __forceinline__ double adjoint_at(const InstanceParams& ip, int n, const R* __restrict__ sC, const R* y,
+                                             double cw, double* acc, int S, R Tt) {
+  R phx[NMAX], psx[NMAX];
+  basis<NMAX, R>(n, y[0], phx, psx);
+  double u = 0.0;
+  if (D == 1) {
+    for (int p = 0; p < n; ++p) u += (double)sC[p] * (double)phx[p];
+  } else {
+    R phy[NMAX], psy[NMAX];
+    basis<NMAX, R>(n, y[1], phy, psy);
+    for (int p1 = 0; p1 < n; ++p1) {
+      double a = 0.0;
+      for (int p2 = 0; p2 < n; ++p2) a += (double)sC[p1 * NMAX + p2] * (double)phy[p2];
+      u += (double)phx[p1] * a;
+    }
+  }
+  double g, dg;
+  reaction_g(ip, u, &g, &dg);
+  const double al = cw * ip.f_scale * dg;
+  if (D == 1) {
+    for (int p = 0; p < n; ++p) {
+      atomicAdd(&acc[p], al * (double)phx[p]);
+      atomicAdd(&acc[S + p], cw * (double)phx[p]);
+      atomicAdd(&acc[2 * S + p], cw * (double)psx[p]);
+    }
+  } else {
+    R phy[NMAX], psy[NMAX];
+    basis<NMAX, R>(n, y[1], phy, psy);
+    for (int p2 = 0; p2 < n; ++p2)
+      for (int p1 = 0; p1 < n; ++p1) {
+        const int p = p1 + n * p2;
+        const double ff = (double)phx[p1] * (double)phy[p2];
+        atomicAdd(&acc[p], al * ff);
+        atomicAdd(&acc[S + p], cw * ff);
+        atomicAdd(&acc[2 * S + p], cw * ((double)psx[p1] * (double)phy[p2] + (double)phx[p1] * (double)psy[p2]));
+      }
+  }
+  double gex = 0.0;
+  if (ip.ex_kind != 0) {
+    // u_ex at y: time factor Tt times the spatial closed form
+    double prod = 1.0;
+    for (int e = 0; e < D; ++e) {
+      const double ye = (double)y[e];
+      if (ip.ex_kind == 1) prod *= sinpi(ye);
+      else if (ip.ex_kind == 2) prod *= cospi(0.5 * ye);
+      else prod *= (1.0 - ye * ye) * (1.0 + ye);
+    }
+    double dgx;
+    reaction_g(ip, (double)Tt * prod, &gex, &dgx);
+  }
+  return cw * (g - gex);
+}
+
+}  // namespace spmc

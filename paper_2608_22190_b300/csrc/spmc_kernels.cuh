@@ -106,7 +106,7 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
                              const InstInterval* __restrict__ inst_of_node, const double* __restrict__ coef,
                              const InstanceParams* __restrict__ ip, R* __restrict__ slices,
                              SliceInfo* __restrict__ sinfo, int n, int n_sub, int row, long long sl_stride) {
-  __shared__ double L[40];
+  __shared__ double L[41];
   long long s = blockIdx.x;
   long long ti = slice_node[s];
   const TimeNode node = tn[ti];
@@ -168,6 +168,10 @@ struct SweepArgs {
   double kappa, shell;
   uint32_t k0, k1;
   int interval, iteration;
+  // adjoint sweep only
+  const double* lambda;     // adjoint of the nodal values (layout of U)
+  double* gT;               // per slice: 3 S accumulators (coefficient order)
+  double* gds;              // per instance: derivative in the reaction scale
 };
 
 // Per-sample walk state, kept in shared memory (structure of arrays).
@@ -260,7 +264,7 @@ struct StateRegion {
   int *k, *q, *last;
 };
 
-template <int D, int NMAX, typename R>
+template <int D, int NMAX, typename R, bool ADJ = false>
 __global__ void __launch_bounds__(256, (sizeof(R) == 4) ? 2 : 1)
 sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__ work_counter,
              void* __restrict__ state_base, long long state_stride) {
@@ -276,6 +280,7 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
   int* mnext = reinterpret_cast<int*>(p); p += W * sizeof(int);
   int* act = reinterpret_cast<int*>(p); p += W * sizeof(int);
   int* ready = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  double* sAcc = reinterpret_cast<double*>(p);   // adjoint: [G][3][S] accumulators of the window
   __shared__ int red[64];
   __shared__ double dred[32];
   __shared__ int s_next, s_nact;
@@ -301,6 +306,7 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
   const R* slices = reinterpret_cast<const R*>(a.slices);
   unsigned long long capped = 0, points = 0;
   double dummy_acc = 0.0;
+  double ds_acc = 0.0;   // adjoint: derivative in the reaction scale (this thread's terms)
 
   // block-wide exclusive scan of one count per thread; returns the total
   auto block_scan = [&](int cnt, int& base) -> int {
@@ -405,6 +411,8 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
         m0 = gmin;
         continue;
       }
+      if (ADJ)
+        for (int i = threadIdx.x; i < G * 3 * S; i += blockDim.x) sAcc[i] = 0.0;
       // stage the window's slices (16-byte vector copies) and time factors
       {
         const int nsl = min(G, Ktot - m0);
@@ -454,8 +462,13 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
           if (w > R(0)) {
             const int bsl = mv - m0;
             const R* sc = sSl + bsl * slst;
-            R res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)s_Tt[bsl], (R)s_dTt[bsl]);
-            st.S[wk] += w * res;
+            if (ADJ) {
+              const double cw = a.lambda[node.u_off + (long long)node.ell * S + j0 + jj] * (double)w / (double)a.M;
+              ds_acc += adjoint_at<D, NMAX, R>(ip, n, sc, Y, cw, sAcc + (long long)bsl * 3 * S, S, (R)s_Tt[bsl]);
+            } else {
+              R res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)s_Tt[bsl], (R)s_dTt[bsl]);
+              st.S[wk] += w * res;
+            }
             ++points;
           }
           if (st.last[wk]) { mnext[wk] = -1; break; }
@@ -471,6 +484,13 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
         }
       }
       __syncthreads();
+      if (ADJ) {
+        const int nsl = min(G, Ktot - m0);
+        for (int i = threadIdx.x; i < nsl * 3 * S; i += blockDim.x) {
+          const double v = sAcc[i];
+          if (v != 0.0) atomicAdd(&a.gT[(node.slice_base + m0) * 3 * S + i], v);
+        }
+      }
       // compact the active list
       int kc = 0;
       for (int i = threadIdx.x; i < nact; i += blockDim.x) kc += (mnext[act[i]] >= 0);
@@ -486,6 +506,22 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
       if (threadIdx.x == 0) s_nact = nkeep;
       __syncthreads();
       m0 += G;
+    }
+    if (ADJ) {
+      // derivative in the reaction scale: block sum of this cohort's terms
+      double t = ds_acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) dred[warp] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tt = 0.0;
+        for (int wv = 0; wv < nwarps; ++wv) tt += dred[wv];
+        if (tt != 0.0) atomicAdd(&a.gds[node.inst], tt);
+      }
+      __syncthreads();
+      ds_acc = 0.0;
+      continue;   // no chunk sums in the adjoint sweep
     }
     // every walk of the cohort has ended: each node's chunk sum in sample order
     for (int jj = 0; jj < JT; ++jj) {
@@ -570,6 +606,125 @@ __global__ void handoff_kernel(const InstInterval* __restrict__ ii, const double
     double acc = 0.0;
     for (int k = 0; k < T; ++k) acc += h[k] * U[w.u_off + (long long)k * S + j];
     for (int l = 0; l < Tn; ++l) U[w.next_u_off + (long long)l * S + j] = acc;
+  }
+}
+
+}  // namespace spmc
+
+namespace spmc {
+
+// ----------------------------------------------------------------- adjoint
+// lambda of interval r before its last iteration: lambda[k][j] = hw_k g_j with
+// g = dL/du(T) (the instance's last interval) or mu of the next interval.
+__global__ void adj_lambda_init_kernel(const InstInterval* __restrict__ ii, const int* __restrict__ last_of_inst,
+                                       const double* __restrict__ hw, const double* __restrict__ dLdz,
+                                       const double* __restrict__ mu, double* __restrict__ lambda, int r, int S) {
+  const InstInterval w = ii[blockIdx.x];
+  const int T = w.Mt + 1;
+  const double* src = (last_of_inst[w.inst] == r ? dLdz : mu) + (long long)w.inst * S;
+  const double* h = hw + w.h_off;
+  for (int i = threadIdx.x; i < T * S; i += blockDim.x) {
+    const int k = i / S, j = i - k * S;
+    lambda[w.u_off + i] = h[k] * src[j];
+  }
+}
+
+// Transposed time contraction of the adjoint slice accumulators:
+// Lam[c][q][p] = sum over the instance's slices s of L_q(xi(tau_s)) gT[s][c][p],
+// c in {alpha Phi, beta Phi, beta Psi}.  One block per active instance.
+__global__ void adj_time_kernel(const InstInterval* __restrict__ ii, const TimeNode* __restrict__ tn,
+                                const long long* __restrict__ first_tn, const SliceInfo* __restrict__ sinfo,
+                                const double* __restrict__ gT, double* __restrict__ lam, int S, int n_sub) {
+  __shared__ double L[41];
+  const InstInterval w = ii[blockIdx.x];
+  const int T = w.Mt + 1;
+  double* out = lam + 3LL * w.c_off / 2;   // c_off counts two (Mt+1) S blocks per instance
+  for (int i = threadIdx.x; i < 3 * T * S; i += blockDim.x) out[i] = 0.0;
+  __syncthreads();
+  for (long long t = first_tn[blockIdx.x]; t < first_tn[blockIdx.x + 1]; ++t) {
+    const TimeNode nd = tn[t];
+    const long long ns = (long long)n_sub * nd.nstar;
+    for (long long m = 0; m < ns; ++m) {
+      const long long sidx = nd.slice_base + m;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double tau = sinfo[sidx].tau;
+        const double xi = (2.0 * tau - w.t0 - (w.t0 + w.h)) / w.h;
+        L[0] = 1.0;
+        if (w.Mt >= 1) L[1] = xi;
+        for (int q = 1; q < w.Mt; ++q) L[q + 1] = ((2.0 * q + 1.0) * xi * L[q] - q * L[q - 1]) / (q + 1.0);
+      }
+      __syncthreads();
+      const double* g = gT + sidx * 3 * S;
+      for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) {
+        const double v = g[i];
+        if (v == 0.0) continue;
+        const int c = i / S, p = i - c * S;
+        for (int q = 0; q < T; ++q) out[((long long)c * T + q) * S + p] += L[q] * v;
+      }
+    }
+  }
+}
+
+// lambda += R^T (Lam_alpha - Dt^T Lam_betaPhi - kappa Lam_betaPsi), R = B x A x ... x A,
+// (Dt^T X)_l = sum_{q < l, l+q odd} (2/h)(2q+1) X_q.  One block per active instance.
+template <int D>
+__global__ void adj_combine_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ lam,
+                                   const double* __restrict__ A, const double* __restrict__ Bt,
+                                   double* __restrict__ lambda, int n, double kappa) {
+  extern __shared__ double sm[];
+  const InstInterval w = ii[blockIdx.x];
+  int S = 1;
+  for (int e = 0; e < D; ++e) S *= n;
+  const int T = w.Mt + 1, tot = T * S;
+  const double* la = lam + 3LL * w.c_off / 2;
+  const double* lb = la + tot;
+  const double* lp = lb + tot;
+  double* x = sm;
+  double* y = sm + tot;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int l = i / S, p = i - l * S;
+    double dt = 0.0;
+    for (int q = l - 1; q >= 0; q -= 2) dt += (2.0 / w.h) * (2.0 * q + 1.0) * lb[q * S + p];
+    x[i] = la[i] - dt - kappa * lp[i];
+  }
+  __syncthreads();
+  // spatial axes: x[..p_e..] -> y[..j_e..] = sum_{p_e} A[p_e][j_e] x
+  double* src = x;
+  double* dst = y;
+  int stride = 1;
+  for (int e = 0; e < D; ++e) {
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+      const int q = i / S, idx = i - q * S;
+      const int je = (idx / stride) % n;
+      const int base = q * S + idx - je * stride;
+      double acc = 0.0;
+      for (int pe = 0; pe < n; ++pe) acc += A[pe * n + je] * src[base + pe * stride];
+      dst[i] = acc;
+    }
+    __syncthreads();
+    double* t = src; src = dst; dst = t;
+    stride *= n;
+  }
+  // time axis: lambda[k][j] += sum_q B[q][k] src[q][j]
+  const double* B = Bt + w.b_off;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int kk = i / S, j = i - kk * S;
+    double acc = 0.0;
+    for (int q = 0; q < T; ++q) acc += B[q * T + kk] * src[q * S + j];
+    lambda[w.u_off + i] += acc;
+  }
+}
+
+// mu_j = sum_l lambda[l][j]: the adjoint of the interval's first row.
+__global__ void adj_mu_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ lambda,
+                              double* __restrict__ mu, int S) {
+  const InstInterval w = ii[blockIdx.x];
+  const int T = w.Mt + 1;
+  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < T; ++l) acc += lambda[w.u_off + (long long)l * S + j];
+    mu[(long long)w.inst * S + j] = acc;
   }
 }
 

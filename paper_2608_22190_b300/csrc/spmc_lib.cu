@@ -87,6 +87,12 @@ struct spmc_plan_s {
   bool solved = false;
   bool timing = false;
   bool params_dirty = false;   // instance parameters / u0 changed, layout unchanged
+  // adjoint workspace (spmc_grad)
+  double *d_lambda = nullptr, *d_Ubak = nullptr, *d_iter = nullptr, *d_gT = nullptr, *d_lam = nullptr;
+  double *d_mu = nullptr, *d_dLdz = nullptr, *d_gds = nullptr, *d_phi = nullptr;
+  int* d_last = nullptr;
+  std::vector<long long*> d_first_tn;   // per round: instance ranges of the time-node table
+  bool grad_ready = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
 };
@@ -259,6 +265,7 @@ spmc_status build(spmc_plan_t plan) {
   if ((st = upload(plan, &plan->d_ip, ips)) != SPMC_OK) return st;
   if ((st = upload(plan, &plan->d_u0, u0)) != SPMC_OK) return st;
   plan->built = true;
+  plan->grad_ready = false;
   return SPMC_OK;
 }
 
@@ -356,6 +363,99 @@ spmc_status dispatch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& r
   return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
 }
 
+// Reconstruction (Step 1) and time slices of the current nodal values of round rd.
+spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
+  const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
+  if (rd.ii.empty()) return SPMC_OK;
+  int maxT = 0;
+  for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
+  size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
+  if (D == 1) {
+    SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
+                                                                          plan->d_coef, n);
+  } else {
+    SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
+                                                                          plan->d_coef, n);
+  }
+  SPMC_CUDA(cudaGetLastError());
+  const bool fp64 = plan->d.precision == SPMC_FP64;
+  if (rd.n_slices > 0) {
+    if (D == 1) {
+      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+    } else {
+      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+    }
+    SPMC_CUDA(cudaGetLastError());
+  }
+  return SPMC_OK;
+}
+
+// The adjoint sweep of iteration `iteration` of round rd (same walks as the forward sweep).
+template <int D, int NMAX, typename R>
+spmc_status launch_adjoint_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const spmc_plan_desc& d = plan->d;
+  SweepArgs a;
+  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
+  a.partial = plan->d_partial; a.counters = plan->d_counters; a.status = plan->d_status;
+  a.n = d.n_space; a.S = plan->S;
+  a.chunk = plan->chunk;
+  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
+  a.n_sub = d.n_sub;
+  int gb = 0;
+  while ((1 << gb) < d.n_sub) ++gb;
+  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
+  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
+  a.interval = interval; a.iteration = iteration;
+  a.M = d.M;
+  a.sl_stride = plan->sl_stride;
+  a.half = plan->half;
+  a.lambda = plan->d_lambda; a.gT = plan->d_gT; a.gds = plan->d_gds;
+  const int JT = std::min(4, plan->S);
+  const int W = JT * plan->chunk;
+  const long long n_jt = (plan->S + JT - 1) / JT;
+  const long long n_cohorts = (long long)rd.tn.size() * n_jt * a.n_chunks;
+  if (n_cohorts <= 0) return SPMC_OK;
+  size_t smem = sweep_smem(d.n_sub, plan->sl_stride, W, sizeof(R)) + (size_t)d.n_sub * 3 * plan->S * sizeof(double);
+  auto kern = sweep_kernel<D, NMAX, R, true>;
+  SPMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, plan->threads, smem));
+  if (occ < 1) return fail(plan, SPMC_ERR_UNSUPPORTED, "adjoint sweep configuration does not fit on an SM");
+  long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
+  const size_t stride = state_stride_bytes(D, W, sizeof(R));
+  if (plan->state_bytes < stride * grid) {
+    cudaFree(plan->d_state);
+    plan->d_state = nullptr;
+    plan->state_bytes = 0;
+    SPMC_CUDA(cudaMalloc(&plan->d_state, stride * grid));
+    plan->state_bytes = stride * grid;
+  }
+  SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
+  kern<<<(unsigned)grid, plan->threads, smem, stream>>>(a, JT, plan->chunk, n_cohorts, plan->d_work, plan->d_state,
+                                                         (long long)stride);
+  SPMC_CUDA(cudaGetLastError());
+  return SPMC_OK;
+}
+
+template <typename R>
+spmc_status dispatch_adjoint(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const int n = plan->d.n_space;
+  if (plan->d.dim == 1) return launch_adjoint_sweep<1, 32, R>(plan, stream, rd, interval, iteration);
+  if (plan->d.dim == 2) {
+    if (n <= 8) return launch_adjoint_sweep<2, 8, R>(plan, stream, rd, interval, iteration);
+    if (n <= 16) return launch_adjoint_sweep<2, 16, R>(plan, stream, rd, interval, iteration);
+    if (n <= 24) return launch_adjoint_sweep<2, 24, R>(plan, stream, rd, interval, iteration);
+    return launch_adjoint_sweep<2, 32, R>(plan, stream, rd, interval, iteration);
+  }
+  return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
+}
+
 // One residual iteration on interval r for every instance that has it.
 spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   Round& rd = plan->rounds[r];
@@ -399,6 +499,39 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
     SPMC_CUDA(cudaGetLastError());
   }
   return SPMC_OK;
+}
+
+// Copy the round's nodal blocks between U and a contiguous buffer (offsets c_off/2).
+__global__ void round_copy_kernel(const InstInterval* __restrict__ ii, double* __restrict__ U,
+                                  double* __restrict__ buf, int S, int to_buf) {
+  const InstInterval w = ii[blockIdx.x];
+  const long long tot = (long long)(w.Mt + 1) * S;
+  double* b = buf + w.c_off / 2;
+  for (long long i = threadIdx.x; i < tot; i += blockDim.x) {
+    if (to_buf) b[i] = U[w.u_off + i];
+    else U[w.u_off + i] = b[i];
+  }
+}
+
+// grad of the u0 coefficients: dL/dc_{c} = sum_j mu_j prod_e phi_{c_e}(x_{j_e}).
+__global__ void u0_coef_grad_kernel(const double* __restrict__ mu, const double* __restrict__ phi,
+                                    const int* __restrict__ ncoef, double* __restrict__ out, long long out_stride,
+                                    int n, int S, int D) {
+  const int inst = blockIdx.x;
+  const int nc = ncoef[inst];
+  if (nc <= 0) return;
+  int NC = 1;
+  for (int e = 0; e < D; ++e) NC *= nc;
+  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < S; ++j) {
+      double prod = mu[(long long)inst * S + j];
+      int jj = j, cc = c;
+      for (int e = 0; e < D; ++e) { prod *= phi[(jj % n) * n + (cc % nc)]; jj /= n; cc /= nc; }
+      acc += prod;
+    }
+    out[(long long)inst * out_stride + c] = acc;
+  }
 }
 
 spmc_status begin_interval(spmc_plan_t plan, cudaStream_t stream, int r) {
@@ -563,12 +696,17 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   if (!desc) return SPMC_ERR_INVALID;
   const spmc_plan_desc& d = *desc;
   if (d.dim < 1 || d.dim > 5 || d.n_space < 2 || d.n_space > 32 || d.max_intervals < 1 || d.max_degree < 1 ||
-      d.max_degree > 32 || d.M < 1 || d.K < 1 || d.n_ref < 1 || d.n_sub < 1 || d.n_sub > 16 ||
+      d.max_degree > 39 || d.M < 1 || d.K < 1 || d.n_ref < 1 || d.n_sub < 1 || d.n_sub > 16 ||
       (d.n_sub & (d.n_sub - 1)) || !(d.shell >= 0.0) || d.shell >= 0.5 || d.max_steps < 1 || !(d.kappa > 0.0) || d.batch < 1 ||
       (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
       (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL)
     return SPMC_ERR_INVALID;
   if (d.dim > 2) return SPMC_ERR_UNSUPPORTED;
+  {
+    // the reconstruction keeps two (M_n+1) x n^d FP64 blocks in shared memory
+    double S = std::pow((double)d.n_space, d.dim);
+    if (2.0 * (d.max_degree + 1) * S * 8.0 > 227.0 * 1024.0) return SPMC_ERR_UNSUPPORTED;
+  }
   if (d.tol > 0.0 && d.batch > 1) return SPMC_ERR_UNSUPPORTED;
   spmc_plan_t plan = new spmc_plan_s();
   plan->d = d;
@@ -841,9 +979,165 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
 
 spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_du_T, double* grad_f_scale,
                       double* grad_u0_coef) {
-  (void)cuda_stream; (void)dloss_du_T; (void)grad_f_scale; (void)grad_u0_coef;
   if (!plan) return SPMC_ERR_INVALID;
-  return fail(plan, SPMC_ERR_UNSUPPORTED, "gradient not built yet");
+  if (!plan->solved) return fail(plan, SPMC_ERR_INVALID, "spmc_grad needs a prior spmc_solve on this plan");
+  if (!dloss_du_T) return fail(plan, SPMC_ERR_INVALID, "null dL/du(T)");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const spmc_plan_desc& d = plan->d;
+  const int S = plan->S, n = d.n_space, D = d.dim, B = d.batch, K = d.K;
+  const int R = (int)plan->rounds.size();
+  if (d.tol > 0.0) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad needs a fixed iteration count (tol <= 0)");
+  // workspace (first call)
+  if (!plan->grad_ready) {
+    cudaFree(plan->d_lambda); cudaFree(plan->d_Ubak); cudaFree(plan->d_iter); cudaFree(plan->d_gT);
+    cudaFree(plan->d_lam); cudaFree(plan->d_mu); cudaFree(plan->d_dLdz); cudaFree(plan->d_gds);
+    cudaFree(plan->d_phi); cudaFree(plan->d_last);
+    for (auto p : plan->d_first_tn) cudaFree(p);
+    plan->d_lambda = plan->d_Ubak = plan->d_iter = plan->d_gT = plan->d_lam = nullptr;
+    plan->d_mu = plan->d_dLdz = plan->d_gds = plan->d_phi = nullptr;
+    plan->d_last = nullptr;
+    long long maxblk = 0;
+    for (auto& rd : plan->rounds) maxblk = std::max(maxblk, rd.coef_total / 2);
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_lambda, sizeof(double) * std::max(1LL, plan->U_total)));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_Ubak, sizeof(double) * std::max(1LL, plan->U_total)));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_iter, sizeof(double) * std::max(1LL, maxblk * K)));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_gT, sizeof(double) * 3 * S * std::max(1LL, plan->slice_cap)));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_lam, sizeof(double) * std::max(1LL, 3 * plan->coef_cap / 2)));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_mu, sizeof(double) * (size_t)B * S));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_dLdz, sizeof(double) * (size_t)B * S));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_gds, sizeof(double) * B));
+    std::vector<int> last(B);
+    for (int i = 0; i < B; ++i) last[i] = plan->probs[i].n_int - 1;
+    spmc_status st;
+    if ((st = upload(plan, &plan->d_last, last)) != SPMC_OK) return st;
+    std::vector<double> ph((size_t)n * n);
+    for (int j = 0; j < n; ++j) phi_values(n, plan->xnodes[j], &ph[(size_t)j * n]);
+    if ((st = upload(plan, &plan->d_phi, ph)) != SPMC_OK) return st;
+    plan->d_first_tn.assign(R, nullptr);
+    for (int r = 0; r < R; ++r) {
+      const Round& rd = plan->rounds[r];
+      std::vector<long long> first(rd.ii.size() + 1, 0);
+      long long t = 0;
+      for (size_t a = 0; a < rd.ii.size(); ++a) {
+        first[a] = t;
+        while (t < (long long)rd.tn.size() && rd.tn[t].inst == rd.ii[a].inst) ++t;
+      }
+      first[rd.ii.size()] = t;
+      if ((st = upload(plan, &plan->d_first_tn[r], first)) != SPMC_OK) return st;
+    }
+    plan->grad_ready = true;
+  }
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_dLdz, dloss_du_T, sizeof(double) * (size_t)B * S, cudaMemcpyDefault, s));
+  SPMC_CUDA(cudaMemsetAsync(plan->d_gds, 0, sizeof(double) * B, s));
+  SPMC_CUDA(cudaMemsetAsync(plan->d_mu, 0, sizeof(double) * (size_t)B * S, s));
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_Ubak, plan->d_U, sizeof(double) * plan->U_total, cudaMemcpyDeviceToDevice, s));
+  const bool fp64 = d.precision == SPMC_FP64;
+  spmc_status st = SPMC_OK;
+  for (int r = R - 1; r >= 0 && st == SPMC_OK; --r) {
+    Round& rd = plan->rounds[r];
+    if (rd.ii.empty()) continue;
+    const unsigned nb = (unsigned)rd.ii.size();
+    const long long blk = rd.coef_total / 2;
+    // recompute the interval's iterates U^(0..K-1) from its first iterate
+    if ((st = begin_interval(plan, s, r)) != SPMC_OK) break;
+    for (int k = 0; k < K; ++k) {
+      round_copy_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_U, plan->d_iter + (long long)k * blk, S, 1);
+      if (k + 1 < K && (st = iterate_once(plan, s, r)) != SPMC_OK) break;
+    }
+    if (st != SPMC_OK) break;
+    adj_lambda_init_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_last, plan->d_hw, plan->d_dLdz, plan->d_mu,
+                                              plan->d_lambda, r, S);
+    SPMC_CUDA(cudaGetLastError());
+    int maxT = 0;
+    for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
+    const size_t csm = sizeof(double) * 2 * (size_t)maxT * S;
+    for (int k = K; k >= 1; --k) {
+      round_copy_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_U, plan->d_iter + (long long)(k - 1) * blk, S, 0);
+      if ((st = prepare_slices(plan, s, rd)) != SPMC_OK) break;
+      SPMC_CUDA(cudaMemsetAsync(plan->d_gT, 0, sizeof(double) * 3 * S * std::max(1LL, rd.n_slices), s));
+      st = fp64 ? dispatch_adjoint<double>(plan, s, rd, r, k) : dispatch_adjoint<float>(plan, s, rd, r, k);
+      if (st != SPMC_OK) break;
+      adj_time_kernel<<<nb, 256, 0, s>>>(rd.d_ii, rd.d_tn, plan->d_first_tn[r], plan->d_sinfo, plan->d_gT,
+                                         plan->d_lam, S, d.n_sub);
+      if (D == 1) {
+        SPMC_CUDA(cudaFuncSetAttribute(adj_combine_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        adj_combine_kernel<1><<<nb, 256, csm, s>>>(rd.d_ii, plan->d_lam, plan->d_A, plan->d_B, plan->d_lambda, n, d.kappa);
+      } else {
+        SPMC_CUDA(cudaFuncSetAttribute(adj_combine_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        adj_combine_kernel<2><<<nb, 256, csm, s>>>(rd.d_ii, plan->d_lam, plan->d_A, plan->d_B, plan->d_lambda, n, d.kappa);
+      }
+      SPMC_CUDA(cudaGetLastError());
+    }
+    if (st != SPMC_OK) break;
+    adj_mu_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_lambda, plan->d_mu, S);
+    SPMC_CUDA(cudaGetLastError());
+  }
+  // the forward solution is restored whatever happened
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_U, plan->d_Ubak, sizeof(double) * plan->U_total, cudaMemcpyDeviceToDevice, s));
+  if (st != SPMC_OK) return st;
+  if (grad_f_scale)
+    SPMC_CUDA(cudaMemcpyAsync(grad_f_scale, plan->d_gds, sizeof(double) * B, cudaMemcpyDefault, s));
+  if (grad_u0_coef) {
+    int maxnc = 0;
+    std::vector<int> nc(B);
+    for (int i = 0; i < B; ++i) { nc[i] = plan->probs[i].u0_kind == SPMC_U0_PHI_COEF ? plan->probs[i].n_coef : 0; maxnc = std::max(maxnc, nc[i]); }
+    if (maxnc > 0) {
+      long long NC = 1;
+      for (int e = 0; e < D; ++e) NC *= maxnc;
+      int* d_nc = nullptr;
+      if ((st = upload(plan, &d_nc, nc)) != SPMC_OK) return st;
+      u0_coef_grad_kernel<<<(unsigned)B, 128, 0, s>>>(plan->d_mu, plan->d_phi, d_nc, grad_u0_coef, NC, n, S, D);
+      SPMC_CUDA(cudaGetLastError());
+      SPMC_CUDA(cudaStreamSynchronize(s));
+      cudaFree(d_nc);
+    }
+  }
+  return read_status(plan, s);
+}
+
+spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, double* best_ms) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built || plan->params_dirty)
+    return fail(plan, SPMC_ERR_INVALID, "spmc_autotune needs a built plan: call spmc_begin_interval first");
+  if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Round& rd = plan->rounds[interval];
+  if (rd.ii.empty()) return SPMC_OK;
+  const bool fp64 = plan->d.precision == SPMC_FP64;
+  // reconstruction and slices of the current nodal values (left unchanged)
+  spmc_status st = prepare_slices(plan, s, rd);
+  if (st != SPMC_OK) return st;
+  // candidate cohort widths that fit two blocks per SM (FP32) / one (FP64)
+  const int wmax = fp64 ? 4096 : 6144;
+  const int cands[] = {1, 2, 4, 6, 8, 12, 16, 24, 32};
+  cudaEvent_t e0, e1;
+  SPMC_CUDA(cudaEventCreate(&e0));
+  SPMC_CUDA(cudaEventCreate(&e1));
+  const int keep = plan->JT;
+  const bool timing = plan->timing;
+  plan->timing = false;
+  float best = 1e30f;
+  int best_jt = keep;
+  for (int jt : cands) {
+    if (jt * plan->chunk > wmax || (jt > plan->S && jt != 1)) continue;
+    plan->JT = jt;
+    SPMC_CUDA(cudaEventRecord(e0, s));
+    st = fp64 ? dispatch_sweep<double>(plan, s, rd, interval, rd.iteration + 1)
+              : dispatch_sweep<float>(plan, s, rd, interval, rd.iteration + 1);
+    if (st != SPMC_OK) break;
+    SPMC_CUDA(cudaEventRecord(e1, s));
+    SPMC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    SPMC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; best_jt = jt; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->timing = timing;
+  plan->JT = (st == SPMC_OK) ? best_jt : keep;
+  if (st != SPMC_OK) return st;
+  if (best_ms) *best_ms = best;
+  return SPMC_OK;
 }
 
 spmc_status spmc_set_timing(spmc_plan_t plan, int enable) {
@@ -880,6 +1174,9 @@ void spmc_destroy(spmc_plan_t plan) {
   cudaFree(plan->d_status);
   cudaFree(plan->d_work);
   cudaFree(plan->d_state);
+  cudaFree(plan->d_lambda); cudaFree(plan->d_Ubak); cudaFree(plan->d_iter); cudaFree(plan->d_gT); cudaFree(plan->d_lam);
+  cudaFree(plan->d_mu); cudaFree(plan->d_dLdz); cudaFree(plan->d_gds); cudaFree(plan->d_phi); cudaFree(plan->d_last);
+  for (auto p : plan->d_first_tn) cudaFree(p);
   delete plan;
 }
 

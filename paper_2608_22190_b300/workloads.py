@@ -145,3 +145,27 @@ def u0_nodal(inst: Instance, grid: np.ndarray) -> np.ndarray:
     if inst.ex_kind == EX_POLY:
         return np.prod((1.0 - grid ** 2) * (1.0 + grid), axis=1)
     raise ValueError("instance has no closed-form initial condition")
+
+
+def time_nodes_reference(family: int, Mt: int) -> np.ndarray:
+    """Reference-interval time nodes (LGL or left Radau) from scipy's Jacobi zeros,
+    for evaluating closed-form solutions at the nodes."""
+    import scipy.special as sps
+    if family == TIME_LGL:
+        inner = sps.roots_jacobi(Mt - 1, 1.0, 1.0)[0] if Mt >= 2 else np.zeros(0)
+        return np.concatenate([[-1.0], inner, [1.0]])
+    return np.concatenate([[-1.0], sps.roots_jacobi(Mt, 0.0, 1.0)[0]])
+
+
+def exact_block(wl: Workload, inst: Instance, grid: np.ndarray, interval: int) -> np.ndarray:
+    """The manufactured closed form at every node of one interval, (M_n+1, S)."""
+    Mt = int(inst.degrees[interval])
+    t0, t1 = inst.t_breaks[interval], inst.t_breaks[interval + 1]
+    t = t0 + (time_nodes_reference(wl.time_family, Mt) + 1.0) * 0.5 * (t1 - t0)
+    if inst.ex_kind == EX_SIN:
+        return np.exp(-inst.ex_beta * t)[:, None] * np.prod(np.sin(np.pi * grid), axis=1)[None, :]
+    if inst.ex_kind == EX_COSHALF:
+        return np.exp(-inst.ex_beta * t)[:, None] * np.prod(np.cos(0.5 * np.pi * grid), axis=1)[None, :]
+    if inst.ex_kind == EX_POLY:
+        return (1.0 + t + t * t)[:, None] * np.prod((1.0 - grid ** 2) * (1.0 + grid), axis=1)[None, :]
+    raise ValueError("instance has no closed form")
