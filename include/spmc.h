@@ -56,7 +56,7 @@ typedef struct spmc_plan_s* spmc_plan_t;
 /* Geometry, discretisation and sampling of a batch of instances.
  * Section 2.1 (notation), Eq. time division (N_*), Lemma Xlocation (walk). */
 typedef struct {
-  int dim;                  /* d in 1..5 (this build: 1, 2 and 5) */
+  int dim;                  /* d: 1, 2 or 5 (n_space <= 8 for d = 5) */
   int n_space;              /* JG(1,1) nodes = spatial modes per axis, 2..32 */
   int time_family;          /* SPMC_TIME_LGL or SPMC_TIME_RADAU_LEFT */
   int max_intervals;        /* largest interval count of any instance */

@@ -729,3 +729,446 @@ __global__ void adj_mu_kernel(const InstInterval* __restrict__ ii, const double*
 }
 
 }  // namespace spmc
+
+namespace spmc {
+
+// ----------------------------------------------------------------- d >= 3
+// Reconstruction in global memory, one axis per launch: out = M x_axis in, for
+// every active instance (blockIdx.y).  axis 0 is time (matrix B_n, row-major
+// [q][k]); axis e >= 1 is space axis e-1 (matrix A, [p][j]).  Blocks are
+// (M_n+1) x n^d FP64, time slowest, x_1 fastest.
+__global__ void mode_product_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ in_base,
+                                    long long in_is_U, double* __restrict__ out_base, const double* __restrict__ A,
+                                    const double* __restrict__ Bt, int n, int S, int axis) {
+  const InstInterval w = ii[blockIdx.y];
+  const int T = w.Mt + 1;
+  const long long tot = (long long)T * S;
+  const double* in = in_is_U ? in_base + w.u_off : in_base + w.c_off / 2;
+  double* out = out_base + w.c_off / 2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / S);
+    const int idx = (int)(i - (long long)q * S);
+    double acc = 0.0;
+    if (axis == 0) {
+      const double* B = Bt + w.b_off;
+      for (int k = 0; k < T; ++k) acc += B[q * T + k] * in[(long long)k * S + idx];
+    } else {
+      int stride = 1;
+      for (int e = 1; e < axis; ++e) stride *= n;
+      const int pe = (idx / stride) % n;
+      const long long base = (long long)q * S + idx - (long long)pe * stride;
+      for (int je = 0; je < n; ++je) acc += A[pe * n + je] * in[base + (long long)je * stride];
+    }
+    out[i] = acc;
+  }
+}
+
+// cu (final mode product) -> coefficient blocks: cu copied, ct by the
+// Legendre derivative identity.
+__global__ void coef_finish_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ src_base,
+                                   double* __restrict__ coef, int S) {
+  const InstInterval w = ii[blockIdx.y];
+  const int T = w.Mt + 1;
+  const long long tot = (long long)T * S;
+  const double* src = src_base + w.c_off / 2;
+  double* cu = coef + w.c_off;
+  double* ct = cu + tot;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / S);
+    const long long p = i - (long long)q * S;
+    cu[i] = src[i];
+    double acc = 0.0;
+    for (int l = q + 1; l < T; l += 2) acc += src[(long long)l * S + p];
+    ct[i] = (2.0 / w.h) * (2.0 * q + 1.0) * acc;
+  }
+}
+
+// Residual at y (d = 5, n <= 8) from a slice streamed through shared memory one
+// x_5 mode at a time: the caller stages tile t (C and H for p_5 = t, n^4 each,
+// x_1 fastest) and calls accumulate for every tile, then finish.  The
+// contraction is sum-factorised from x_1 to x_5 with three running states:
+// S0 (all phi), S1 (one psi, the Laplacian) and H (all phi, d_t part).
+template <typename R>
+struct Eval5 {
+  R ph[5][8], ps[5][8];
+  R s0, s1, hh;   // final contractions
+  __device__ __forceinline__ void init(int n, const R* y) {
+#pragma unroll
+    for (int e = 0; e < 5; ++e) basis<8, R>(n, y[e], ph[e], ps[e]);
+    s0 = R(0); s1 = R(0); hh = R(0);
+  }
+  // entry idx of a register array (runtime index without local memory)
+  static __device__ __forceinline__ R pick(const R* v, int idx) {
+    R out = v[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) out = (idx == k) ? v[k] : out;
+    return out;
+  }
+  // tile of p_5 = t: C[p1 + n p2 + n^2 p3 + n^3 p4], H likewise
+  __device__ __forceinline__ void accumulate(int n, int t, const R* __restrict__ C, const R* __restrict__ H) {
+    R a0 = R(0), a1 = R(0), ah = R(0);          // level 4 (over p4)
+    for (int p4 = 0; p4 < n; ++p4) {
+      R b0 = R(0), b1 = R(0), bh = R(0);        // level 3 (over p3)
+#pragma unroll
+      for (int p3 = 0; p3 < 8; ++p3) {
+        if (p3 < n) {
+          R c0 = R(0), c1 = R(0), ch = R(0);    // level 2 (over p2)
+#pragma unroll
+          for (int p2 = 0; p2 < 8; ++p2) {
+            if (p2 < n) {
+              const R* cr = C + ((p4 * n + p3) * n + p2) * n;
+              const R* hr = H + ((p4 * n + p3) * n + p2) * n;
+              R d0 = R(0), d1 = R(0), dh = R(0);   // level 1 (over p1)
+#pragma unroll
+              for (int p1 = 0; p1 < 8; ++p1) {
+                if (p1 < n) {
+                  const R cv = cr[p1];
+                  d0 += cv * ph[0][p1];
+                  d1 += cv * ps[0][p1];
+                  dh += hr[p1] * ph[0][p1];
+                }
+              }
+              c0 += d0 * ph[1][p2];
+              c1 += d1 * ph[1][p2] + d0 * ps[1][p2];
+              ch += dh * ph[1][p2];
+            }
+          }
+          b0 += c0 * ph[2][p3];
+          b1 += c1 * ph[2][p3] + c0 * ps[2][p3];
+          bh += ch * ph[2][p3];
+        }
+      }
+      const R f4 = pick(ph[3], p4), g4 = pick(ps[3], p4);
+      a0 += b0 * f4;
+      a1 += b1 * f4 + b0 * g4;
+      ah += bh * f4;
+    }
+    const R f5 = pick(ph[4], t), g5 = pick(ps[4], t);
+    s0 += a0 * f5;
+    s1 += a1 * f5 + a0 * g5;
+    hh += ah * f5;
+  }
+  // r = f(u*) + f_add + H - kappa (-Delta u*)
+  __device__ __forceinline__ R finish(const InstanceParams& ip, R kappa, const R* y, R Tt, R dTt) const {
+    return reaction<R>(ip, s0) + source<5, R>(ip, kappa, y, Tt, dTt) + hh - kappa * s1;
+  }
+};
+
+}  // namespace spmc
+
+namespace spmc {
+
+// Persistent sweep for d = 5 (n <= 8).  Cohorts, windows and walks as in
+// sweep_kernel; the evaluation differs: a slice (2 n^5 entries) does not fit in
+// shared memory, so each window runs rounds of
+//   (a) the pending evaluation point (Green point, roulette) of every walk
+//       pending in the window,
+//   (b) for each of the window's slices, all walks pending at it together: the
+//       slice streams through shared memory one x_5 mode (2 n^4 entries) at a
+//       time and every walk accumulates its sum-factorised contraction,
+//   (c) one step of every walk pending in the window,
+// until no walk is pending in the window.
+template <typename R>
+__global__ void __launch_bounds__(256)
+sweep5_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__ work_counter,
+              void* __restrict__ state_base, long long state_stride) {
+  constexpr int D = 5;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int S = a.S, n = a.n;
+  const int G = a.n_sub;
+  const long long slst = a.sl_stride;
+  const int half = a.half;
+  const int W = JT * CC;
+  const int n_jt = (S + JT - 1) / JT;
+  const int n4 = n * n * n * n;
+  R* tC = reinterpret_cast<R*>(smraw);                       // [2][n^4] tile
+  unsigned char* p = smraw + ((2 * n4 * sizeof(R) + 15) / 16) * 16;
+  int* mnext = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  int* act = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  int* ready = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  int* elist = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  int* eb = reinterpret_cast<int*>(p); p += W * sizeof(int);
+  R* ew = reinterpret_cast<R*>(p); p += W * sizeof(R);
+  R* eY = reinterpret_cast<R*>(p); p += 5 * W * sizeof(R);
+  __shared__ int red[64];
+  __shared__ double dred[32];
+  __shared__ int s_next, s_nact;
+  __shared__ double s_Tt[16], s_dTt[16];
+
+  unsigned char* gb = reinterpret_cast<unsigned char*>(state_base) + (long long)blockIdx.x * state_stride;
+  WalkState<D, R> st;
+#pragma unroll
+  for (int e = 0; e < D; ++e) { st.X[e] = reinterpret_cast<R*>(gb); gb += W * sizeof(R); }
+  st.f = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.w = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.r = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.S = reinterpret_cast<R*>(gb); gb += W * sizeof(R);
+  st.k = reinterpret_cast<int*>(gb); gb += W * sizeof(int);
+  st.q = reinterpret_cast<int*>(gb); gb += W * sizeof(int);
+  st.last = reinterpret_cast<int*>(gb); gb += W * sizeof(int);
+  st.mnext = mnext;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const R kappa = (R)a.kappa;
+  const R shell = (R)a.shell;
+  const R* slices = reinterpret_cast<const R*>(a.slices);
+  unsigned long long capped = 0, points = 0;
+  double dummy_acc = 0.0;
+
+  auto block_scan = [&](int cnt, int& base) -> int {
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+    for (int wv = 0; wv < nwarps; ++wv) {
+      if (wv < warp) wbase += red[wv];
+      total += red[wv];
+    }
+    __syncthreads();
+    base = wbase + incl - cnt;
+    return total;
+  };
+
+  while (true) {
+    if (threadIdx.x == 0) s_next = atomicAdd(work_counter, 1);
+    __syncthreads();
+    const long long id = s_next;
+    __syncthreads();
+    if (id >= n_cohorts) break;
+    long long b = id;
+    const int chunk = (int)(b % a.n_chunks);
+    b /= a.n_chunks;
+    const int jt = (int)(b % n_jt);
+    const long long ti = b / n_jt;
+    const TimeNode node = a.tn[ti];
+    const InstanceParams ip = a.ip[node.inst];
+    const int j0 = jt * JT;
+    const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
+    const R delta = Ar<R>::div(sdur, (R)node.nstar);
+    const R J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
+    const R sub = Ar<R>::div(delta, (R)G);
+    const int Ktot = G * node.nstar;
+    const uint32_t tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+                         (uint32_t)(a.iteration & 0x3ff);
+    const long long sample0 = (long long)chunk * CC;
+    WalkStream ws;
+    ws.k0 = a.k0; ws.k1 = a.k1; ws.tag = tag;
+
+    int cnt = 0;
+    for (int wk = threadIdx.x; wk < W; wk += blockDim.x) {
+      const int jj = wk / CC, s = wk - jj * CC;
+      const int j = j0 + jj;
+      st.S[wk] = R(0);
+      if (j >= S || sample0 + s >= a.M) { mnext[wk] = -1; continue; }
+      int jr = j;
+#pragma unroll
+      for (int e = 0; e < D; ++e) { st.X[e][wk] = (R)a.xnodes[jr % n]; jr /= n; }
+      st.f[wk] = R(0); st.k[wk] = 0; st.q[wk] = 0;
+      ws.node = (uint32_t)(node.ell * S + j);
+      ws.sample = (uint32_t)(sample0 + s);
+      prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps, dummy_acc, capped);
+      if (mnext[wk] >= 0) ++cnt;
+    }
+    __syncthreads();
+    {
+      int base;
+      const int tot = block_scan(cnt, base);
+      for (int wk = threadIdx.x; wk < W; wk += blockDim.x)
+        if (mnext[wk] >= 0) act[base++] = wk;
+      if (threadIdx.x == 0) s_nact = tot;
+      __syncthreads();
+    }
+    int m0 = 0;
+    const int max_passes = 2 * Ktot + 8;
+    int passes = 0;
+    while (s_nact > 0) {
+      const int nact = s_nact;
+      if (++passes > max_passes) {
+        if (threadIdx.x == 0) { atomicOr(a.status, 2); s_nact = 0; }
+        for (int i = threadIdx.x; i < nact; i += blockDim.x) mnext[act[i]] = -1;
+        __syncthreads();
+        break;
+      }
+      int rc = 0, mn = 0x7fffffff;
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) {
+        const int mv = mnext[act[i]];
+        if (mv < m0 + G) ++rc; else mn = min(mn, mv);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      if (lane == 0) red[32 + warp] = mn;
+      int rbase;
+      const int nready = block_scan(rc, rbase);
+      int gmin = 0x7fffffff;
+      for (int wv = 0; wv < nwarps; ++wv) gmin = min(gmin, red[32 + wv]);
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) {
+        const int wk = act[i];
+        if (mnext[wk] < m0 + G) ready[rbase++] = wk;
+      }
+      if (nready == 0) {
+        __syncthreads();
+        m0 = gmin;
+        continue;
+      }
+      if (threadIdx.x < G && m0 + (int)threadIdx.x < Ktot) {
+        SliceInfo si = a.sinfo[node.slice_base + m0 + threadIdx.x];
+        s_Tt[threadIdx.x] = si.Tt; s_dTt[threadIdx.x] = si.dTt;
+      }
+      __syncthreads();
+      int rounds = 0;
+      while (true) {
+        if (++rounds > a.max_steps + 8) {  // cannot happen: each round advances every pending walk by a step
+          if (threadIdx.x == 0) atomicOr(a.status, 2);
+          for (int i = threadIdx.x; i < nready; i += blockDim.x) mnext[ready[i]] = -1;
+          __syncthreads();
+          break;
+        }
+        // (a) pending evaluation points
+        for (int i = threadIdx.x; i < nready; i += blockDim.x) {
+          const int wk = ready[i];
+          const int mv = mnext[wk];
+          eb[wk] = -1;
+          if (!(mv >= m0 && mv < m0 + G)) continue;
+          const int jj = wk / CC;
+          ws.node = (uint32_t)(node.ell * S + j0 + jj);
+          ws.sample = (uint32_t)(sample0 + (wk - jj * CC));
+          const int q = st.q[wk];
+          constexpr int WS = step_words(D);
+          const uint32_t w0 = (uint32_t)q * WS;
+          const R r = st.r[wk];
+          R w = st.w[wk];
+          if (r < J && w > R(0)) {
+            const uint32_t rw = stream_word(ws, w0 + rword_index(D));
+            const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
+            w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
+          }
+          if (w > R(0)) {
+            R thg[D];
+            direction<D, R>(ws, w0 + dir_words(D), thg);
+            const uint32_t wr = w0 + 2 * dir_words(D);
+            Philox4 rb = ws.block(wr >> 2);
+            const R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
+            const R v = green_radius<D, R>(U1, R(0));
+            const R rv = Ar<R>::mul(r, v);
+#pragma unroll
+            for (int e = 0; e < D; ++e) eY[e * W + wk] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(rv, thg[e]));
+            ew[wk] = w;
+            eb[wk] = mv - m0;
+          }
+        }
+        __syncthreads();
+        // (b) evaluations, slice by slice
+        for (int bs = 0; bs < G; ++bs) {
+          if (m0 + bs >= Ktot) break;
+          int ec = 0;
+          for (int i = threadIdx.x; i < nready; i += blockDim.x) ec += (eb[ready[i]] == bs);
+          int ebase;
+          const int ne = block_scan(ec, ebase);
+          for (int i = threadIdx.x; i < nready; i += blockDim.x)
+            if (eb[ready[i]] == bs) elist[ebase++] = ready[i];
+          __syncthreads();
+          if (ne == 0) continue;
+          const R* sl = slices + (node.slice_base + m0 + bs) * slst;
+          for (int c0 = 0; c0 < ne; c0 += blockDim.x) {
+            const int i = c0 + threadIdx.x;
+            const bool has = i < ne;
+            const int wk = has ? elist[i] : 0;
+            Eval5<R> ev;
+            R Y[D];
+            if (has) {
+#pragma unroll
+              for (int e = 0; e < D; ++e) Y[e] = eY[e * W + wk];
+              ev.init(n, Y);
+            }
+            for (int t5 = 0; t5 < n; ++t5) {
+              __syncthreads();
+              for (int x = threadIdx.x; x < n4; x += blockDim.x) {
+                tC[x] = sl[(long long)t5 * n4 + x];
+                tC[n4 + x] = sl[half + (long long)t5 * n4 + x];
+              }
+              __syncthreads();
+              if (has) ev.accumulate(n, t5, tC, tC + n4);
+            }
+            if (has) {
+              const R res = ev.finish(ip, kappa, Y, (R)s_Tt[bs], (R)s_dTt[bs]);
+              st.S[wk] += ew[wk] * res;
+              ++points;
+            }
+          }
+          __syncthreads();
+        }
+        // (c) one step of every walk pending in the window
+        int pend = 0;
+        for (int i = threadIdx.x; i < nready; i += blockDim.x) {
+          const int wk = ready[i];
+          int mv = mnext[wk];
+          if (!(mv >= m0 && mv < m0 + G)) continue;
+          if (st.last[wk]) { mnext[wk] = -1; continue; }
+          const int jj = wk / CC;
+          ws.node = (uint32_t)(node.ell * S + j0 + jj);
+          ws.sample = (uint32_t)(sample0 + (wk - jj * CC));
+          const int q = st.q[wk];
+          constexpr int WS = step_words(D);
+          const uint32_t w0 = (uint32_t)q * WS;
+          const R r = st.r[wk];
+          R th[D];
+          direction<D, R>(ws, w0, th);
+#pragma unroll
+          for (int e = 0; e < D; ++e) st.X[e][wk] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(r, th[e]));
+          st.q[wk] = q + 1;
+          prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps,
+                             dummy_acc, capped);
+          mv = mnext[wk];
+          pend += (mv >= m0 && mv < m0 + G);
+        }
+        if (!__syncthreads_or(pend)) break;
+      }
+      // compact the active list
+      int kc = 0;
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) kc += (mnext[act[i]] >= 0);
+      int kbase;
+      const int nkeep = block_scan(kc, kbase);
+      for (int i = threadIdx.x; i < nact; i += blockDim.x) {
+        const int wk = act[i];
+        if (mnext[wk] >= 0) ready[kbase++] = wk;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < nkeep; i += blockDim.x) act[i] = ready[i];
+      if (threadIdx.x == 0) s_nact = nkeep;
+      __syncthreads();
+      m0 += G;
+    }
+    for (int jj = 0; jj < JT; ++jj) {
+      const int j = j0 + jj;
+      if (j >= S) break;
+      double t = 0.0;
+      for (int s = threadIdx.x; s < CC; s += blockDim.x) t += (double)st.S[jj * CC + s];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) dred[warp] = t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tt = 0.0;
+        for (int wv = 0; wv < nwarps; ++wv) tt += dred[wv];
+        a.partial[(ti * S + j) * a.n_chunks + chunk] = tt;
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    points += __shfl_xor_sync(0xffffffffu, points, o);
+    capped += __shfl_xor_sync(0xffffffffu, capped, o);
+  }
+  if (lane == 0) {
+    if (points) atomicAdd(&a.counters[0], points);
+    if (capped) atomicAdd(&a.counters[1], capped);
+  }
+}
+
+}  // namespace spmc

@@ -69,6 +69,7 @@ struct spmc_plan_s {
   double* d_u0 = nullptr;
   double* d_U = nullptr;
   double* d_coef = nullptr;
+  double* d_rec = nullptr;       // d >= 3: two reconstruction buffers of coef_cap / 2 each
   void* d_slices = nullptr;
   SliceInfo* d_sinfo = nullptr;
   double* d_partial = nullptr;
@@ -145,6 +146,7 @@ void slice_geometry(spmc_plan_t plan) {
   const int n = plan->d.n_space;
   int row = 32;
   if (plan->d.dim == 2) row = n <= 8 ? 8 : (n <= 16 ? 16 : (n <= 24 ? 24 : 32));
+  if (plan->d.dim >= 3) row = plan->S;
   plan->row = row;
   plan->half = plan->d.dim == 2 ? n * row : row;
   long long SL = 2LL * plan->half;
@@ -251,6 +253,9 @@ spmc_status build(spmc_plan_t plan) {
   size_t rsz = d.precision == SPMC_FP64 ? sizeof(double) : sizeof(float);
   SPMC_CUDA(cudaMalloc((void**)&plan->d_U, sizeof(double) * std::max(1LL, plan->U_total)));
   SPMC_CUDA(cudaMalloc((void**)&plan->d_coef, sizeof(double) * std::max(1LL, coef_cap)));
+  cudaFree(plan->d_rec);
+  plan->d_rec = nullptr;
+  if (d.dim >= 3) SPMC_CUDA(cudaMalloc((void**)&plan->d_rec, sizeof(double) * std::max(1LL, coef_cap)));
   slice_geometry(plan);
   SPMC_CUDA(cudaMalloc(&plan->d_slices, rsz * plan->sl_stride * std::max(1LL, slice_cap)));
   SPMC_CUDA(cudaMalloc((void**)&plan->d_sinfo, sizeof(SliceInfo) * std::max(1LL, slice_cap)));
@@ -351,8 +356,67 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
 }
 
 template <typename R>
+spmc_status launch_sweep5(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const spmc_plan_desc& d = plan->d;
+  SweepArgs a;
+  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
+  a.partial = plan->d_partial; a.counters = plan->d_counters; a.status = plan->d_status;
+  a.n = d.n_space; a.S = plan->S;
+  a.chunk = plan->chunk;
+  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
+  a.n_sub = d.n_sub;
+  int gb = 0;
+  while ((1 << gb) < d.n_sub) ++gb;
+  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
+  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
+  a.interval = interval; a.iteration = iteration;
+  a.M = d.M;
+  a.sl_stride = plan->sl_stride;
+  a.half = plan->half;
+  const int JT = std::max(1, std::min(plan->JT, plan->S));
+  const int W = JT * plan->chunk;
+  const long long n_jt = (plan->S + JT - 1) / JT;
+  const long long n_cohorts = (long long)rd.tn.size() * n_jt * a.n_chunks;
+  if (n_cohorts <= 0) return SPMC_OK;
+  const int n4 = d.n_space * d.n_space * d.n_space * d.n_space;
+  size_t smem = ((2 * (size_t)n4 * sizeof(R) + 15) / 16) * 16 + (size_t)W * (5 * sizeof(int) + 6 * sizeof(R)) + 16;
+  auto kern = sweep5_kernel<R>;
+  SPMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, plan->threads, smem));
+  if (occ < 1) return fail(plan, SPMC_ERR_UNSUPPORTED, "5-D sweep configuration does not fit on an SM");
+  long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
+  const size_t stride = state_stride_bytes(5, W, sizeof(R));
+  if (plan->state_bytes < stride * grid) {
+    cudaFree(plan->d_state);
+    plan->d_state = nullptr;
+    plan->state_bytes = 0;
+    SPMC_CUDA(cudaMalloc(&plan->d_state, stride * grid));
+    plan->state_bytes = stride * grid;
+  }
+  SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (plan->timing) {
+    if (!plan->ev_free.empty()) { ev = plan->ev_free.back(); plan->ev_free.pop_back(); }
+    else { SPMC_CUDA(cudaEventCreate(&ev.first)); SPMC_CUDA(cudaEventCreate(&ev.second)); }
+    SPMC_CUDA(cudaEventRecord(ev.first, stream));
+  }
+  kern<<<(unsigned)grid, plan->threads, smem, stream>>>(a, JT, plan->chunk, n_cohorts, plan->d_work, plan->d_state,
+                                                         (long long)stride);
+  SPMC_CUDA(cudaGetLastError());
+  if (plan->timing) {
+    SPMC_CUDA(cudaEventRecord(ev.second, stream));
+    plan->ev_pending.push_back(ev);
+  }
+  return SPMC_OK;
+}
+
+template <typename R>
 spmc_status dispatch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
   const int n = plan->d.n_space;
+  if (plan->d.dim == 5) return launch_sweep5<R>(plan, stream, rd, interval, iteration);
   if (plan->d.dim == 1) return launch_sweep<1, 32, R>(plan, stream, rd, interval, iteration);
   if (plan->d.dim == 2) {
     if (n <= 8) return launch_sweep<2, 8, R>(plan, stream, rd, interval, iteration);
@@ -367,6 +431,28 @@ spmc_status dispatch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& r
 spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
   if (rd.ii.empty()) return SPMC_OK;
+  if (D >= 3) {
+    // reconstruction in global memory: time axis, then each space axis
+    const long long half_cap = plan->coef_cap / 2;
+    double* buf[2] = {plan->d_rec, plan->d_rec + half_cap};
+    dim3 grid(256, (unsigned)rd.ii.size());
+    mode_product_kernel<<<grid, 256, 0, stream>>>(rd.d_ii, plan->d_U, 1, buf[0], plan->d_A, plan->d_B, n, S, 0);
+    int cur = 0;
+    for (int e = 1; e <= D; ++e) {
+      mode_product_kernel<<<grid, 256, 0, stream>>>(rd.d_ii, buf[cur], 0, buf[1 - cur], plan->d_A, plan->d_B, n, S, e);
+      cur = 1 - cur;
+    }
+    coef_finish_kernel<<<grid, 256, 0, stream>>>(rd.d_ii, buf[cur], plan->d_coef, S);
+    SPMC_CUDA(cudaGetLastError());
+    if (rd.n_slices > 0) {
+      if (plan->d.precision == SPMC_FP64)
+        slice_kernel<5, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      else
+        slice_kernel<5, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      SPMC_CUDA(cudaGetLastError());
+    }
+    return SPMC_OK;
+  }
   int maxT = 0;
   for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
   size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
@@ -459,33 +545,12 @@ spmc_status dispatch_adjoint(spmc_plan_t plan, cudaStream_t stream, const Round&
 // One residual iteration on interval r for every instance that has it.
 spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   Round& rd = plan->rounds[r];
-  const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
+  const int S = plan->S;
   const int iteration = ++rd.iteration;
   if (rd.ii.empty()) return SPMC_OK;
-  int maxT = 0;
-  for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
-  size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
-  if (D == 1) {
-    SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
-                                                                          plan->d_coef, n);
-  } else {
-    SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
-                                                                          plan->d_coef, n);
-  }
-  SPMC_CUDA(cudaGetLastError());
+  spmc_status pst = prepare_slices(plan, stream, rd);
+  if (pst != SPMC_OK) return pst;
   bool fp64 = plan->d.precision == SPMC_FP64;
-  if (rd.n_slices > 0) {
-    if (D == 1) {
-      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-    } else {
-      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-    }
-    SPMC_CUDA(cudaGetLastError());
-  }
   spmc_status st = fp64 ? dispatch_sweep<double>(plan, stream, rd, r, iteration)
                         : dispatch_sweep<float>(plan, stream, rd, r, iteration);
   if (st != SPMC_OK) return st;
@@ -701,8 +766,9 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
       (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
       (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL)
     return SPMC_ERR_INVALID;
-  if (d.dim > 2) return SPMC_ERR_UNSUPPORTED;
-  {
+  if (d.dim != 1 && d.dim != 2 && d.dim != 5) return SPMC_ERR_UNSUPPORTED;
+  if (d.dim == 5 && d.n_space > 8) return SPMC_ERR_UNSUPPORTED;
+  if (d.dim <= 2) {
     // the reconstruction keeps two (M_n+1) x n^d FP64 blocks in shared memory
     double S = std::pow((double)d.n_space, d.dim);
     if (2.0 * (d.max_degree + 1) * S * 8.0 > 227.0 * 1024.0) return SPMC_ERR_UNSUPPORTED;
@@ -715,6 +781,10 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   plan->probs.assign(d.batch, HostProblem());
   plan->chunk = (int)std::min<long long>(d.precision == SPMC_FP64 ? 256 : 512, ((d.M + 31) / 32) * 32);
   plan->JT = (d.precision == SPMC_FP64 ? 4096 : 6144) / plan->chunk;
+  if (d.dim == 5) {
+    plan->chunk = (int)std::min<long long>(256, ((d.M + 31) / 32) * 32);
+    plan->JT = 4;
+  }
   slice_geometry(plan);
   plan->threads = 256;
   // tables
@@ -906,6 +976,7 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
   if (!plan) return SPMC_ERR_INVALID;
   if (!plan->built || plan->params_dirty)
     return fail(plan, SPMC_ERR_INVALID, "spmc_iterate_static needs a built plan: call spmc_begin_interval first");
+  if (plan->d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_iterate_static: dimensions 1 and 2 only");
   if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   Round& rd = plan->rounds[interval];
@@ -987,6 +1058,7 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
   const int S = plan->S, n = d.n_space, D = d.dim, B = d.batch, K = d.K;
   const int R = (int)plan->rounds.size();
   if (d.tol > 0.0) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad needs a fixed iteration count (tol <= 0)");
+  if (d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: dimensions 1 and 2 only");
   // workspace (first call)
   if (!plan->grad_ready) {
     cudaFree(plan->d_lambda); cudaFree(plan->d_Ubak); cudaFree(plan->d_iter); cudaFree(plan->d_gT);
@@ -1108,7 +1180,7 @@ spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, dou
   spmc_status st = prepare_slices(plan, s, rd);
   if (st != SPMC_OK) return st;
   // candidate cohort widths that fit two blocks per SM (FP32) / one (FP64)
-  const int wmax = fp64 ? 4096 : 6144;
+  const int wmax = plan->d.dim == 5 ? 2048 : (fp64 ? 4096 : 6144);
   const int cands[] = {1, 2, 4, 6, 8, 12, 16, 24, 32};
   cudaEvent_t e0, e1;
   SPMC_CUDA(cudaEventCreate(&e0));
@@ -1169,7 +1241,7 @@ void spmc_destroy(spmc_plan_t plan) {
   for (auto& ev : plan->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   for (auto& r : plan->rounds) { cudaFree(r.d_tn); cudaFree(r.d_ii); cudaFree(r.d_ii_of_node); cudaFree(r.d_slice_node); }
   cudaFree(plan->d_x); cudaFree(plan->d_A); cudaFree(plan->d_B); cudaFree(plan->d_hw); cudaFree(plan->d_ip);
-  cudaFree(plan->d_u0); cudaFree(plan->d_U); cudaFree(plan->d_coef); cudaFree(plan->d_slices);
+  cudaFree(plan->d_u0); cudaFree(plan->d_U); cudaFree(plan->d_coef); cudaFree(plan->d_slices); cudaFree(plan->d_rec);
   cudaFree(plan->d_sinfo); cudaFree(plan->d_partial); cudaFree(plan->d_counters); cudaFree(plan->d_maxeps);
   cudaFree(plan->d_status);
   cudaFree(plan->d_work);

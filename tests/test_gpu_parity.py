@@ -154,3 +154,35 @@ def test_polynomial_fixed_point_full_size(api, precision, M):
     after = plan.get_nodes(0, 0).cpu().numpy()
     assert np.abs(after - exact).max() < tol
     plan.close()
+
+
+def test_fp64_5d_stepwise(O, api):
+    """d = 5 (the 5-D workload's shape at 3 nodes per axis): stepwise parity."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w4(M=48, K=2, n_space=3, degree=2)
+    wl.n_ref = 6
+    for g, r in _stepwise(O, api, wl, 2):
+        assert np.all(np.abs(g - r) <= parity_tol(r)), np.abs(g - r).max()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-4)])
+def test_5d_polynomial_fixed_point_full_geometry(api, precision, tol):
+    """The 5-D workload's full node geometry (8^5 JG x 8 LGL): an exactly
+    representable solution is a fixed point (eps = 0 at every node)."""
+    import scipy.special as sps
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w4(M=32, K=1)
+    inst = wl.instances[0]
+    inst.ex_kind = W.EX_POLY
+    plan = api.Plan.from_workload(wl, precision=precision)
+    grid = plan.node_grid()
+    Mt = int(inst.degrees[0])
+    xi = np.concatenate([[-1.0], sps.roots_jacobi(Mt - 1, 1.0, 1.0)[0], [1.0]])
+    t = (xi + 1.0) * 0.5 * 0.5
+    g = np.prod((1.0 - grid ** 2) * (1.0 + grid), axis=1)
+    exact = (1.0 + t + t * t)[:, None] * g[None, :]
+    plan.begin_interval(0)
+    plan.set_nodes(0, 0, torch.from_numpy(exact))
+    mx = plan.iterate(0, 1)
+    assert mx < tol, mx
+    plan.close()
