@@ -175,6 +175,24 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
 spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_du_T,
                       double* grad_f_scale, double* grad_u0_coef);
 
+/* Forward-sweep strategy for d <= 2 (d = 5, spmc_grad and spmc_iterate_static
+ * always use the cohort kernel):
+ *   SPMC_SWEEP_EVENTS (default): per batch of `batch` samples, the walks run
+ *     twice (count, then fill) and write their evaluation events (Green point,
+ *     weight, node) grouped by time slice; one block per slice then evaluates
+ *     all of them against the slice staged once in shared memory.  Per-event
+ *     terms are summed in FP64.  Device memory: 16 (FP32) or 32 (FP64) bytes per
+ *     event of a batch, allocated on first use and kept.  batch <= 0 picks about
+ *     2^26 walks per batch.
+ *   SPMC_SWEEP_COHORT: the persistent cohort kernel; a walk's terms are summed
+ *     in the sweep precision, then in FP64 per chunk.
+ * The two give the same walks and the same points; only summation order and,
+ * in SPMC_MIXED, the per-walk FP32 partial sums differ.  Returns
+ * SPMC_ERR_INVALID for an unknown mode. */
+#define SPMC_SWEEP_EVENTS 0
+#define SPMC_SWEEP_COHORT 1
+spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch);
+
 /* Enable (1) or disable (0) CUDA-event timing of every sweep kernel launch; the
  * totals accumulate in spmc_stats.sweep_ms / sweep_launches (reset on enable). */
 spmc_status spmc_set_timing(spmc_plan_t plan, int enable);

@@ -20,6 +20,7 @@ FP64, MIXED = 0, 1
 F_POLY3, F_SIN = 0, 1
 EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
 U0_NODAL, U0_PHI_COEF = 0, 1
+SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT = 0, 1
 
 
 class PlanDesc(C.Structure):
@@ -60,6 +61,7 @@ _SIGNATURES = {
     "spmc_iterate_static": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spmc_set_timing": (C.c_int, [_PLAN, C.c_int]),
+    "spmc_set_sweep": (C.c_int, [_PLAN, C.c_int, C.c_longlong]),
     "spmc_autotune": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_space_nodes": (C.c_int, [_PLAN, C.POINTER(C.c_double)]),
     "spmc_get_stats": (C.c_int, [_PLAN, C.POINTER(Stats)]),

@@ -185,6 +185,11 @@ class Plan:
         L.check(L.lib.spmc_autotune(self._h, C.c_void_p(_stream_ptr(stream)), interval, C.byref(ms)), self._h)
         return ms.value
 
+    def set_sweep(self, mode: str = "events", batch: int = 0):
+        """Forward-sweep strategy for d <= 2: "events" (default) or "cohort"."""
+        m = {"events": L.SPMC_SWEEP_EVENTS, "cohort": L.SPMC_SWEEP_COHORT}[mode]
+        L.check(L.lib.spmc_set_sweep(self._h, m, int(batch)), self._h)
+
     def set_timing(self, enable: bool):
         L.check(L.lib.spmc_set_timing(self._h, 1 if enable else 0), self._h)
 

@@ -1,0 +1,330 @@
+// spmc_events.cuh -- the forward sweep as an event pipeline (d = 1, 2).
+//
+// The time slices depend only on (instance, time node, sub-point), not on the
+// spatial node, so the residual evaluations of one slice can be done together
+// for every node and sample of its time node.  Per batch of samples:
+//   walk_events_kernel<COUNT>  every walk runs its steps (Lemma Xlocation,
+//                              inside balls, roulette) and counts its
+//                              evaluation events per (slice, spatial node);
+//   scan kernels               exclusive offsets of the (slice, node) segments;
+//   walk_events_kernel<FILL>   the same walks again (pure functions of their
+//                              Philox streams) write each event (Green point,
+//                              weight) into its segment;
+//   eval_events_kernel         one block per slice stages the slice once in
+//                              shared memory and evaluates all its events; the
+//                              weighted residuals are summed per node in FP64.
+// The per-node sums feed the update kernel (eps = sum / M).
+#pragma once
+#include "spmc_kernels.cuh"
+
+namespace spmc {
+
+template <typename R>
+struct Event {
+  R y[2];
+  R w;
+  int j;
+};
+
+struct EventArgs {
+  const TimeNode* tn;
+  const double* xnodes;
+  unsigned int* counts;          // (slice, node) counters / fill cursors
+  void* events;                  // Event<R>[]
+  int n, S, n_sub, gbits, max_steps, interval, iteration;
+  long long n_tn;
+  long long i0, nb;              // sample range of the batch
+  double kappa, shell;
+  uint32_t k0, k1;
+  unsigned long long* counters;  // [0] points, [1] capped
+  unsigned long long cap;        // events the buffer holds (FILL)
+  int* status;                   // bit 4: an event fell outside its segment
+};
+
+// Every walk of the batch, lane by lane: a lane takes the next walk when its
+// current one ends, so the lanes of a warp stay busy.  Walk ids run sample
+// fastest (consecutive lanes share a node and mostly a slice).
+template <int D, typename R, bool FILL>
+__global__ void __launch_bounds__(256) walk_events_kernel(EventArgs a) {
+  const long long total = a.n_tn * a.S * a.nb;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long wid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int S = a.S, n = a.n, G = a.n_sub;
+  const R kappa = (R)a.kappa, shell = (R)a.shell;
+  Event<R>* ev = reinterpret_cast<Event<R>*>(a.events);
+  unsigned long long capped = 0, points = 0;
+
+  // walk state
+  bool live = false;
+  R X[D], f = R(0), delta = R(0), J = R(0), sub = R(0);
+  int k = 0, q = 0, Ktot = 0, j = 0;
+  long long slice_base = 0;
+  WalkStream ws;
+  ws.k0 = a.k0; ws.k1 = a.k1;
+  constexpr int WS = step_words(D);
+  while (true) {
+    if (!live) {
+      if (wid >= total) break;
+      const long long ti = wid / ((long long)S * a.nb);
+      const long long rem = wid - ti * (long long)S * a.nb;
+      j = (int)(rem / a.nb);
+      const long long i = a.i0 + (rem - (long long)j * a.nb);
+      wid += stride;
+      const TimeNode node = a.tn[ti];
+      const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
+      delta = Ar<R>::div(sdur, (R)node.nstar);
+      J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
+      sub = Ar<R>::div(delta, (R)G);
+      Ktot = G * node.nstar;
+      slice_base = node.slice_base;
+      int jr = j;
+#pragma unroll
+      for (int e = 0; e < D; ++e) { X[e] = (R)a.xnodes[jr % n]; jr /= n; }
+      f = R(0); k = 0; q = 0;
+      ws.node = (uint32_t)(node.ell * S + j);
+      ws.sample = (uint32_t)i;
+      ws.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+               (uint32_t)(a.iteration & 0x3ff);
+      live = true;
+    }
+    // ---- one step, as the CPU reference: absorb, ball, weight, sub-point
+    R dist = R(1);
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      R de = Ar<R>::sub(R(1), fabs(X[e]));
+      if (de < dist) dist = de;
+    }
+    if (q >= a.max_steps || dist < shell) {
+      if (q >= a.max_steps) ++capped;
+      live = false;
+      continue;
+    }
+    const uint32_t w0 = (uint32_t)q * WS;
+    const Philox4 bg = ws.block((w0 + gword_index(D)) >> 2);
+    const uint32_t gword = bg.v[(w0 + gword_index(D)) & 3];
+    const int g = a.gbits ? (int)(gword >> (32 - a.gbits)) : 0;
+    R left = Ar<R>::sub(Ar<R>::mul((R)(Ktot - k), sub), f);
+    R w, r;
+    int m, last = 0;
+    if (J <= dist) {
+      r = J;
+      w = delta;
+      if (k + G >= Ktot) {
+        const int ahead = Ktot - k;
+        m = k + (a.gbits ? (int)(((unsigned long long)gword * (unsigned long long)ahead) >> 32) : 0);
+        w = left;
+        last = 1;
+      } else {
+        m = k + g;
+        k += G;
+      }
+    } else {
+      r = dist;
+      w = Ar<R>::div(Ar<R>::mul(r, r), Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa));
+      m = k;
+      if (w >= left) { w = left; last = 1; }
+      else {
+        f = Ar<R>::add(f, w);
+        while (f >= sub) { f = Ar<R>::sub(f, sub); ++k; }
+        if (k >= Ktot) last = 1;
+      }
+    }
+    // roulette for shrunk balls (the roulette word shares the sub-point word's block)
+    if (r < J && w > R(0)) {
+      const uint32_t rw = bg.v[(w0 + rword_index(D)) & 3];
+      const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
+      w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
+    }
+    const Philox4 b0 = ws.block(w0 >> 2);   // next-step and Green directions (d <= 2: one block)
+    if (w > R(0)) {
+      R thg[D];
+      if (D == 1) {
+        thg[0] = (b0.v[(w0 + dir_words(D)) & 3] >> 31) ? R(-1) : R(1);
+      } else {
+        const uint32_t o = (w0 + dir_words(D)) & 3;
+        const R U = U01<R>::pair(b0.v[o], b0.v[o + 1]);
+        R sn, cs;
+        Ar<R>::sincos2pi(U, &sn, &cs);
+        thg[0] = cs; thg[1] = sn;
+      }
+      const uint32_t wr = w0 + 2 * dir_words(D);
+      const Philox4 rb = (D == 1) ? b0 : ws.block(wr >> 2);
+      const R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
+      const R U2 = (D == 2) ? U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]) : R(0);
+      const R v = green_radius<D, R>(U1, U2);
+      const R rv = Ar<R>::mul(r, v);
+      const unsigned int key = (unsigned int)((slice_base + m) * S + j);
+      if (!FILL) {
+        atomicAdd(&a.counts[key], 1u);
+      } else {
+        const unsigned int slot = atomicAdd(&a.counts[key], 1u);
+        if ((unsigned long long)slot < a.cap) {
+          Event<R> e;
+          e.y[0] = Ar<R>::add(X[0], Ar<R>::mul(rv, thg[0]));
+          e.y[1] = (D == 2) ? Ar<R>::add(X[1], Ar<R>::mul(rv, thg[1])) : R(0);
+          e.w = w;
+          e.j = j;
+          ev[slot] = e;
+        } else {
+          atomicOr(a.status, 4);   // cannot happen: both passes take the same walks
+        }
+        ++points;
+      }
+    }
+    if (last) { live = false; continue; }
+    // step to the sphere of the ball
+    if (D == 1) {
+      const R th = (b0.v[w0 & 3] >> 31) ? R(-1) : R(1);
+      X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, th));
+    } else {
+      const R U = U01<R>::pair(b0.v[w0 & 3], b0.v[(w0 & 3) + 1]);
+      R sn, cs;
+      Ar<R>::sincos2pi(U, &sn, &cs);
+      X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, cs));
+      X[D - 1] = Ar<R>::add(X[D - 1], Ar<R>::mul(r, sn));
+    }
+    ++q;
+  }
+  if (FILL) {
+    for (int o = 16; o > 0; o >>= 1) {
+      points += __shfl_xor_sync(0xffffffffu, points, o);
+      capped += __shfl_xor_sync(0xffffffffu, capped, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (points) atomicAdd(&a.counters[0], points);
+      if (capped) atomicAdd(&a.counters[1], capped);
+    }
+  }
+}
+
+// Exclusive scan of n unsigned counts in place, in three launches (block scans
+// of 1024 entries, a scan of the block totals, the add-back).
+__global__ void scan_blocks_kernel(unsigned int* __restrict__ v, unsigned long long* __restrict__ bsum, long long n) {
+  __shared__ unsigned int tmp[1024];
+  __shared__ unsigned int wsum[32];
+  const long long base = (long long)blockIdx.x * 1024;
+  unsigned int x[4];
+  const int t = threadIdx.x;   // 256 threads x 4 entries
+  unsigned int s = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long i = base + t * 4 + u;
+    x[u] = i < n ? v[i] : 0u;
+    s += x[u];
+  }
+  // inclusive scan of s over the block
+  unsigned int incl = s;
+  const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  unsigned int wbase = 0, tot = 0;
+  for (int wv = 0; wv < 8; ++wv) { if (wv < warp) wbase += wsum[wv]; tot += wsum[wv]; }
+  unsigned int run = wbase + incl - s;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long long i = base + t * 4 + u;
+    if (i < n) v[i] = run;
+    run += x[u];
+  }
+  if (t == 0) bsum[blockIdx.x] = tot;
+  (void)tmp;
+}
+
+// exclusive scan of the block totals (one block, serial chunks)
+__global__ void scan_totals_kernel(unsigned long long* __restrict__ bsum, long long nb, unsigned long long* total) {
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ unsigned long long wsum[32];
+  for (long long c0 = 0; c0 < nb; c0 += blockDim.x) {
+    const long long i = c0 + threadIdx.x;
+    const unsigned long long s = i < nb ? bsum[i] : 0ull;
+    unsigned long long incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    unsigned long long wbase = 0, tot = 0;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) { if (wv < warp) wbase += wsum[wv]; tot += wsum[wv]; }
+    if (i < nb) bsum[i] = carry + wbase + incl - s;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_add_kernel(unsigned int* __restrict__ v, const unsigned long long* __restrict__ bsum,
+                                unsigned int* __restrict__ starts, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const unsigned int o = v[i] + (unsigned int)bsum[i / 1024];
+    v[i] = o;
+    starts[i] = o;
+  }
+}
+
+// One block per slice: stage the slice, evaluate its events, sum w r per node.
+template <int D, int NMAX, typename R>
+__global__ void __launch_bounds__(256) eval_events_kernel(const long long* __restrict__ slice_node,
+                                                          const TimeNode* __restrict__ tn,
+                                                          const InstanceParams* __restrict__ ipt,
+                                                          const void* __restrict__ slices_v,
+                                                          const SliceInfo* __restrict__ sinfo,
+                                                          const unsigned int* __restrict__ starts,
+                                                          const void* __restrict__ events_v,
+                                                          double* __restrict__ acc, int n, int S,
+                                                          long long sl_stride, int half, double kappa_d,
+                                                          unsigned long long n_events) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sC = reinterpret_cast<R*>(smraw);
+  const long long sidx = blockIdx.x;
+  const unsigned int e0 = starts[sidx * S];
+  const unsigned long long e1 = (sidx + 1 < (long long)gridDim.x) ? starts[(sidx + 1) * S] : n_events;
+  if ((unsigned long long)e0 >= e1) return;
+  const R* src = reinterpret_cast<const R*>(slices_v) + sidx * sl_stride;
+  for (int i = threadIdx.x; i < (int)sl_stride; i += blockDim.x) sC[i] = src[i];
+  const long long ti = slice_node[sidx];
+  const TimeNode node = tn[ti];
+  const InstanceParams ip = ipt[node.inst];
+  const SliceInfo si = sinfo[sidx];
+  const R kappa = (R)kappa_d;
+  __syncthreads();
+  const Event<R>* ev = reinterpret_cast<const Event<R>*>(events_v);
+  const unsigned int lane = threadIdx.x & 31;
+  for (unsigned long long base = e0; base < e1; base += blockDim.x) {
+    const unsigned long long i = base + threadIdx.x;
+    const bool has = i < e1;
+    double val = 0.0;
+    int jv = -1;
+    if (has) {
+      const Event<R> e = ev[i];
+      R Y[D];
+      Y[0] = e.y[0];
+      if (D == 2) Y[1] = e.y[1];
+      const R res = residual_at<D, NMAX, R>(ip, kappa, n, sC, sC + half, Y, (R)si.Tt, (R)si.dTt);
+      val = (double)(e.w * res);
+      jv = e.j;
+    }
+    // segmented warp sum by node (events of a node are contiguous)
+    const unsigned int same = __match_any_sync(0xffffffffu, jv);
+    const int leader = __ffs(same) - 1;
+    double sum = 0.0;
+    for (unsigned int mm = same; mm; mm &= mm - 1) {
+      const int src_lane = __ffs(mm) - 1;
+      sum += __shfl_sync(same, val, src_lane);
+    }
+    if (has && (int)lane == leader) atomicAdd(&acc[ti * S + jv], sum);
+  }
+}
+
+}  // namespace spmc

@@ -14,6 +14,7 @@
 
 #include "spmc.h"
 #include "spmc_kernels.cuh"
+#include "spmc_events.cuh"
 #include "spmc_tables.h"
 
 using namespace spmc;
@@ -57,6 +58,18 @@ struct spmc_plan_s {
   int* d_work = nullptr;             // persistent-kernel work counter
   void* d_state = nullptr;           // block-private walk state regions
   size_t state_bytes = 0;
+  // event pipeline (forward sweep, d <= 2)
+  int sweep_mode = 0;                // 0: event pipeline, 1: cohort kernel
+  long long ev_batch = 0;            // samples per batch (0: automatic)
+  unsigned int* d_counts = nullptr;  // (slice, node) counters / cursors
+  unsigned int* d_starts = nullptr;  // segment starts
+  unsigned long long* d_bsum = nullptr;
+  unsigned long long* d_total = nullptr;
+  long long counts_cap = 0, bsum_cap = 0;
+  void* d_events = nullptr;
+  size_t events_bytes = 0;
+  double* d_acc = nullptr;           // per (time node, node) FP64 sums
+  long long acc_cap = 0;
   std::vector<HostProblem> probs;
   bool built = false;
   std::vector<double> xnodes;
@@ -542,6 +555,107 @@ spmc_status dispatch_adjoint(spmc_plan_t plan, cudaStream_t stream, const Round&
   return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
 }
 
+template <int D, typename R>
+spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const spmc_plan_desc& d = plan->d;
+  const int S = plan->S;
+  const long long n_tn = (long long)rd.tn.size();
+  const long long nkeys = rd.n_slices * S;
+  if (n_tn == 0 || nkeys == 0) return SPMC_OK;
+  if (nkeys > 0xffffffffLL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event sweep: more than 2^32 (slice, node) pairs");
+  // workspace
+  if (plan->counts_cap < nkeys) {
+    cudaFree(plan->d_counts); cudaFree(plan->d_starts);
+    plan->d_counts = nullptr; plan->d_starts = nullptr; plan->counts_cap = 0;
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_counts, sizeof(unsigned int) * nkeys));
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_starts, sizeof(unsigned int) * nkeys));
+    plan->counts_cap = nkeys;
+  }
+  const long long nblk = (nkeys + 1023) / 1024;
+  if (plan->bsum_cap < nblk) {
+    cudaFree(plan->d_bsum);
+    plan->d_bsum = nullptr; plan->bsum_cap = 0;
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_bsum, sizeof(unsigned long long) * nblk));
+    plan->bsum_cap = nblk;
+  }
+  if (!plan->d_total) SPMC_CUDA(cudaMalloc((void**)&plan->d_total, sizeof(unsigned long long)));
+  if (plan->acc_cap < n_tn * S) {
+    cudaFree(plan->d_acc);
+    plan->d_acc = nullptr; plan->acc_cap = 0;
+    SPMC_CUDA(cudaMalloc((void**)&plan->d_acc, sizeof(double) * n_tn * S));
+    plan->acc_cap = n_tn * S;
+  }
+  SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, sizeof(double) * n_tn * S, stream));
+  EventArgs a;
+  a.tn = rd.d_tn; a.xnodes = plan->d_x; a.counts = plan->d_counts; a.events = plan->d_events;
+  a.n = d.n_space; a.S = S; a.n_sub = d.n_sub;
+  int gb = 0;
+  while ((1 << gb) < d.n_sub) ++gb;
+  a.gbits = gb; a.max_steps = d.max_steps; a.interval = interval; a.iteration = iteration;
+  a.n_tn = n_tn; a.kappa = d.kappa; a.shell = plan->shell;
+  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
+  a.counters = plan->d_counters;
+  a.status = plan->d_status;
+  a.cap = 0;
+  int dev = 0, sms = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned wgrid = (unsigned)(sms * 8);
+  // samples per batch: about 2^26 walks per batch
+  long long nb = plan->ev_batch > 0 ? plan->ev_batch : std::max(1LL, (1LL << 26) / (n_tn * S));
+  nb = std::min<long long>(nb, d.M);
+  const int NMAXv = (D == 1) ? 32 : (d.n_space <= 8 ? 8 : (d.n_space <= 16 ? 16 : (d.n_space <= 24 ? 24 : 32)));
+  for (long long i0 = 0; i0 < d.M; i0 += nb) {
+    a.i0 = i0;
+    a.nb = std::min<long long>(nb, d.M - i0);
+    SPMC_CUDA(cudaMemsetAsync(plan->d_counts, 0, sizeof(unsigned int) * nkeys, stream));
+    walk_events_kernel<D, R, false><<<wgrid, 256, 0, stream>>>(a);
+    SPMC_CUDA(cudaGetLastError());
+    scan_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(plan->d_counts, plan->d_bsum, nkeys);
+    scan_totals_kernel<<<1, 1024, 0, stream>>>(plan->d_bsum, nblk, plan->d_total);
+    scan_add_kernel<<<(unsigned)((nkeys + 255) / 256), 256, 0, stream>>>(plan->d_counts, plan->d_bsum,
+                                                                          plan->d_starts, nkeys);
+    SPMC_CUDA(cudaGetLastError());
+    unsigned long long total = 0;
+    SPMC_CUDA(cudaMemcpyAsync(&total, plan->d_total, sizeof(total), cudaMemcpyDeviceToHost, stream));
+    SPMC_CUDA(cudaStreamSynchronize(stream));
+    if (total > 0xffffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch above 2^32 events");
+    const size_t need = sizeof(Event<R>) * (size_t)std::max(1ULL, total);
+    if (plan->events_bytes < need) {
+      cudaFree(plan->d_events);
+      plan->d_events = nullptr; plan->events_bytes = 0;
+      SPMC_CUDA(cudaMalloc(&plan->d_events, need + need / 4));
+      plan->events_bytes = need + need / 4;
+    }
+    a.events = plan->d_events;
+    a.cap = plan->events_bytes / sizeof(Event<R>);
+    if (total == 0) continue;
+    walk_events_kernel<D, R, true><<<wgrid, 256, 0, stream>>>(a);
+    SPMC_CUDA(cudaGetLastError());
+    const size_t esmem = sizeof(R) * (size_t)plan->sl_stride;
+    if (D == 1) {
+      eval_events_kernel<1, 32, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(
+          rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
+          plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
+    } else {
+      if (NMAXv == 8) eval_events_kernel<2, 8, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
+      else if (NMAXv == 16) eval_events_kernel<2, 16, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
+      else if (NMAXv == 24) eval_events_kernel<2, 24, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
+      else eval_events_kernel<2, 32, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
+    }
+    SPMC_CUDA(cudaGetLastError());
+  }
+  return SPMC_OK;
+}
+
+spmc_status event_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const bool fp64 = plan->d.precision == SPMC_FP64;
+  if (plan->d.dim == 1) return fp64 ? event_sweep_t<1, double>(plan, stream, rd, interval, iteration)
+                                    : event_sweep_t<1, float>(plan, stream, rd, interval, iteration);
+  return fp64 ? event_sweep_t<2, double>(plan, stream, rd, interval, iteration)
+              : event_sweep_t<2, float>(plan, stream, rd, interval, iteration);
+}
+
 // One residual iteration on interval r for every instance that has it.
 spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   Round& rd = plan->rounds[r];
@@ -551,14 +665,27 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   spmc_status pst = prepare_slices(plan, stream, rd);
   if (pst != SPMC_OK) return pst;
   bool fp64 = plan->d.precision == SPMC_FP64;
-  spmc_status st = fp64 ? dispatch_sweep<double>(plan, stream, rd, r, iteration)
-                        : dispatch_sweep<float>(plan, stream, rd, r, iteration);
+  const bool events = plan->d.dim <= 2 && plan->sweep_mode == 0;
+  std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
+  if (events && plan->timing) {
+    if (!plan->ev_free.empty()) { tev = plan->ev_free.back(); plan->ev_free.pop_back(); }
+    else { SPMC_CUDA(cudaEventCreate(&tev.first)); SPMC_CUDA(cudaEventCreate(&tev.second)); }
+    SPMC_CUDA(cudaEventRecord(tev.first, stream));
+  }
+  spmc_status st = events ? event_sweep(plan, stream, rd, r, iteration)
+                          : (fp64 ? dispatch_sweep<double>(plan, stream, rd, r, iteration)
+                                  : dispatch_sweep<float>(plan, stream, rd, r, iteration));
   if (st != SPMC_OK) return st;
+  if (events && plan->timing) {
+    SPMC_CUDA(cudaEventRecord(tev.second, stream));
+    plan->ev_pending.push_back(tev);
+  }
   SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, stream));
   long long nn = (long long)rd.tn.size() * S;
-  int n_chunks = (int)((plan->d.M + plan->chunk - 1) / plan->chunk);
+  int n_chunks = events ? 1 : (int)((plan->d.M + plan->chunk - 1) / plan->chunk);
   if (nn > 0) {
-    update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(rd.d_tn, plan->d_partial, plan->d_U, nullptr,
+    update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(rd.d_tn, events ? plan->d_acc : plan->d_partial,
+                                                                    plan->d_U, nullptr,
                                                                     plan->d_maxeps, plan->d_status, nn, S, n_chunks,
                                                                     1.0 / (double)plan->d.M);
     SPMC_CUDA(cudaGetLastError());
@@ -620,6 +747,7 @@ spmc_status read_status(spmc_plan_t plan, cudaStream_t stream) {
   SPMC_CUDA(cudaStreamSynchronize(stream));
   if (h & 1) return fail(plan, SPMC_ERR_NONFINITE, "a non-finite eps was produced");
   if (h & 2) return fail(plan, SPMC_ERR_TIMEOUT, "a sweep block exceeded its round budget");
+  if (h & 4) return fail(plan, SPMC_ERR_CUDA, "event sweep: an event fell outside its segment");
   return SPMC_OK;
 }
 
@@ -1212,6 +1340,15 @@ spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, dou
   return SPMC_OK;
 }
 
+spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (mode != SPMC_SWEEP_EVENTS && mode != SPMC_SWEEP_COHORT)
+    return fail(plan, SPMC_ERR_INVALID, "spmc_set_sweep: unknown mode");
+  plan->sweep_mode = mode;
+  plan->ev_batch = batch > 0 ? batch : 0;
+  return SPMC_OK;
+}
+
 spmc_status spmc_set_timing(spmc_plan_t plan, int enable) {
   if (!plan) return SPMC_ERR_INVALID;
   drain_timing(plan);
@@ -1246,6 +1383,8 @@ void spmc_destroy(spmc_plan_t plan) {
   cudaFree(plan->d_status);
   cudaFree(plan->d_work);
   cudaFree(plan->d_state);
+  cudaFree(plan->d_counts); cudaFree(plan->d_starts); cudaFree(plan->d_bsum); cudaFree(plan->d_total);
+  cudaFree(plan->d_events); cudaFree(plan->d_acc);
   cudaFree(plan->d_lambda); cudaFree(plan->d_Ubak); cudaFree(plan->d_iter); cudaFree(plan->d_gT); cudaFree(plan->d_lam);
   cudaFree(plan->d_mu); cudaFree(plan->d_dLdz); cudaFree(plan->d_gds); cudaFree(plan->d_phi); cudaFree(plan->d_last);
   for (auto p : plan->d_first_tn) cudaFree(p);

@@ -16,10 +16,10 @@ def api():
     return A
 
 
-def _stepwise(O, api, wl, K, precision=0):
-    from paper_2608_22190_b300 import _lib as L
+def _stepwise(O, api, wl, K, precision=0, sweep="events", batch=0):
     inst = wl.instances[0]
     plan = api.Plan.from_workload(wl, precision=precision)
+    plan.set_sweep(sweep, batch)
     spec = oracle_spec(O, wl, inst)
     u0 = oracle_u0(O, wl, inst, spec)
     Mt = int(inst.degrees[0])
@@ -35,28 +35,55 @@ def _stepwise(O, api, wl, K, precision=0):
     return out
 
 
-def test_fp64_1d_radau_stepwise(O, api):
+SWEEPS = [("events", 0), ("events", 37), ("cohort", 0)]   # 37: ragged sample batches
+
+
+@pytest.mark.parametrize("sweep,batch", SWEEPS)
+def test_fp64_1d_radau_stepwise(O, api, sweep, batch):
     from paper_2608_22190_b300 import workloads as W
     wl = W.w1(M=300, K=3, n_space=6, degree=5)
     wl.n_ref = 12
-    for g, r in _stepwise(O, api, wl, 3):
+    for g, r in _stepwise(O, api, wl, 3, sweep=sweep, batch=batch):
         assert np.all(np.abs(g - r) <= parity_tol(r)), np.abs(g - r).max()
 
 
-def test_fp64_1d_ragged_chunks(O, api):
+@pytest.mark.parametrize("sweep,batch", SWEEPS)
+def test_fp64_1d_ragged_chunks(O, api, sweep, batch):
     from paper_2608_22190_b300 import workloads as W
     wl = W.w1(M=2500, K=2, n_space=5, degree=3)   # chunks of 1024: the third one is partial
     wl.n_ref = 8
-    for g, r in _stepwise(O, api, wl, 2):
+    for g, r in _stepwise(O, api, wl, 2, sweep=sweep, batch=batch):
         assert np.all(np.abs(g - r) <= parity_tol(r)), np.abs(g - r).max()
 
 
-def test_fp64_2d_stepwise(O, api):
+@pytest.mark.parametrize("sweep,batch", SWEEPS)
+def test_fp64_2d_stepwise(O, api, sweep, batch):
     from paper_2608_22190_b300 import workloads as W
     wl = W.w2(M=200, K=2, n_space=5, degree=3, n_intervals=1, h=0.5)
     wl.n_ref = 10
-    for g, r in _stepwise(O, api, wl, 2):
+    for g, r in _stepwise(O, api, wl, 2, sweep=sweep, batch=batch):
         assert np.all(np.abs(g - r) <= parity_tol(r)), np.abs(g - r).max()
+
+
+def test_mixed_events_match_cohort(api):
+    """Mixed precision: the event sweep (per-term FP64 sums) and the cohort
+    sweep (per-walk FP32 sums) take the same walks and points; they agree to
+    FP32 rounding of the walk sums."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w2(M=1024, K=1, n_space=8, degree=4, n_intervals=1, h=0.5)
+    wl.n_ref = 16
+    out = {}
+    for sweep in ("events", "cohort"):
+        plan = api.Plan.from_workload(wl, precision=1)
+        plan.set_sweep(sweep)
+        plan.begin_interval(0)
+        U0 = plan.get_nodes(0, 0).cpu().numpy()
+        plan.iterate(0, 1)
+        out[sweep] = (plan.get_nodes(0, 0).cpu().numpy() - U0, plan.stats()["points"])
+        plan.close()
+    (ee, pe), (ec, pc) = out["events"], out["cohort"]
+    assert pe == pc
+    assert np.abs(ee - ec).max() <= 1e-5 * np.abs(ec).max(), np.abs(ee - ec).max()
 
 
 def test_fp64_1d_multi_interval_solve(O, api):

@@ -30,6 +30,7 @@ def test_iterate_static_matches_iterate(precision):
     wl = W.w2(M=1500, K=2, n_space=6, degree=4, n_intervals=1, h=0.5)   # ragged last chunk
     wl.n_ref = 12
     ref = Plan.from_workload(wl, precision=precision)
+    ref.set_sweep("cohort")      # the static entry point runs the cohort kernel
     sta = Plan.from_workload(wl, precision=precision)
     stream = torch.cuda.current_stream()
     sp = C.c_void_p(stream.cuda_stream)
