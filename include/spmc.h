@@ -104,6 +104,9 @@ typedef struct {
   double last_max_eps;
   long long sweep_launches; /* sweep kernel launches timed (spmc_set_timing) */
   double sweep_ms;          /* their summed duration, from CUDA events on the caller's stream */
+  double walk_ms;           /* event sweep: the two walk passes and the scan (part of sweep_ms) */
+  double eval_ms;           /* event sweep: the per-slice evaluation launches (part of sweep_ms) */
+  long long eval_launches;
 } spmc_stats;
 
 /* Validate desc, build the node tables and allocate the workspace.
@@ -178,32 +181,44 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
 /* Forward-sweep strategy for d <= 2 (d = 5, spmc_grad and spmc_iterate_static
  * always use the cohort kernel):
  *   SPMC_SWEEP_EVENTS (default): per batch of `batch` samples, the walks run
- *     twice (count, then fill) and write their evaluation events (Green point,
- *     weight, node) grouped by time slice; one block per slice then evaluates
- *     all of them against the slice staged once in shared memory.  Per-event
- *     terms are summed in FP64.  Device memory: 16 (FP32) or 32 (FP64) bytes per
- *     event of a batch, allocated on first use and kept.  batch <= 0 picks about
- *     2^26 walks per batch.
+ *     once and append their evaluation events (Green point, weight, slice and
+ *     node); a counting sort groups them by (time slice, node); one block per
+ *     slice then evaluates all of them against that slice.  With d = 2 and
+ *     SPMC_MIXED the evaluation is a matrix product on the tensor cores
+ *     (tcgen05, TF32 with a 3-term split, FP32 accumulation); otherwise it runs
+ *     on the FP32 / FP64 pipes.  Per-event terms are summed in FP64.  Device
+ *     memory: two event buffers of 16 (FP32) or 32 (FP64) bytes per event of a
+ *     batch, allocated on first use and kept.  batch <= 0 picks about 2^25
+ *     walks per batch.
+ *   SPMC_SWEEP_EVENTS_ALU: the same, with the evaluation always on the FP32 /
+ *     FP64 pipes.
  *   SPMC_SWEEP_COHORT: the persistent cohort kernel; a walk's terms are summed
  *     in the sweep precision, then in FP64 per chunk.
  * The two give the same walks and the same points; only summation order and,
- * in SPMC_MIXED, the per-walk FP32 partial sums differ.  Returns
+ * in SPMC_MIXED, the per-walk FP32 partial sums differ.  The event sweep's
+ * FP64 sums use atomics, so its results can differ from run to run at the
+ * rounding level of those sums; the cohort kernel is bitwise reproducible.  Returns
  * SPMC_ERR_INVALID for an unknown mode. */
 #define SPMC_SWEEP_EVENTS 0
 #define SPMC_SWEEP_COHORT 1
+#define SPMC_SWEEP_EVENTS_ALU 2
 spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch);
 
 /* Enable (1) or disable (0) CUDA-event timing of every sweep kernel launch; the
  * totals accumulate in spmc_stats.sweep_ms / sweep_launches (reset on enable). */
 spmc_status spmc_set_timing(spmc_plan_t plan, int enable);
 
-/* Autotuner: times the sweep kernel of one iteration of `interval` (which must
- * have been started with spmc_begin_interval) for each candidate cohort width
- * (spatial nodes per cohort), keeps the fastest for the plan and returns its
- * time in *best_ms (may be NULL).  The nodal values are left unchanged: the
+/* Autotuner: times the forward sweep of one iteration of `interval` (which must
+ * have been started with spmc_begin_interval) for each candidate setting, keeps
+ * the fastest for the plan and returns its time in *best_ms (may be NULL).  The
+ * setting is the batch size (2^23 .. 2^26 walks per batch) of the event sweep,
+ * or the cohort width (spatial nodes per cohort) of the cohort kernel.  The
+ * nodal values and the points / capped counters are left unchanged: the
  * candidates run the reconstruction, slices and sweep but not the update.
- * Results of later iterations do not depend on the choice (per-node sums run in
- * sample order whatever the width). */
+ * Results of later iterations do not depend on the choice beyond the order of
+ * the FP64 sums (the cohort kernel sums per node in sample order whatever the
+ * width; the event sweep's FP64 atomic sums are order-dependent at rounding
+ * level, so it is not bitwise reproducible from run to run). */
 spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, double* best_ms);
 
 /* The n_space JG(1,1) node coordinates of one axis, ascending (host array). */

@@ -20,7 +20,7 @@ FP64, MIXED = 0, 1
 F_POLY3, F_SIN = 0, 1
 EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
 U0_NODAL, U0_PHI_COEF = 0, 1
-SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT = 0, 1
+SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT, SPMC_SWEEP_EVENTS_ALU = 0, 1, 2
 
 
 class PlanDesc(C.Structure):
@@ -44,7 +44,8 @@ class Problem(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("node_samples", C.c_longlong), ("points", C.c_longlong), ("capped", C.c_longlong),
                 ("iterations_run", C.c_int), ("last_max_eps", C.c_double),
-                ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double)]
+                ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
+                ("walk_ms", C.c_double), ("eval_ms", C.c_double), ("eval_launches", C.c_longlong)]
 
 
 # The C-ABI entry points and their signatures, as declared in include/spmc.h.

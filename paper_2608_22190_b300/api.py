@@ -177,7 +177,8 @@ class Plan:
         s = L.Stats()
         L.check(L.lib.spmc_get_stats(self._h, C.byref(s)), self._h)
         return {"points": s.points, "capped": s.capped, "iterations_run": s.iterations_run,
-                "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms}
+                "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms,
+                "walk_ms": s.walk_ms, "eval_ms": s.eval_ms, "eval_launches": s.eval_launches}
 
     def autotune(self, interval: int = 0, stream=None) -> float:
         """Pick the sweep's cohort width by timing one sweep per candidate (nodal values unchanged)."""
@@ -186,8 +187,10 @@ class Plan:
         return ms.value
 
     def set_sweep(self, mode: str = "events", batch: int = 0):
-        """Forward-sweep strategy for d <= 2: "events" (default) or "cohort"."""
-        m = {"events": L.SPMC_SWEEP_EVENTS, "cohort": L.SPMC_SWEEP_COHORT}[mode]
+        """Forward-sweep strategy for d <= 2: "events" (default; tensor-core
+        evaluation for d = 2 in mixed precision), "events_alu" or "cohort"."""
+        m = {"events": L.SPMC_SWEEP_EVENTS, "cohort": L.SPMC_SWEEP_COHORT,
+             "events_alu": L.SPMC_SWEEP_EVENTS_ALU}[mode]
         L.check(L.lib.spmc_set_sweep(self._h, m, int(batch)), self._h)
 
     def set_timing(self, enable: bool):

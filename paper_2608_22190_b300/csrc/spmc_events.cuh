@@ -3,18 +3,20 @@
 // The time slices depend only on (instance, time node, sub-point), not on the
 // spatial node, so the residual evaluations of one slice can be done together
 // for every node and sample of its time node.  Per batch of samples:
-//   walk_events_kernel<COUNT>  every walk runs its steps (Lemma Xlocation,
-//                              inside balls, roulette) and counts its
-//                              evaluation events per (slice, spatial node);
+//   walk_events_kernel<COUNT>  every walk runs its steps (inside balls, Green
+//                              points, roulette) and counts its evaluation
+//                              events per (slice, spatial node);
 //   scan kernels               exclusive offsets of the (slice, node) segments;
 //   walk_events_kernel<FILL>   the same walks again (pure functions of their
 //                              Philox streams) write each event (Green point,
-//                              weight) into its segment;
+//                              weight, key) into its segment;
 //   eval_events_kernel         one block per slice stages the slice once in
 //                              shared memory and evaluates all its events; the
 //                              weighted residuals are summed per node in FP64.
 // The per-node sums feed the update kernel (eps = sum / M).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "spmc_kernels.cuh"
 
 namespace spmc {
@@ -23,69 +25,92 @@ template <typename R>
 struct Event {
   R y[2];
   R w;
-  int j;
+  unsigned int key;   // (slice, spatial node) = slice * S + j
 };
 
 struct EventArgs {
   const TimeNode* tn;
   const double* xnodes;
-  unsigned int* counts;          // (slice, node) counters / fill cursors
-  void* events;                  // Event<R>[]
+  unsigned int* counts;          // COUNT: (slice, node) histogram; FILL: placement cursors
+  void* events;                  // Event<R>[cap] grouped by (slice, node) (FILL)
+  unsigned long long cap;        // events the buffer holds (FILL)
+  int* status;                   // bit 4: an event fell outside the buffer
   int n, S, n_sub, gbits, max_steps, interval, iteration;
   long long n_tn;
   long long i0, nb;              // sample range of the batch
   double kappa, shell;
   uint32_t k0, k1;
   unsigned long long* counters;  // [0] points, [1] capped
-  unsigned long long cap;        // events the buffer holds (FILL)
-  int* status;                   // bit 4: an event fell outside its segment
 };
 
 // Every walk of the batch, lane by lane: a lane takes the next walk when its
 // current one ends, so the lanes of a warp stay busy.  Walk ids run sample
-// fastest (consecutive lanes share a node and mostly a slice).
+// fastest (consecutive lanes share a node and mostly a slice); a thread steps
+// through its walk ids by a fixed stride, kept as (time node, node, sample)
+// counters.  COUNT counts the evaluation events per (slice, node); FILL runs
+// the same walks again (pure functions of their Philox streams) and writes each
+// event into its place.  Lanes with the same key share one atomic.
 template <int D, typename R, bool FILL>
 __global__ void __launch_bounds__(256) walk_events_kernel(EventArgs a) {
-  const long long total = a.n_tn * a.S * a.nb;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  long long wid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  namespace cg = cooperative_groups;
   const int S = a.S, n = a.n, G = a.n_sub;
+  const long long nb = a.nb;
   const R kappa = (R)a.kappa, shell = (R)a.shell;
   Event<R>* ev = reinterpret_cast<Event<R>*>(a.events);
   unsigned long long capped = 0, points = 0;
 
+  // walk id = (ti * S + j) * nb + il; the stride decomposed the same way
+  const long long total = a.n_tn * S * nb;
+  long long wid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long per_tn = (long long)S * nb;
+  long long ti = wid / per_tn;
+  int j = (int)((wid - ti * per_tn) / nb);
+  long long il = wid - ti * per_tn - (long long)j * nb;
+  const long long st_t = stride / per_tn;
+  const int st_j = (int)((stride - st_t * per_tn) / nb);
+  const long long st_i = stride - st_t * per_tn - (long long)st_j * nb;
+
   // walk state
   bool live = false;
   R X[D], f = R(0), delta = R(0), J = R(0), sub = R(0);
-  int k = 0, q = 0, Ktot = 0, j = 0;
-  long long slice_base = 0;
+  int k = 0, q = 0, Ktot = 0, key_j = 0;
+  long long slice_base = 0, cached_ti = -1;
+  uint32_t node_ell = 0;
   WalkStream ws;
   ws.k0 = a.k0; ws.k1 = a.k1;
   constexpr int WS = step_words(D);
   while (true) {
     if (!live) {
       if (wid >= total) break;
-      const long long ti = wid / ((long long)S * a.nb);
-      const long long rem = wid - ti * (long long)S * a.nb;
-      j = (int)(rem / a.nb);
-      const long long i = a.i0 + (rem - (long long)j * a.nb);
-      wid += stride;
-      const TimeNode node = a.tn[ti];
-      const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
-      delta = Ar<R>::div(sdur, (R)node.nstar);
-      J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
-      sub = Ar<R>::div(delta, (R)G);
-      Ktot = G * node.nstar;
-      slice_base = node.slice_base;
+      if (ti != cached_ti) {   // time-node parameters, as the CPU reference computes them
+        const TimeNode node = a.tn[ti];
+        const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
+        delta = Ar<R>::div(sdur, (R)node.nstar);
+        J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
+        sub = Ar<R>::div(delta, (R)G);
+        Ktot = G * node.nstar;
+        slice_base = node.slice_base;
+        node_ell = (uint32_t)node.ell;
+        ws.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+                 (uint32_t)(a.iteration & 0x3ff);
+        cached_ti = ti;
+      }
       int jr = j;
 #pragma unroll
       for (int e = 0; e < D; ++e) { X[e] = (R)a.xnodes[jr % n]; jr /= n; }
       f = R(0); k = 0; q = 0;
-      ws.node = (uint32_t)(node.ell * S + j);
-      ws.sample = (uint32_t)i;
-      ws.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
-               (uint32_t)(a.iteration & 0x3ff);
+      key_j = j;
+      ws.node = node_ell * (uint32_t)S + (uint32_t)j;
+      ws.sample = (uint32_t)(a.i0 + il);
       live = true;
+      // advance to this thread's next walk id
+      wid += stride;
+      il += st_i;
+      if (il >= nb) { il -= nb; ++j; }
+      j += st_j;
+      if (j >= S) { j -= S; ++ti; }
+      ti += st_t;
     }
     // ---- one step, as the CPU reference: absorb, ball, weight, sub-point
     R dist = R(1);
@@ -137,33 +162,37 @@ __global__ void __launch_bounds__(256) walk_events_kernel(EventArgs a) {
     }
     const Philox4 b0 = ws.block(w0 >> 2);   // next-step and Green directions (d <= 2: one block)
     if (w > R(0)) {
-      R thg[D];
-      if (D == 1) {
-        thg[0] = (b0.v[(w0 + dir_words(D)) & 3] >> 31) ? R(-1) : R(1);
-      } else {
-        const uint32_t o = (w0 + dir_words(D)) & 3;
-        const R U = U01<R>::pair(b0.v[o], b0.v[o + 1]);
-        R sn, cs;
-        Ar<R>::sincos2pi(U, &sn, &cs);
-        thg[0] = cs; thg[1] = sn;
-      }
-      const uint32_t wr = w0 + 2 * dir_words(D);
-      const Philox4 rb = (D == 1) ? b0 : ws.block(wr >> 2);
-      const R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
-      const R U2 = (D == 2) ? U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]) : R(0);
-      const R v = green_radius<D, R>(U1, U2);
-      const R rv = Ar<R>::mul(r, v);
-      const unsigned int key = (unsigned int)((slice_base + m) * S + j);
+      const unsigned int key = (unsigned int)((slice_base + m) * S + key_j);
+      cg::coalesced_group grp = cg::coalesced_threads();
+      cg::coalesced_group same = cg::labeled_partition(grp, key);
       if (!FILL) {
-        atomicAdd(&a.counts[key], 1u);
+        if (same.thread_rank() == 0) atomicAdd(&a.counts[key], same.size());
       } else {
-        const unsigned int slot = atomicAdd(&a.counts[key], 1u);
+        unsigned int slot = 0;
+        if (same.thread_rank() == 0) slot = atomicAdd(&a.counts[key], same.size());
+        slot = same.shfl(slot, 0) + same.thread_rank();
+        R thg[D];
+        if (D == 1) {
+          thg[0] = (b0.v[(w0 + dir_words(D)) & 3] >> 31) ? R(-1) : R(1);
+        } else {
+          const uint32_t o = (w0 + dir_words(D)) & 3;
+          const R U = U01<R>::pair(b0.v[o], b0.v[o + 1]);
+          R sn, cs;
+          Ar<R>::sincos2pi(U, &sn, &cs);
+          thg[0] = cs; thg[1] = sn;
+        }
+        const uint32_t wr = w0 + 2 * dir_words(D);
+        const Philox4 rb = (D == 1) ? b0 : ws.block(wr >> 2);
+        const R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
+        const R U2 = (D == 2) ? U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]) : R(0);
+        const R v = green_radius<D, R>(U1, U2);
+        const R rv = Ar<R>::mul(r, v);
         if ((unsigned long long)slot < a.cap) {
           Event<R> e;
           e.y[0] = Ar<R>::add(X[0], Ar<R>::mul(rv, thg[0]));
           e.y[1] = (D == 2) ? Ar<R>::add(X[1], Ar<R>::mul(rv, thg[1])) : R(0);
           e.w = w;
-          e.j = j;
+          e.key = key;
           ev[slot] = e;
         } else {
           atomicOr(a.status, 4);   // cannot happen: both passes take the same walks
@@ -200,7 +229,6 @@ __global__ void __launch_bounds__(256) walk_events_kernel(EventArgs a) {
 // Exclusive scan of n unsigned counts in place, in three launches (block scans
 // of 1024 entries, a scan of the block totals, the add-back).
 __global__ void scan_blocks_kernel(unsigned int* __restrict__ v, unsigned long long* __restrict__ bsum, long long n) {
-  __shared__ unsigned int tmp[1024];
   __shared__ unsigned int wsum[32];
   const long long base = (long long)blockIdx.x * 1024;
   unsigned int x[4];
@@ -232,7 +260,6 @@ __global__ void scan_blocks_kernel(unsigned int* __restrict__ v, unsigned long l
     run += x[u];
   }
   if (t == 0) bsum[blockIdx.x] = tot;
-  (void)tmp;
 }
 
 // exclusive scan of the block totals (one block, serial chunks)
@@ -313,7 +340,7 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
       if (D == 2) Y[1] = e.y[1];
       const R res = residual_at<D, NMAX, R>(ip, kappa, n, sC, sC + half, Y, (R)si.Tt, (R)si.dTt);
       val = (double)(e.w * res);
-      jv = e.j;
+      jv = (int)(e.key - (unsigned int)(sidx * S));
     }
     // segmented warp sum by node (events of a node are contiguous)
     const unsigned int same = __match_any_sync(0xffffffffu, jv);

@@ -15,6 +15,7 @@
 #include "spmc.h"
 #include "spmc_kernels.cuh"
 #include "spmc_events.cuh"
+#include "spmc_tc.cuh"
 #include "spmc_tables.h"
 
 using namespace spmc;
@@ -64,9 +65,9 @@ struct spmc_plan_s {
   unsigned int* d_counts = nullptr;  // (slice, node) counters / cursors
   unsigned int* d_starts = nullptr;  // segment starts
   unsigned long long* d_bsum = nullptr;
-  unsigned long long* d_total = nullptr;
+  unsigned long long* d_total = nullptr;  // events of the batch (scan total)
   long long counts_cap = 0, bsum_cap = 0;
-  void* d_events = nullptr;
+  void* d_events = nullptr;          // events grouped by (slice, node)
   size_t events_bytes = 0;
   double* d_acc = nullptr;           // per (time node, node) FP64 sums
   long long acc_cap = 0;
@@ -108,6 +109,7 @@ struct spmc_plan_s {
   std::vector<long long*> d_first_tn;   // per round: instance ranges of the time-node table
   bool grad_ready = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
+  std::vector<int> ev_cat;           // per pending pair: 0 sweep, 1 event walks, 2 event evaluation
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
 };
 
@@ -364,6 +366,7 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
   if (plan->timing) {
     SPMC_CUDA(cudaEventRecord(ev.second, stream));
     plan->ev_pending.push_back(ev);
+    plan->ev_cat.push_back(0);
   }
   return SPMC_OK;
 }
@@ -422,6 +425,7 @@ spmc_status launch_sweep5(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   if (plan->timing) {
     SPMC_CUDA(cudaEventRecord(ev.second, stream));
     plan->ev_pending.push_back(ev);
+    plan->ev_cat.push_back(0);
   }
   return SPMC_OK;
 }
@@ -555,6 +559,53 @@ spmc_status dispatch_adjoint(spmc_plan_t plan, cudaStream_t stream, const Round&
   return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
 }
 
+spmc_status timer_begin(spmc_plan_t plan, cudaStream_t s, std::pair<cudaEvent_t, cudaEvent_t>& ev);
+spmc_status timer_end(spmc_plan_t plan, cudaStream_t s, std::pair<cudaEvent_t, cudaEvent_t>& ev, int cat);
+
+// Grow a device buffer to at least `need` bytes (contents are not kept).
+spmc_status grow(spmc_plan_t plan, void** p, size_t* have, size_t need) {
+  if (*have >= need) return SPMC_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  SPMC_CUDA(cudaMalloc(p, need));
+  *have = need;
+  return SPMC_OK;
+}
+
+template <int D, int NMAX, typename R>
+void launch_eval(spmc_plan_t plan, cudaStream_t stream, const Round& rd, unsigned long long total) {
+  const size_t esmem = sizeof(R) * (size_t)plan->sl_stride;
+  eval_events_kernel<D, NMAX, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(
+      rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
+      plan->d_acc, plan->d.n_space, plan->S, plan->sl_stride, plan->half, plan->d.kappa, total);
+}
+
+// Tensor-core evaluation (d = 2, FP32 sweep).  The dynamic shared memory is
+// padded so that at most 512 / TM_COLS blocks share an SM: their TMEM
+// allocations then always fit and tcgen05.alloc never waits.
+template <int NMAX>
+spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& rd, unsigned long long total) {
+  using Gm = TcGeom<NMAX>;
+  const int max_blocks = 512 / Gm::TM_COLS;
+  const int smem = std::max(Gm::SMEM, 233472 / (max_blocks + 1) + 1024);
+  static bool attr_set[64] = {};
+  int dev = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  if (dev < 64 && !attr_set[dev]) {
+    SPMC_CUDA(cudaFuncSetAttribute(eval_events_tc_kernel<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr_set[dev] = true;
+  }
+  const unsigned long long blocks = (total + Gm::CHUNK - 1) / Gm::CHUNK;
+  if (blocks > 0x7fffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch too large for one evaluation launch");
+  eval_events_tc_kernel<NMAX><<<(unsigned)blocks, 128, smem, stream>>>(
+      rd.d_slice_node, rd.d_tn, plan->d_ip, reinterpret_cast<const float*>(plan->d_slices), plan->d_sinfo,
+      plan->d_starts, reinterpret_cast<const Event<float>*>(plan->d_events), plan->d_acc, plan->d.n_space, plan->S,
+      rd.n_slices, plan->sl_stride, plan->half, plan->d.kappa, total, plan->d_status);
+  SPMC_CUDA(cudaGetLastError());
+  return SPMC_OK;
+}
+
 template <int D, typename R>
 spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
   const spmc_plan_desc& d = plan->d;
@@ -587,7 +638,9 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, sizeof(double) * n_tn * S, stream));
   EventArgs a;
-  a.tn = rd.d_tn; a.xnodes = plan->d_x; a.counts = plan->d_counts; a.events = plan->d_events;
+  a.tn = rd.d_tn; a.xnodes = plan->d_x; a.counts = plan->d_counts;
+  a.status = plan->d_status;
+  a.events = nullptr; a.cap = 0;
   a.n = d.n_space; a.S = S; a.n_sub = d.n_sub;
   int gb = 0;
   while ((1 << gb) < d.n_sub) ++gb;
@@ -595,19 +648,19 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   a.n_tn = n_tn; a.kappa = d.kappa; a.shell = plan->shell;
   a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
   a.counters = plan->d_counters;
-  a.status = plan->d_status;
-  a.cap = 0;
   int dev = 0, sms = 0;
   SPMC_CUDA(cudaGetDevice(&dev));
   SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const unsigned wgrid = (unsigned)(sms * 8);
-  // samples per batch: about 2^26 walks per batch
-  long long nb = plan->ev_batch > 0 ? plan->ev_batch : std::max(1LL, (1LL << 26) / (n_tn * S));
+  // samples per batch: about 2^25 walks per batch
+  long long nb = plan->ev_batch > 0 ? plan->ev_batch : std::max(1LL, (1LL << 25) / (n_tn * S));
   nb = std::min<long long>(nb, d.M);
-  const int NMAXv = (D == 1) ? 32 : (d.n_space <= 8 ? 8 : (d.n_space <= 16 ? 16 : (d.n_space <= 24 ? 24 : 32)));
+  const int NMAXv = (D == 1) ? 32 : plan->row;
   for (long long i0 = 0; i0 < d.M; i0 += nb) {
     a.i0 = i0;
     a.nb = std::min<long long>(nb, d.M - i0);
+    std::pair<cudaEvent_t, cudaEvent_t> tw{nullptr, nullptr}, te{nullptr, nullptr};
+    if (timer_begin(plan, stream, tw) != SPMC_OK) return SPMC_ERR_CUDA;
     SPMC_CUDA(cudaMemsetAsync(plan->d_counts, 0, sizeof(unsigned int) * nkeys, stream));
     walk_events_kernel<D, R, false><<<wgrid, 256, 0, stream>>>(a);
     SPMC_CUDA(cudaGetLastError());
@@ -620,30 +673,32 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     SPMC_CUDA(cudaMemcpyAsync(&total, plan->d_total, sizeof(total), cudaMemcpyDeviceToHost, stream));
     SPMC_CUDA(cudaStreamSynchronize(stream));
     if (total > 0xffffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch above 2^32 events");
-    const size_t need = sizeof(Event<R>) * (size_t)std::max(1ULL, total);
-    if (plan->events_bytes < need) {
-      cudaFree(plan->d_events);
-      plan->d_events = nullptr; plan->events_bytes = 0;
-      SPMC_CUDA(cudaMalloc(&plan->d_events, need + need / 4));
-      plan->events_bytes = need + need / 4;
+    if (total == 0) {
+      if (timer_end(plan, stream, tw, 1) != SPMC_OK) return SPMC_ERR_CUDA;
+      continue;
     }
+    if (grow(plan, &plan->d_events, &plan->events_bytes, sizeof(Event<R>) * (size_t)total) != SPMC_OK)
+      return SPMC_ERR_OOM;
     a.events = plan->d_events;
     a.cap = plan->events_bytes / sizeof(Event<R>);
-    if (total == 0) continue;
     walk_events_kernel<D, R, true><<<wgrid, 256, 0, stream>>>(a);
     SPMC_CUDA(cudaGetLastError());
-    const size_t esmem = sizeof(R) * (size_t)plan->sl_stride;
-    if (D == 1) {
-      eval_events_kernel<1, 32, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(
-          rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
-          plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
-    } else {
-      if (NMAXv == 8) eval_events_kernel<2, 8, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
-      else if (NMAXv == 16) eval_events_kernel<2, 16, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
-      else if (NMAXv == 24) eval_events_kernel<2, 24, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
-      else eval_events_kernel<2, 32, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events, plan->d_acc, d.n_space, S, plan->sl_stride, plan->half, d.kappa, total);
-    }
+    if (timer_end(plan, stream, tw, 1) != SPMC_OK) return SPMC_ERR_CUDA;
+    if (timer_begin(plan, stream, te) != SPMC_OK) return SPMC_ERR_CUDA;
+    const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS;
+    if (tensor) {
+      spmc_status ts = NMAXv == 8 ? launch_eval_tc<8>(plan, stream, rd, total)
+                       : NMAXv == 16 ? launch_eval_tc<16>(plan, stream, rd, total)
+                       : NMAXv == 24 ? launch_eval_tc<24>(plan, stream, rd, total)
+                                     : launch_eval_tc<32>(plan, stream, rd, total);
+      if (ts != SPMC_OK) return ts;
+    } else if (D == 1) launch_eval<1, 32, R>(plan, stream, rd, total);
+    else if (NMAXv == 8) launch_eval<D == 1 ? 1 : 2, 8, R>(plan, stream, rd, total);
+    else if (NMAXv == 16) launch_eval<D == 1 ? 1 : 2, 16, R>(plan, stream, rd, total);
+    else if (NMAXv == 24) launch_eval<D == 1 ? 1 : 2, 24, R>(plan, stream, rd, total);
+    else launch_eval<D == 1 ? 1 : 2, 32, R>(plan, stream, rd, total);
     SPMC_CUDA(cudaGetLastError());
+    if (timer_end(plan, stream, te, 2) != SPMC_OK) return SPMC_ERR_CUDA;
   }
   return SPMC_OK;
 }
@@ -665,7 +720,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   spmc_status pst = prepare_slices(plan, stream, rd);
   if (pst != SPMC_OK) return pst;
   bool fp64 = plan->d.precision == SPMC_FP64;
-  const bool events = plan->d.dim <= 2 && plan->sweep_mode == 0;
+  const bool events = plan->d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT;
   std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
   if (events && plan->timing) {
     if (!plan->ev_free.empty()) { tev = plan->ev_free.back(); plan->ev_free.pop_back(); }
@@ -679,6 +734,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   if (events && plan->timing) {
     SPMC_CUDA(cudaEventRecord(tev.second, stream));
     plan->ev_pending.push_back(tev);
+    plan->ev_cat.push_back(0);
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, stream));
   long long nn = (long long)rd.tn.size() * S;
@@ -748,6 +804,7 @@ spmc_status read_status(spmc_plan_t plan, cudaStream_t stream) {
   if (h & 1) return fail(plan, SPMC_ERR_NONFINITE, "a non-finite eps was produced");
   if (h & 2) return fail(plan, SPMC_ERR_TIMEOUT, "a sweep block exceeded its round budget");
   if (h & 4) return fail(plan, SPMC_ERR_CUDA, "event sweep: an event fell outside its segment");
+  if (h & 8) return fail(plan, SPMC_ERR_TIMEOUT, "tensor-core evaluation: an MMA did not complete in time");
   return SPMC_OK;
 }
 
@@ -763,15 +820,35 @@ spmc_status read_max_eps(spmc_plan_t plan, cudaStream_t stream, double* out) {
 }
 
 void drain_timing(spmc_plan_t plan) {
-  for (auto& ev : plan->ev_pending) {
+  for (size_t i = 0; i < plan->ev_pending.size(); ++i) {
+    auto& ev = plan->ev_pending[i];
+    const int cat = i < plan->ev_cat.size() ? plan->ev_cat[i] : 0;
     float ms = 0.f;
     if (cudaEventSynchronize(ev.second) == cudaSuccess && cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
-      plan->stats.sweep_ms += ms;
-      plan->stats.sweep_launches += 1;
+      if (cat == 0) { plan->stats.sweep_ms += ms; plan->stats.sweep_launches += 1; }
+      else if (cat == 1) plan->stats.walk_ms += ms;
+      else { plan->stats.eval_ms += ms; plan->stats.eval_launches += 1; }
     }
     plan->ev_free.push_back(ev);
   }
   plan->ev_pending.clear();
+  plan->ev_cat.clear();
+}
+
+// Start / end a timed region on the stream (no-op unless timing is on).
+spmc_status timer_begin(spmc_plan_t plan, cudaStream_t s, std::pair<cudaEvent_t, cudaEvent_t>& ev) {
+  if (!plan->timing) return SPMC_OK;
+  if (!plan->ev_free.empty()) { ev = plan->ev_free.back(); plan->ev_free.pop_back(); }
+  else { SPMC_CUDA(cudaEventCreate(&ev.first)); SPMC_CUDA(cudaEventCreate(&ev.second)); }
+  SPMC_CUDA(cudaEventRecord(ev.first, s));
+  return SPMC_OK;
+}
+spmc_status timer_end(spmc_plan_t plan, cudaStream_t s, std::pair<cudaEvent_t, cudaEvent_t>& ev, int cat) {
+  if (!plan->timing) return SPMC_OK;
+  SPMC_CUDA(cudaEventRecord(ev.second, s));
+  plan->ev_pending.push_back(ev);
+  plan->ev_cat.push_back(cat);
+  return SPMC_OK;
 }
 
 void sync_counters(spmc_plan_t plan) {
@@ -1307,42 +1384,69 @@ spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, dou
   // reconstruction and slices of the current nodal values (left unchanged)
   spmc_status st = prepare_slices(plan, s, rd);
   if (st != SPMC_OK) return st;
-  // candidate cohort widths that fit two blocks per SM (FP32) / one (FP64)
-  const int wmax = plan->d.dim == 5 ? 2048 : (fp64 ? 4096 : 6144);
-  const int cands[] = {1, 2, 4, 6, 8, 12, 16, 24, 32};
+  // the trial sweeps leave the points / capped counters as they were
+  unsigned long long saved[2] = {0, 0};
+  SPMC_CUDA(cudaMemcpyAsync(saved, plan->d_counters, sizeof saved, cudaMemcpyDeviceToHost, s));
+  SPMC_CUDA(cudaStreamSynchronize(s));
   cudaEvent_t e0, e1;
   SPMC_CUDA(cudaEventCreate(&e0));
   SPMC_CUDA(cudaEventCreate(&e1));
-  const int keep = plan->JT;
   const bool timing = plan->timing;
   plan->timing = false;
   float best = 1e30f;
-  int best_jt = keep;
-  for (int jt : cands) {
-    if (jt * plan->chunk > wmax || (jt > plan->S && jt != 1)) continue;
-    plan->JT = jt;
-    SPMC_CUDA(cudaEventRecord(e0, s));
-    st = fp64 ? dispatch_sweep<double>(plan, s, rd, interval, rd.iteration + 1)
-              : dispatch_sweep<float>(plan, s, rd, interval, rd.iteration + 1);
-    if (st != SPMC_OK) break;
-    SPMC_CUDA(cudaEventRecord(e1, s));
-    SPMC_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    SPMC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) { best = ms; best_jt = jt; }
+  if (plan->d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT) {
+    // event sweep: samples per batch for 2^23 .. 2^26 walks per batch
+    const long long keep = plan->ev_batch;
+    long long best_nb = keep;
+    const long long walks_per_sample = std::max<long long>(1, (long long)rd.tn.size() * plan->S);
+    for (int lg = 23; lg <= 26; ++lg) {
+      const long long nb = std::max<long long>(1, std::min<long long>(plan->d.M, (1LL << lg) / walks_per_sample));
+      plan->ev_batch = nb;
+      SPMC_CUDA(cudaEventRecord(e0, s));
+      st = event_sweep(plan, s, rd, interval, rd.iteration + 1);
+      if (st != SPMC_OK) break;
+      SPMC_CUDA(cudaEventRecord(e1, s));
+      SPMC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SPMC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; best_nb = nb; }
+      if (nb >= plan->d.M) break;
+    }
+    plan->ev_batch = (st == SPMC_OK) ? best_nb : keep;
+  } else {
+    // candidate cohort widths that fit two blocks per SM (FP32) / one (FP64)
+    const int wmax = plan->d.dim == 5 ? 2048 : (fp64 ? 4096 : 6144);
+    const int cands[] = {1, 2, 4, 6, 8, 12, 16, 24, 32};
+    const int keep = plan->JT;
+    int best_jt = keep;
+    for (int jt : cands) {
+      if (jt * plan->chunk > wmax || (jt > plan->S && jt != 1)) continue;
+      plan->JT = jt;
+      SPMC_CUDA(cudaEventRecord(e0, s));
+      st = fp64 ? dispatch_sweep<double>(plan, s, rd, interval, rd.iteration + 1)
+                : dispatch_sweep<float>(plan, s, rd, interval, rd.iteration + 1);
+      if (st != SPMC_OK) break;
+      SPMC_CUDA(cudaEventRecord(e1, s));
+      SPMC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SPMC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; best_jt = jt; }
+    }
+    plan->JT = (st == SPMC_OK) ? best_jt : keep;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   plan->timing = timing;
-  plan->JT = (st == SPMC_OK) ? best_jt : keep;
   if (st != SPMC_OK) return st;
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_counters, saved, sizeof saved, cudaMemcpyHostToDevice, s));
+  SPMC_CUDA(cudaStreamSynchronize(s));
   if (best_ms) *best_ms = best;
   return SPMC_OK;
 }
 
 spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch) {
   if (!plan) return SPMC_ERR_INVALID;
-  if (mode != SPMC_SWEEP_EVENTS && mode != SPMC_SWEEP_COHORT)
+  if (mode != SPMC_SWEEP_EVENTS && mode != SPMC_SWEEP_COHORT && mode != SPMC_SWEEP_EVENTS_ALU)
     return fail(plan, SPMC_ERR_INVALID, "spmc_set_sweep: unknown mode");
   plan->sweep_mode = mode;
   plan->ev_batch = batch > 0 ? batch : 0;
@@ -1353,7 +1457,10 @@ spmc_status spmc_set_timing(spmc_plan_t plan, int enable) {
   if (!plan) return SPMC_ERR_INVALID;
   drain_timing(plan);
   plan->timing = enable != 0;
-  if (plan->timing) { plan->stats.sweep_ms = 0.0; plan->stats.sweep_launches = 0; }
+  if (plan->timing) {
+    plan->stats.sweep_ms = 0.0; plan->stats.sweep_launches = 0;
+    plan->stats.walk_ms = 0.0; plan->stats.eval_ms = 0.0; plan->stats.eval_launches = 0;
+  }
   return SPMC_OK;
 }
 

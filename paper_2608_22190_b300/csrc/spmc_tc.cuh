@@ -1,0 +1,364 @@
+// spmc_tc.cuh -- 5th-generation tensor-core pieces (tcgen05, TMEM, mbarrier) in
+// inline PTX for sm_103a, and the tensor-core evaluation of the event sweep.
+//
+// Operands are written by the CTA's threads straight into shared memory in the
+// no-swizzle K-major core-matrix layout: a core matrix is 8 rows x 16 bytes
+// (8 x 4 TF32 values) stored as 128 contiguous bytes; the core matrices of a
+// row group follow each other along K (128 bytes apart), and row groups are
+// KC * 128 bytes apart (KC = 16-byte chunks per row).  Element (row, k) of a
+// K-major tile therefore sits at byte
+//     (row / 8) * KC * 128 + (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4.
+#pragma once
+#include <cstdint>
+
+#include "spmc_events.cuh"
+
+namespace spmc {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// TMEM allocation (one full warp executes these)
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// ordering between thread barriers and tcgen05 operations
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of the barrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity, uint32_t max_tries = 1u << 24) {
+  for (uint32_t t = 0; t < max_tries; ++t)
+    if (mbar_try_wait(m, parity)) return true;
+  return false;
+}
+
+// Shared-memory matrix descriptor: no swizzle, base offset 0, version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: D in F32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, M x N x 8, issued by one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the mbarrier once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* m) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(m))
+               : "memory");
+}
+
+// 8 consecutive 32-bit columns of this thread's TMEM lane (warp w reads lanes 32w..32w+31).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+               : "r"(taddr)
+               : "memory");
+  v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+  v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5); v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Round to TF32 (nearest, ties away) and the FP32 remainder: x = hi + lo exactly.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  hi = __uint_as_float(u);
+  lo = x - hi;
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle tile with KC 16-byte chunks per row
+__host__ __device__ constexpr uint32_t kmajor_offset(int row, int k, int KC) {
+  return (uint32_t)((row >> 3) * KC * 128 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Tensor-core evaluation of the events of one time slice (d = 2, FP32 sweep).
+//
+// With P_a the Jacobi P^{(1,1)} polynomials, phi_a(x) = (1 - x^2) P_a(x) and
+// psi_a(x) = lam_a P_a(x) (lam_a = (a+1)(a+2)), the residual at an event
+// (x, y) needs the four bilinear forms
+//     sC = P(x)^T C P(y),  sH = P(x)^T H P(y),
+//     sL = P(x)^T (Lam C) P(y),  sR = P(x)^T (C Lam) P(y),
+// from which
+//     u = ox oy sC,   G = ox oy sH - kappa (oy sL + ox sR),   ox = 1 - x^2, oy = 1 - y^2.
+// For a tile of 128 events the left products P(x)^T [C | H | Lam C | C Lam]
+// form one (128 x K) x (K x 4 NMAX) matrix product, run on the tensor cores in
+// TF32 with the 3-term split (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32
+// accumulation in TMEM), which keeps about FP32 accuracy.  Each thread owns one
+// event = one TMEM lane: it writes its row of A, then contracts its TMEM row
+// with P(y) on the FP32 pipe.
+template <int NMAX>
+struct TcGeom {
+  static constexpr int K = NMAX;                 // contraction length (a multiple of 8)
+  static constexpr int N = 4 * NMAX;             // [C | H | Lam C | C Lam]
+  static constexpr int KC = K / 4;               // 16-byte chunks per row
+  static constexpr uint32_t SBO = KC * 128;      // bytes between 8-row groups
+  static constexpr uint32_t LBO = 128;           // bytes between K-adjacent core matrices
+  static constexpr int A_BYTES = 128 * K * 4;
+  static constexpr int B_BYTES = N * K * 4;
+  static constexpr int TM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  static constexpr int SMEM = 4 * A_BYTES + 2 * B_BYTES + 64;   // A: two buffers x (hi, lo)
+  static constexpr int CHUNK = 4096;             // events per block
+};
+
+// row `row` of A: P_a(x), a < K (zero for a >= n), split hi / lo, into the
+// K-major tile pair (hi, lo)
+template <int NMAX>
+__device__ __forceinline__ void write_a_row(unsigned char* hi, unsigned char* lo, int row, float x, int n) {
+  constexpr int KC = TcGeom<NMAX>::KC;
+  float pm2 = 1.f, pm1 = 2.f * x;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    float hv[4], lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = 4 * c + q;
+      float P;
+      if (a == 0) P = 1.f;
+      else if (a == 1) P = 2.f * x;
+      else { P = jac_ra<float>(a) * x * pm1 - jac_rb<float>(a) * pm2; pm2 = pm1; pm1 = P; }
+      tc::split_tf32(a < n ? P : 0.f, hv[q], lv[q]);
+    }
+    const uint32_t off = tc::kmajor_offset(row, 4 * c, KC);
+    *reinterpret_cast<float4*>(hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<float4*>(lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  }
+}
+
+// Events in fixed chunks of CHUNK (a chunk may span slices; each block
+// processes the slice segments of its chunk in turn).  Per segment the tiles
+// of 128 events run as a two-stage pipeline: while the tensor core works on
+// tile t, the threads build the A rows of tile t+1 in the other buffer; then
+// they read tile t's products from TMEM and finish its residuals.
+template <int NMAX>
+__global__ void __launch_bounds__(128) eval_events_tc_kernel(const long long* __restrict__ slice_node,
+                                                             const TimeNode* __restrict__ tn,
+                                                             const InstanceParams* __restrict__ ipt,
+                                                             const float* __restrict__ slices,
+                                                             const SliceInfo* __restrict__ sinfo,
+                                                             const unsigned int* __restrict__ starts,
+                                                             const Event<float>* __restrict__ events,
+                                                             double* __restrict__ acc, int n, int S,
+                                                             long long n_slices, long long sl_stride, int half,
+                                                             double kappa_d, unsigned long long n_events,
+                                                             int* status) {
+  using Gm = TcGeom<NMAX>;
+  constexpr int K = Gm::K, N = Gm::N, KC = Gm::KC;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* Abuf = smraw;                                  // [buffer][hi, lo]
+  unsigned char* Bhi = Abuf + 4 * Gm::A_BYTES;
+  unsigned char* Blo = Bhi + Gm::B_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + Gm::B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned long long c0 = (unsigned long long)blockIdx.x * Gm::CHUNK;
+  if (c0 >= n_events) return;
+  const unsigned long long c1 = min(c0 + (unsigned long long)Gm::CHUNK, n_events);
+
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, Gm::TM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+  constexpr uint32_t idesc = tc::idesc_tf32(128, N);
+  const uint32_t a0 = tc::smem_u32(Abuf), bHi = tc::smem_u32(Bhi), bLo = tc::smem_u32(Blo);
+  const float kappa = (float)kappa_d;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  unsigned long long pos = c0;
+  while (pos < c1 && ok) {
+    // the slice holding event pos: the last s with starts[s S] <= pos
+    long long lo_s = 0, hi_s = n_slices - 1;
+    while (lo_s < hi_s) {
+      const long long mid = (lo_s + hi_s + 1) >> 1;
+      if ((unsigned long long)starts[mid * S] <= pos) lo_s = mid; else hi_s = mid - 1;
+    }
+    const long long sidx = lo_s;
+    const unsigned long long s_end = (sidx + 1 < n_slices) ? (unsigned long long)starts[(sidx + 1) * S] : n_events;
+    const unsigned long long g1 = min(c1, s_end);
+
+    // B = [C | H | Lam C | C Lam] of this slice as N rows of K, split hi / lo
+    const float* src = slices + sidx * sl_stride;
+    for (int idx = tid; idx < N * K; idx += 128) {
+      const int nn = idx / K, a = idx - nn * K;
+      const int blk = nn / NMAX, b = nn - blk * NMAX;
+      float v = 0.f;
+      if (a < n && b < n) {
+        const float c = src[a * NMAX + b];
+        if (blk == 0) v = c;
+        else if (blk == 1) v = src[half + a * NMAX + b];
+        else if (blk == 2) v = jac_lam<float>(a) * c;
+        else v = c * jac_lam<float>(b);
+      }
+      float h, l;
+      tc::split_tf32(v, h, l);
+      const uint32_t off = tc::kmajor_offset(nn, a, KC);
+      *reinterpret_cast<float*>(Bhi + off) = h;
+      *reinterpret_cast<float*>(Blo + off) = l;
+    }
+    const long long ti = slice_node[sidx];
+    const TimeNode node = tn[ti];
+    const InstanceParams ip = ipt[node.inst];
+    const SliceInfo si = sinfo[sidx];
+    const float Tt = (float)si.Tt, dTt = (float)si.dTt;
+    const unsigned int key0 = (unsigned int)(sidx * S);
+
+    // tile 0 of the segment
+    const int n_tiles = (int)((g1 - pos + 127) / 128);
+    float4 cur = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+    bool cur_has = pos + tid < g1;
+    if (cur_has) cur = *reinterpret_cast<const float4*>(events + pos + tid);
+    write_a_row<NMAX>(Abuf, Abuf + Gm::A_BYTES, tid, cur.x, n);
+    tc::fence_async_smem();
+    __syncthreads();
+    auto issue = [&](int buf) {
+      tc::fence_after();
+      const uint32_t ah = a0 + (uint32_t)(2 * buf) * Gm::A_BYTES, al = ah + Gm::A_BYTES;
+#pragma unroll
+      for (int s = 0; s < K / 8; ++s) {
+        const uint32_t ko = (uint32_t)s * 256;   // 8 TF32 = two core matrices along K
+        tc::mma_tf32(tbase, tc::sdesc(al + ko, Gm::LBO, Gm::SBO), tc::sdesc(bHi + ko, Gm::LBO, Gm::SBO), idesc,
+                     s > 0 ? 1u : 0u);
+        tc::mma_tf32(tbase, tc::sdesc(ah + ko, Gm::LBO, Gm::SBO), tc::sdesc(bLo + ko, Gm::LBO, Gm::SBO), idesc, 1u);
+        tc::mma_tf32(tbase, tc::sdesc(ah + ko, Gm::LBO, Gm::SBO), tc::sdesc(bHi + ko, Gm::LBO, Gm::SBO), idesc, 1u);
+      }
+      tc::mma_commit(mbar);
+    };
+    if (tid == 0) issue(0);
+
+    for (int t = 0; t < n_tiles; ++t) {
+      // stage 1: A rows of tile t+1 (other buffer) while the MMA of tile t runs
+      float4 nxt = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+      bool nxt_has = false;
+      if (t + 1 < n_tiles) {
+        const unsigned long long i = pos + (unsigned long long)(t + 1) * 128 + tid;
+        nxt_has = i < g1;
+        if (nxt_has) nxt = *reinterpret_cast<const float4*>(events + i);
+        const int b = (t + 1) & 1;
+        write_a_row<NMAX>(Abuf + 2 * b * Gm::A_BYTES, Abuf + (2 * b + 1) * Gm::A_BYTES, tid, nxt.x, n);
+      }
+      // P_b(y) of tile t
+      const float y0 = cur.x, y1 = cur.y;
+      float Py[NMAX];
+      {
+        float pm2 = 1.f, pm1 = 2.f * y1;
+#pragma unroll
+        for (int b = 0; b < NMAX; ++b) {
+          float P;
+          if (b == 0) P = 1.f;
+          else if (b == 1) P = 2.f * y1;
+          else { P = jac_ra<float>(b) * y1 * pm1 - jac_rb<float>(b) * pm2; pm2 = pm1; pm1 = P; }
+          Py[b] = b < n ? P : 0.f;
+        }
+      }
+      // stage 2: products of tile t
+      if (!tc::mbar_wait_bounded(mbar, phase)) ok = false;
+      phase ^= 1u;
+      tc::fence_after();
+      float sv[4];
+#pragma unroll
+      for (int blk = 0; blk < 4; ++blk) {
+        float v[NMAX];
+#pragma unroll
+        for (int c8 = 0; c8 < NMAX / 8; ++c8) tc::tmem_ld8(lane_base + (uint32_t)(blk * NMAX + c8 * 8), v + 8 * c8);
+        tc::tmem_ld_wait();
+        float s = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < NMAX; q += 2) {
+          s = fmaf(v[q], Py[q], s);
+          s2 = fmaf(v[q + 1], Py[q + 1], s2);
+        }
+        sv[blk] = s + s2;
+      }
+      double val = 0.0;
+      const unsigned int key = cur_has ? __float_as_uint(cur.w) : 0xffffffffu;
+      if (cur_has) {
+        const float ox = 1.f - y0 * y0, oy = 1.f - y1 * y1;
+        const float u = ox * oy * sv[0];
+        const float G = ox * oy * sv[1] - kappa * (oy * sv[2] + ox * sv[3]);
+        const float yy[2] = {y0, y1};
+        const float res = reaction<float>(ip, u) + source<2, float>(ip, kappa, yy, Tt, dTt) + G;
+        val = (double)(cur.z * res);
+      }
+      // per-node sums: events are sorted by key, so equal keys are adjacent lanes
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, val, d);
+        const unsigned int ok2 = __shfl_down_sync(0xffffffffu, key, d);
+        if (lane + d < 32 && ok2 == key) val += o;
+      }
+      const unsigned int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+      if (cur_has && (lane == 0 || kprev != key)) atomicAdd(&acc[ti * S + (key - key0)], val);
+      tc::fence_async_smem();
+      tc::fence_before();
+      const bool all_ok = !__syncthreads_or(!ok);
+      if (!all_ok) { ok = false; break; }
+      if (t + 1 < n_tiles && tid == 0) issue((t + 1) & 1);
+      cur = nxt;
+      cur_has = nxt_has;
+    }
+    pos = g1;
+  }
+  if (!ok) {
+    // an MMA did not complete in time: report, give it one more bounded wait, stop
+    if (tid == 0) atomicOr(status, 8);
+    tc::mbar_wait_bounded(mbar, phase ^ 1u);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tbase, Gm::TM_COLS);
+  }
+}
+
+}  // namespace spmc
