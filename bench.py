@@ -115,6 +115,64 @@ def flops_per_point(dim, n):
     return 2 * 3 * n + 10 * n
 
 
+def walk_ops_per_event(dim, fill):
+    """Algorithmic 32-bit operations of one walk step that ends in an evaluation
+    event: Philox4x32-10 blocks (10 rounds x (2 32x32->64 multiplies = 4 ops,
+    4 xors) + 9 key bumps x 2 adds = 98 ops) -- two per step (d = 2; one at
+    d = 1), a third for the Green point's radius words when the event is
+    written (fill pass, d = 2) -- plus the step's geometry (distance, ball,
+    weight, sub-point, the sin/cos pairs and the Green radius, about 60 FP32
+    ops)."""
+    blocks = (3 if fill else 2) if dim == 2 else 2
+    return 98 * blocks + 60
+
+
+def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
+    """Per-kernel roofline figures of the event sweep and the dominant one."""
+    from paper_2608_22190_b300 import _lib as L
+    n = wl.n_space
+    nmax = 8 if n <= 8 else (16 if n <= 16 else (24 if n <= 24 else 32))
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12          # lane-ops/s (one FP32 or INT32 lane op per cycle)
+    tf32_ratio = 1.1 / 2.25                               # nominal dense TF32 / BF16 (recipe table)
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1375.3)
+    kern = {}
+    t_count, t_fill, t_eval = st["walk_ms"] / 1e3, st["fill_ms"] / 1e3, st["eval_ms"] / 1e3
+    per_ev_c, per_ev_f = walk_ops_per_event(wl.dim, False), walk_ops_per_event(wl.dim, True)
+    if t_count > 0:
+        a = points * per_ev_c / t_count / 1e12
+        kern["walk_count"] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s", "frac": a / alu_peak,
+                              "ms": t_count * 1e3 / steps, "ops_per_event": per_ev_c}
+    if t_fill > 0:
+        a = points * per_ev_f / t_fill / 1e12
+        kern["walk_fill"] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s", "frac": a / alu_peak,
+                             "ms": t_fill * 1e3 / steps, "ops_per_event": per_ev_f}
+    if t_eval > 0:
+        if prec == L.MIXED and wl.dim == 2:
+            fpe = 2 * nmax * 4 * nmax                     # one (1 x K)(K x 4 NMAX) product per event
+            peak = bf16_sus * tf32_ratio
+            a = points * fpe / t_eval / 1e12
+            kern["eval_tc"] = {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                               "ms": t_eval * 1e3 / steps, "flops_per_event": fpe,
+                               "executed_tensor_tflops": 3 * a,
+                               "peak_source": "bf16_tflops_sustained (MEASURED_PEAKS.json) x nominal TF32/BF16 1.1/2.25"}
+        else:
+            fpe = flops_per_point(wl.dim, n)
+            peak = 1.25 if prec == L.FP64 else alu_peak * 2
+            a = points * fpe / t_eval / 1e12
+            kern["eval_alu"] = {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                                "ms": t_eval * 1e3 / steps, "flops_per_event": fpe,
+                                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if prec == L.FP64
+                                else "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
+    name = max(kern, key=lambda k: kern[k]["ms"]) if kern else None
+    roof = dict(kern[name]) if name else {}
+    if name:
+        roof["kernel"] = name
+        roof["share_of_step"] = roof["ms"] / step_ms
+        roof["traffic"] = None
+    return roof, kern
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -228,27 +286,15 @@ def run_ours(args):
     per_step = sum(node_samples_per_interval(wl, r) for r in done) / len(done)
     value = per_step * world / (ms / 1e3)
 
-    # roofline of the dominant kernel (the sweep): algorithmic flops / its event time
+    # roofline of the dominant kernel of the sweep (by device time in the timed
+    # region; every launch bracketed by CUDA events on the launching stream)
     points = st["points"] - base_points
-    fpp = flops_per_point(wl.dim, wl.n_space)
-    sweep_s = st["sweep_ms"] / 1e3
     peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    if prec == L.MIXED:
-        peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock
-        bound = "alu"
-    else:
-        peak = 1.25                                     # nominal FP64 rate of the recipe's table
-        bound = "alu"
-    achieved = points * fpp / sweep_s / 1e12 if sweep_s > 0 else None
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "sweep_kernel", "sweep_share": sweep_s * 1e3 / (ms * args.steps),
-            "flops_per_point": fpp, "points_per_step": points // max(1, args.steps),
-            "peak_source": "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz (MEASURED_PEAKS.json)" if prec == L.MIXED
-            else "nominal FP64 1.25 TFLOP/s (recipe table)"}
-    launches_per_step = 1 + 4 * wl.K     # hand-off (or first iterate), then per iteration:
-    # reconstruction, slices, sweep, update
+    roof, kernels = sweep_roofline(wl, prec, points, st, peaks, args.steps, ms)
+    batches = st["eval_launches"]
+    # per step: hand-off (or first iterate); per iteration: reconstruction,
+    # slices, update; per batch: count walk, three scan kernels, fill walk, evaluation
+    launches = args.steps * (1 + 3 * wl.K) + 6 * batches
 
     line = {"metric": "node-samples/sec & time to L-inf err 1e-6: batched mixed vs plain FP64, 1 B300",
             "value": value, "unit": "node-samples/s", "n_gpus": world, "steps": args.steps,
@@ -262,8 +308,8 @@ def run_ours(args):
                        "node_samples_per_step": per_step,
                        "step": "one interval of the hp solve: hand-off + K = 8 iterations",
                        "intervals_timed": done},
-            "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps, "roofline": roof,
-            "wall_s": t_wall, "autotune": {"sweep_ms": tune_ms, "nodes_per_cohort": None}}
+            "clocks": clk.summary(), "gpu_launches": launches, "roofline": roof, "kernels": kernels,
+            "wall_s": t_wall, "autotune": {"sweep_ms": tune_ms}}
 
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(args, wl, prec)

@@ -104,9 +104,10 @@ typedef struct {
   double last_max_eps;
   long long sweep_launches; /* sweep kernel launches timed (spmc_set_timing) */
   double sweep_ms;          /* their summed duration, from CUDA events on the caller's stream */
-  double walk_ms;           /* event sweep: the two walk passes and the scan (part of sweep_ms) */
+  double walk_ms;           /* event sweep: the counting walk pass and the scan (part of sweep_ms) */
   double eval_ms;           /* event sweep: the per-slice evaluation launches (part of sweep_ms) */
   long long eval_launches;
+  double fill_ms;           /* event sweep: the placing walk pass (part of sweep_ms) */
 } spmc_stats;
 
 /* Validate desc, build the node tables and allocate the workspace.

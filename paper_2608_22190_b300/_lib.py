@@ -45,7 +45,8 @@ class Stats(C.Structure):
     _fields_ = [("node_samples", C.c_longlong), ("points", C.c_longlong), ("capped", C.c_longlong),
                 ("iterations_run", C.c_int), ("last_max_eps", C.c_double),
                 ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
-                ("walk_ms", C.c_double), ("eval_ms", C.c_double), ("eval_launches", C.c_longlong)]
+                ("walk_ms", C.c_double), ("eval_ms", C.c_double), ("eval_launches", C.c_longlong),
+                ("fill_ms", C.c_double)]
 
 
 # The C-ABI entry points and their signatures, as declared in include/spmc.h.

@@ -178,7 +178,8 @@ class Plan:
         L.check(L.lib.spmc_get_stats(self._h, C.byref(s)), self._h)
         return {"points": s.points, "capped": s.capped, "iterations_run": s.iterations_run,
                 "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms,
-                "walk_ms": s.walk_ms, "eval_ms": s.eval_ms, "eval_launches": s.eval_launches}
+                "walk_ms": s.walk_ms, "fill_ms": s.fill_ms, "eval_ms": s.eval_ms,
+                "eval_launches": s.eval_launches}
 
     def autotune(self, interval: int = 0, stream=None) -> float:
         """Pick the sweep's cohort width by timing one sweep per candidate (nodal values unchanged)."""

@@ -51,7 +51,7 @@ struct EventArgs {
 // the same walks again (pure functions of their Philox streams) and writes each
 // event into its place.  Lanes with the same key share one atomic.
 template <int D, typename R, bool FILL>
-__global__ void __launch_bounds__(256) walk_events_kernel(EventArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kernel(EventArgs a) {
   namespace cg = cooperative_groups;
   const int S = a.S, n = a.n, G = a.n_sub;
   const long long nb = a.nb;

@@ -109,7 +109,7 @@ struct spmc_plan_s {
   std::vector<long long*> d_first_tn;   // per round: instance ranges of the time-node table
   bool grad_ready = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
-  std::vector<int> ev_cat;           // per pending pair: 0 sweep, 1 event walks, 2 event evaluation
+  std::vector<int> ev_cat;           // per pending pair: 0 sweep, 1 count walks + scan, 2 evaluation, 3 fill walks
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
 };
 
@@ -651,7 +651,12 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   int dev = 0, sms = 0;
   SPMC_CUDA(cudaGetDevice(&dev));
   SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned wgrid = (unsigned)(sms * 8);
+  // one wave of resident blocks: every thread then gets the same number of walks
+  int occ_c = 0, occ_f = 0;
+  SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, walk_events_kernel<D, R, false>, 256, 0));
+  SPMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, walk_events_kernel<D, R, true>, 256, 0));
+  const unsigned wgrid_c = (unsigned)(sms * std::max(1, occ_c));
+  const unsigned wgrid_f = (unsigned)(sms * std::max(1, occ_f));
   // samples per batch: about 2^25 walks per batch
   long long nb = plan->ev_batch > 0 ? plan->ev_batch : std::max(1LL, (1LL << 25) / (n_tn * S));
   nb = std::min<long long>(nb, d.M);
@@ -662,28 +667,28 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     std::pair<cudaEvent_t, cudaEvent_t> tw{nullptr, nullptr}, te{nullptr, nullptr};
     if (timer_begin(plan, stream, tw) != SPMC_OK) return SPMC_ERR_CUDA;
     SPMC_CUDA(cudaMemsetAsync(plan->d_counts, 0, sizeof(unsigned int) * nkeys, stream));
-    walk_events_kernel<D, R, false><<<wgrid, 256, 0, stream>>>(a);
+    walk_events_kernel<D, R, false><<<wgrid_c, 256, 0, stream>>>(a);
     SPMC_CUDA(cudaGetLastError());
     scan_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(plan->d_counts, plan->d_bsum, nkeys);
     scan_totals_kernel<<<1, 1024, 0, stream>>>(plan->d_bsum, nblk, plan->d_total);
     scan_add_kernel<<<(unsigned)((nkeys + 255) / 256), 256, 0, stream>>>(plan->d_counts, plan->d_bsum,
                                                                           plan->d_starts, nkeys);
     SPMC_CUDA(cudaGetLastError());
+    if (timer_end(plan, stream, tw, 1) != SPMC_OK) return SPMC_ERR_CUDA;
     unsigned long long total = 0;
     SPMC_CUDA(cudaMemcpyAsync(&total, plan->d_total, sizeof(total), cudaMemcpyDeviceToHost, stream));
     SPMC_CUDA(cudaStreamSynchronize(stream));
     if (total > 0xffffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch above 2^32 events");
-    if (total == 0) {
-      if (timer_end(plan, stream, tw, 1) != SPMC_OK) return SPMC_ERR_CUDA;
-      continue;
-    }
+    if (total == 0) continue;
     if (grow(plan, &plan->d_events, &plan->events_bytes, sizeof(Event<R>) * (size_t)total) != SPMC_OK)
       return SPMC_ERR_OOM;
     a.events = plan->d_events;
     a.cap = plan->events_bytes / sizeof(Event<R>);
-    walk_events_kernel<D, R, true><<<wgrid, 256, 0, stream>>>(a);
+    std::pair<cudaEvent_t, cudaEvent_t> tf{nullptr, nullptr};
+    if (timer_begin(plan, stream, tf) != SPMC_OK) return SPMC_ERR_CUDA;
+    walk_events_kernel<D, R, true><<<wgrid_f, 256, 0, stream>>>(a);
     SPMC_CUDA(cudaGetLastError());
-    if (timer_end(plan, stream, tw, 1) != SPMC_OK) return SPMC_ERR_CUDA;
+    if (timer_end(plan, stream, tf, 3) != SPMC_OK) return SPMC_ERR_CUDA;
     if (timer_begin(plan, stream, te) != SPMC_OK) return SPMC_ERR_CUDA;
     const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS;
     if (tensor) {
@@ -827,6 +832,7 @@ void drain_timing(spmc_plan_t plan) {
     if (cudaEventSynchronize(ev.second) == cudaSuccess && cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
       if (cat == 0) { plan->stats.sweep_ms += ms; plan->stats.sweep_launches += 1; }
       else if (cat == 1) plan->stats.walk_ms += ms;
+      else if (cat == 3) plan->stats.fill_ms += ms;
       else { plan->stats.eval_ms += ms; plan->stats.eval_launches += 1; }
     }
     plan->ev_free.push_back(ev);
@@ -1459,7 +1465,7 @@ spmc_status spmc_set_timing(spmc_plan_t plan, int enable) {
   plan->timing = enable != 0;
   if (plan->timing) {
     plan->stats.sweep_ms = 0.0; plan->stats.sweep_launches = 0;
-    plan->stats.walk_ms = 0.0; plan->stats.eval_ms = 0.0; plan->stats.eval_launches = 0;
+    plan->stats.walk_ms = 0.0; plan->stats.fill_ms = 0.0; plan->stats.eval_ms = 0.0; plan->stats.eval_launches = 0;
   }
   return SPMC_OK;
 }
