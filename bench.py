@@ -7,8 +7,9 @@ One step = one interval of the hp solve: the hand-off from the previous interval
 (Algorithm 1, Step 4) and K residual iterations (Steps 1-3); consecutive steps
 continue the solve interval after interval.  Inputs are resident in HBM; L2 is
 flushed between steps outside the timed events.  The JSON
-line also carries the FP64 path's throughput on a bounded run, the sweep
-kernel's roofline figures, an end-to-end figure through the C-ABI with host
+line also carries the FP64 path's throughput on a bounded run, the roofline
+figures of the sweep's kernels (count walk, fill walk, evaluation; the
+dominant one as `roofline`), an end-to-end figure through the C-ABI with host
 buffers, and the CPU oracle's throughput on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -164,12 +165,19 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
                                 "ms": t_eval * 1e3 / steps, "flops_per_event": fpe,
                                 "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if prec == L.FP64
                                 else "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
+    # DRAM bytes per event from one ncu capture of each kernel as it is now
+    # (profiles/walk_fill_w2_fullset.md, profiles/eval_tc_w2_fullset.md: M = 1024,
+    # 1.0216e8 events), scaled by the events of one launch; traffic grows with the events
+    per_event_bytes = {"walk_fill": (0.836140 + 2.335618) * 1e9 / 1.0216e8,
+                       "eval_tc": (1.659414 + 0.003520) * 1e9 / 1.0216e8}
+    launches = max(1, st["eval_launches"])
+    for k, v in kern.items():
+        v["traffic"] = per_event_bytes[k] * points / launches if (k in per_event_bytes and wl.dim == 2) else None
     name = max(kern, key=lambda k: kern[k]["ms"]) if kern else None
     roof = dict(kern[name]) if name else {}
     if name:
         roof["kernel"] = name
         roof["share_of_step"] = roof["ms"] / step_ms
-        roof["traffic"] = None
     return roof, kern
 
 
