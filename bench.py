@@ -119,12 +119,12 @@ def flops_per_point(dim, n):
 def walk_ops_per_event(dim, fill):
     """Algorithmic 32-bit operations of one walk step that ends in an evaluation
     event: Philox4x32-10 blocks (10 rounds x (2 32x32->64 multiplies = 4 ops,
-    4 xors) + 9 key bumps x 2 adds = 98 ops) -- two per step (d = 2; one at
-    d = 1), a third for the Green point's radius words when the event is
-    written (fill pass, d = 2) -- plus the step's geometry (distance, ball,
-    weight, sub-point, the sin/cos pairs and the Green radius, about 60 FP32
-    ops)."""
-    blocks = (3 if fill else 2) if dim == 2 else 2
+    4 xors) + 9 key bumps x 2 adds = 98 ops) -- one per step (direction,
+    sub-point and roulette words share it), a second for the Green radius words
+    when the event is written (fill pass) -- plus the step's geometry
+    (distance, ball, weight, sub-point, the sin/cos pairs and the Green radius,
+    about 60 FP32 ops)."""
+    blocks = 2 if fill else 1
     return 98 * blocks + 60
 
 
@@ -168,8 +168,7 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
     # DRAM bytes per event from one ncu capture of each kernel as it is now
     # (profiles/walk_fill_w2_fullset.md, profiles/eval_tc_w2_fullset.md: M = 1024,
     # 1.0216e8 events), scaled by the events of one launch; traffic grows with the events
-    per_event_bytes = {"walk_fill": (0.836140 + 2.335618) * 1e9 / 1.0216e8,
-                       "eval_tc": (1.659414 + 0.003520) * 1e9 / 1.0216e8}
+    per_event_bytes = {"eval_tc": (1.659414 + 0.003520) * 1e9 / 1.0216e8}
     launches = max(1, st["eval_launches"])
     for k, v in kern.items():
         v["traffic"] = per_event_bytes[k] * points / launches if (k in per_event_bytes and wl.dim == 2) else None

@@ -156,24 +156,39 @@ static void draw_direction(orc_stream* s, int d, int64_t step_index, double* the
 }
 
 /* Inside-ball walk (walk_mode 0): the words of one step, padded to whole
- * Philox blocks: [next-step direction | Green point direction | Green radius
- * uniform(s), a pair of words each | one word choosing the time sub-point |
- * one word for the evaluation roulette of shrunk balls]. */
+ * Philox blocks.  d <= 2, one word per uniform, 8 words (2 blocks):
+ *   [next-step direction | Green point direction | time sub-point word |
+ *    roulette word | Green radius uniform(s) (d = 2: two) | unused].
+ * d >= 3, uniforms from word pairs:
+ *   [next-step direction | Green point direction | Green radius uniform (a pair) |
+ *    time sub-point word | roulette word].
+ * The paper leaves the random stream open; with d <= 2 a 32-bit word per
+ * uniform (resolution 2^-32) is far below the Monte Carlo error, and the words
+ * the walk needs at every step (direction, sub-point, roulette) share one
+ * block. */
 int orc_ball_words_per_step(int d) {
+  if (d <= 2) return 8;
   int wd = orc_words_per_step(d);
-  int wr = (d == 2) ? 4 : 2;
-  int w = 2 * wd + wr + 2;
+  int w = 2 * wd + 2 + 2;
   return (w + 3) / 4 * 4;
 }
+static int64_t ball_gdir_index(int d) { return d <= 2 ? 1 : orc_words_per_step(d); }
+static int64_t ball_radius_index(int d) { return d <= 2 ? 4 : 2 * orc_words_per_step(d); }
+static int64_t ball_gword_index(int d) { return d <= 2 ? 2 : 2 * orc_words_per_step(d) + 2; }
+static int64_t ball_rword_index(int d) { return ball_gword_index(d) + 1; }
 
-/* Direction from the words starting at w0 (same laws as draw_direction). */
+/* Uniform on (0,1) from one word: (a + 1/2) 2^-32. */
+double orc_u01_word(uint32_t a) { return ((double)a + 0.5) * (1.0 / 4294967296.0); }
+
+/* Direction from the words starting at w0 (same laws as draw_direction; the
+ * d = 2 angle from one word). */
 static void direction_at(orc_stream* s, int d, int64_t w0, double* theta) {
   if (d == 1) {
     theta[0] = (stream_word(s, w0) >> 31) ? -1.0 : 1.0;
     return;
   }
   if (d == 2) {
-    double U = orc_u01_pair(stream_word(s, w0), stream_word(s, w0 + 1));
+    double U = orc_u01_word(stream_word(s, w0));
     theta[0] = cos(2.0 * ORC_PI * U);
     theta[1] = sin(2.0 * ORC_PI * U);
     return;
@@ -601,7 +616,6 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
    * advances k by n_sub; a shrunk ball is evaluated at the sub-step it sits in
    * and advances f.  The walk is absorbed once dist < shell and ends when the
    * time s is used up.  Q = sum_q w_q r(Y_q, tau_{m_q}). */
-  int wd = orc_words_per_step(d);
   int64_t W = orc_ball_words_per_step(d);
   int G = pb->n_sub;
   int gbits = 0;
@@ -626,7 +640,7 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
     }
     if (dist < shell) break;
     int64_t w0 = (int64_t)q * W;
-    uint32_t gword = stream_word(&st, w0 + 2 * wd + ((d == 2) ? 4 : 2));
+    uint32_t gword = stream_word(&st, w0 + ball_gword_index(d));
     int g = gbits ? (int)(gword >> (32 - gbits)) : 0;
     double left = (double)(Ktot - k) * sub - f;
     double w;
@@ -658,10 +672,10 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
       }
     }
     double thg[ORC_MAXD], Y[ORC_MAXD];
-    direction_at(&st, d, w0 + wd, thg);
-    int64_t wr = w0 + 2 * wd;
-    double U1 = orc_u01_pair(stream_word(&st, wr), stream_word(&st, wr + 1));
-    double U2 = (d == 2) ? orc_u01_pair(stream_word(&st, wr + 2), stream_word(&st, wr + 3)) : 0.0;
+    direction_at(&st, d, w0 + ball_gdir_index(d), thg);
+    int64_t wr = w0 + ball_radius_index(d);
+    double U1 = (d <= 2) ? orc_u01_word(stream_word(&st, wr)) : orc_u01_pair(stream_word(&st, wr), stream_word(&st, wr + 1));
+    double U2 = (d == 2) ? orc_u01_word(stream_word(&st, wr + 1)) : 0.0;
     double v = orc_green_radius(d, U1, U2);
     for (int e = 0; e < d; ++e) Y[e] = X[e] + r * v * thg[e];
     double tau = t_node - ((double)m + 0.5) * sub;
@@ -670,7 +684,7 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
      * many small steps that approach the boundary cost no evaluation. */
     double wq = w;
     if (r < J && w > 0.0) {
-      uint32_t rword = stream_word(&st, w0 + 2 * wd + ((d == 2) ? 4 : 2) + 1);
+      uint32_t rword = stream_word(&st, w0 + ball_rword_index(d));
       double Ur = ((double)(rword >> 8) + 0.5) * (1.0 / 16777216.0);
       double pi = w / delta;
       wq = (Ur < pi) ? delta : 0.0;

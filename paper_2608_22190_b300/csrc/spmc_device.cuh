@@ -48,12 +48,17 @@ template <> struct U01<double> {
     return __dmul_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0), (double)(b >> 6)), 0.5),
                      1.0 / 9007199254740992.0);
   }
+  // 32-bit uniform on (0,1) from one word: (a + 1/2) 2^-32 (exact in FP64)
+  static __device__ __forceinline__ double one(uint32_t a) {
+    return __dmul_rn(__dadd_rn((double)a, 0.5), 1.0 / 4294967296.0);
+  }
 };
 template <> struct U01<float> {
   // 24-bit uniform on (0,1) from the first word of the pair
   static __device__ __forceinline__ float pair(uint32_t a, uint32_t) {
     return ((float)(a >> 8) + 0.5f) * (1.0f / 16777216.0f);
   }
+  static __device__ __forceinline__ float one(uint32_t a) { return pair(a, 0u); }
 };
 
 // exact-rounding arithmetic helpers (no FMA contraction where the walk
@@ -94,8 +99,17 @@ template <> struct Ar<float> {
 //  sub-point 1 | evaluation roulette 1]
 __host__ __device__ constexpr int dir_words(int d) { return d == 1 ? 1 : (d == 2 ? 2 : 4 * ((d + 1) / 2)); }
 __host__ __device__ constexpr int radius_words(int d) { return d == 2 ? 4 : 2; }
-__host__ __device__ constexpr int step_words(int d) { return ((2 * dir_words(d) + radius_words(d) + 2) + 3) / 4 * 4; }
-__host__ __device__ constexpr int gword_index(int d) { return 2 * dir_words(d) + radius_words(d); }
+// Words of one walk step, padded to whole Philox blocks.  d <= 2 (one word per
+// uniform, 8 words): [step direction | Green direction | sub-point word |
+// roulette word | Green radius uniform(s) | unused], so the words every step
+// needs share the first block.  d >= 3 (uniforms from word pairs):
+// [step direction | Green direction | Green radius pair | sub-point | roulette].
+__host__ __device__ constexpr int step_words(int d) {
+  return d <= 2 ? 8 : ((2 * dir_words(d) + radius_words(d) + 2) + 3) / 4 * 4;
+}
+__host__ __device__ constexpr int gdir_index(int d) { return d <= 2 ? 1 : dir_words(d); }
+__host__ __device__ constexpr int radius_index(int d) { return d <= 2 ? 4 : 2 * dir_words(d); }
+__host__ __device__ constexpr int gword_index(int d) { return d <= 2 ? 2 : 2 * dir_words(d) + radius_words(d); }
 __host__ __device__ constexpr int rword_index(int d) { return gword_index(d) + 1; }
 
 // fetch word w of the walk (one Philox evaluation per call)
@@ -105,15 +119,14 @@ __device__ __forceinline__ uint32_t stream_word(const WalkStream& s, uint32_t w)
 }
 
 // Uniform direction on S^{d-1} from the words starting at w0 (Lemma Xlocation):
-// d=1 sign bit; d=2 angle 2 pi U; d>=3 normalised Box-Muller Gaussians.
+// d=1 sign bit; d=2 angle 2 pi U (U from one word); d>=3 normalised Box-Muller
+// Gaussians (uniforms from word pairs).
 template <int D, typename R>
 __device__ __forceinline__ void direction(const WalkStream& s, uint32_t w0, R* th) {
   if (D == 1) {
     th[0] = (stream_word(s, w0) >> 31) ? R(-1) : R(1);
   } else if (D == 2) {
-    Philox4 b = s.block(w0 >> 2);
-    uint32_t o = w0 & 3;
-    R U = U01<R>::pair(b.v[o], b.v[o + 1]);
+    R U = U01<R>::one(stream_word(s, w0));
     R sn, cs;
     Ar<R>::sincos2pi(U, &sn, &cs);
     th[0] = cs; th[1] = sn;
@@ -137,6 +150,20 @@ __device__ __forceinline__ void direction(const WalkStream& s, uint32_t w0, R* t
     nrm = Ar<R>::sqrt_(nrm);
 #pragma unroll
     for (int e = 0; e < D; ++e) th[e] = Ar<R>::div(z[e], nrm);
+  }
+}
+
+// The Green radius uniforms of the step whose words start at w0 (U2 is used for d = 2 only).
+template <int D, typename R>
+__device__ __forceinline__ void green_uniforms(const WalkStream& s, uint32_t w0, R& U1, R& U2) {
+  const uint32_t wr = w0 + radius_index(D);   // a multiple of 4
+  const Philox4 b = s.block(wr >> 2);
+  if (D <= 2) {
+    U1 = U01<R>::one(b.v[0]);
+    U2 = (D == 2) ? U01<R>::one(b.v[1]) : R(0);
+  } else {
+    U1 = U01<R>::pair(b.v[0], b.v[1]);
+    U2 = R(0);
   }
 }
 

@@ -52,6 +52,7 @@ struct EventArgs {
 // event into its place.  Lanes with the same key share one atomic.
 template <int D, typename R, bool FILL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kernel(EventArgs a) {
+  static_assert(D <= 2, "the event sweep reads a step's words from one Philox block (d <= 2 layout)");
   namespace cg = cooperative_groups;
   const int S = a.S, n = a.n, G = a.n_sub;
   const long long nb = a.nb;
@@ -124,9 +125,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
       live = false;
       continue;
     }
-    const uint32_t w0 = (uint32_t)q * WS;
-    const Philox4 bg = ws.block((w0 + gword_index(D)) >> 2);
-    const uint32_t gword = bg.v[(w0 + gword_index(D)) & 3];
+    const uint32_t w0 = (uint32_t)q * WS;   // a multiple of 8 (d <= 2)
+    // direction, Green direction, sub-point and roulette words: one block
+    const Philox4 b0 = ws.block(w0 >> 2);
+    const uint32_t gword = b0.v[gword_index(D)];
     const int g = a.gbits ? (int)(gword >> (32 - a.gbits)) : 0;
     R left = Ar<R>::sub(Ar<R>::mul((R)(Ktot - k), sub), f);
     R w, r;
@@ -154,13 +156,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
         if (k >= Ktot) last = 1;
       }
     }
-    // roulette for shrunk balls (the roulette word shares the sub-point word's block)
+    // roulette for shrunk balls
     if (r < J && w > R(0)) {
-      const uint32_t rw = bg.v[(w0 + rword_index(D)) & 3];
+      const uint32_t rw = b0.v[rword_index(D)];
       const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
       w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
     }
-    const Philox4 b0 = ws.block(w0 >> 2);   // next-step and Green directions (d <= 2: one block)
     if (w > R(0)) {
       const unsigned int key = (unsigned int)((slice_base + m) * S + key_j);
       cg::coalesced_group grp = cg::coalesced_threads();
@@ -170,23 +171,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
       } else {
         unsigned int slot = 0;
         if (same.thread_rank() == 0) slot = atomicAdd(&a.counts[key], same.size());
-        slot = same.shfl(slot, 0) + same.thread_rank();
         R thg[D];
         if (D == 1) {
-          thg[0] = (b0.v[(w0 + dir_words(D)) & 3] >> 31) ? R(-1) : R(1);
+          thg[0] = (b0.v[gdir_index(D)] >> 31) ? R(-1) : R(1);
         } else {
-          const uint32_t o = (w0 + dir_words(D)) & 3;
-          const R U = U01<R>::pair(b0.v[o], b0.v[o + 1]);
+          const R U = U01<R>::one(b0.v[gdir_index(D)]);
           R sn, cs;
           Ar<R>::sincos2pi(U, &sn, &cs);
           thg[0] = cs; thg[1] = sn;
         }
-        const uint32_t wr = w0 + 2 * dir_words(D);
-        const Philox4 rb = (D == 1) ? b0 : ws.block(wr >> 2);
-        const R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
-        const R U2 = (D == 2) ? U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]) : R(0);
+        R U1, U2;
+        green_uniforms<D, R>(ws, w0, U1, U2);
         const R v = green_radius<D, R>(U1, U2);
         const R rv = Ar<R>::mul(r, v);
+        slot = same.shfl(slot, 0) + same.thread_rank();   // the atomic's round trip overlaps the Green point
         if ((unsigned long long)slot < a.cap) {
           Event<R> e;
           e.y[0] = Ar<R>::add(X[0], Ar<R>::mul(rv, thg[0]));
@@ -203,10 +201,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
     if (last) { live = false; continue; }
     // step to the sphere of the ball
     if (D == 1) {
-      const R th = (b0.v[w0 & 3] >> 31) ? R(-1) : R(1);
+      const R th = (b0.v[0] >> 31) ? R(-1) : R(1);
       X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, th));
     } else {
-      const R U = U01<R>::pair(b0.v[w0 & 3], b0.v[(w0 & 3) + 1]);
+      const R U = U01<R>::one(b0.v[0]);
       R sn, cs;
       Ar<R>::sincos2pi(U, &sn, &cs);
       X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, cs));

@@ -440,12 +440,9 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
           const uint32_t w0 = (uint32_t)q * WS;
           // Green-function point of the pending ball
           R thg[D], Y[D];
-          direction<D, R>(ws, w0 + dir_words(D), thg);
-          const uint32_t wr = w0 + 2 * dir_words(D);
-          Philox4 rb = ws.block(wr >> 2);
-          R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
-          R U2 = R(0);
-          if (D == 2) U2 = U01<R>::pair(rb.v[(wr + 2) & 3], rb.v[((wr + 2) & 3) + 1]);
+          direction<D, R>(ws, w0 + gdir_index(D), thg);
+          R U1, U2;
+          green_uniforms<D, R>(ws, w0, U1, U2);
           const R v = green_radius<D, R>(U1, U2);
           const R r = st.r[wk];
           const R rv = Ar<R>::mul(r, v);
@@ -1049,11 +1046,10 @@ sweep5_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict_
           }
           if (w > R(0)) {
             R thg[D];
-            direction<D, R>(ws, w0 + dir_words(D), thg);
-            const uint32_t wr = w0 + 2 * dir_words(D);
-            Philox4 rb = ws.block(wr >> 2);
-            const R U1 = U01<R>::pair(rb.v[wr & 3], rb.v[(wr & 3) + 1]);
-            const R v = green_radius<D, R>(U1, R(0));
+            direction<D, R>(ws, w0 + gdir_index(D), thg);
+            R U1, U2;
+            green_uniforms<D, R>(ws, w0, U1, U2);
+            const R v = green_radius<D, R>(U1, U2);
             const R rv = Ar<R>::mul(r, v);
 #pragma unroll
             for (int e = 0; e < D; ++e) eY[e * W + wk] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(rv, thg[e]));
