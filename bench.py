@@ -168,7 +168,8 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
     # DRAM bytes per event from one ncu capture of each kernel as it is now
     # (profiles/walk_fill_w2_fullset.md, profiles/eval_tc_w2_fullset.md: M = 1024,
     # 1.0216e8 events), scaled by the events of one launch; traffic grows with the events
-    per_event_bytes = {"eval_tc": (1.659414 + 0.003520) * 1e9 / 1.0216e8}
+    per_event_bytes = {"walk_fill": (0.828278 + 2.333514) * 1e9 / 1.0216e8,
+                       "eval_tc": (1.659346 + 0.003315) * 1e9 / 1.0216e8}
     launches = max(1, st["eval_launches"])
     for k, v in kern.items():
         v["traffic"] = per_event_bytes[k] * points / launches if (k in per_event_bytes and wl.dim == 2) else None
