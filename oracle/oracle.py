@@ -59,6 +59,8 @@ def lib():
         sig = {
             "orc_philox4x32_10": (None, [U32, U32, U32]),
             "orc_u01_pair": (C.c_double, [C.c_uint32, C.c_uint32]),
+            "orc_u01_word": (C.c_double, [C.c_uint32]),
+            "orc_ball_words_per_step": (C.c_int, [C.c_int]),
             "orc_words_per_step": (C.c_int, [C.c_int]),
             "orc_legendre": (None, [C.c_int, C.c_double, D]),
             "orc_jacobi11": (None, [C.c_int, C.c_double, D]),

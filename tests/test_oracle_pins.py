@@ -180,6 +180,26 @@ def test_philox_matches_independent_implementation(O):
         assert O.philox(c[:4], [seed & 0xffffffff, seed >> 32]) == ref
 
 
+def test_uniforms_from_words(O):
+    """Uniforms on (0, 1) from the stream: one word gives (a + 1/2) 2^-32 (the
+    d <= 2 walk), a pair gives ((a >> 5) 2^26 + (b >> 6) + 1/2) 2^-53.  Both are
+    the midpoints of equal cells, so the extreme words map to half a cell from
+    0 and 1, and the map is strictly increasing."""
+    L = O.lib()
+    assert L.orc_u01_word(0) == 2.0 ** -33
+    assert L.orc_u01_word(0xffffffff) == 1.0 - 2.0 ** -33
+    assert L.orc_u01_word(0x80000000) == 0.5 + 2.0 ** -33
+    assert L.orc_u01_pair(0, 0) == 2.0 ** -54
+    assert L.orc_u01_pair(0xffffffff, 0xffffffff) == 1.0 - 2.0 ** -54
+    rng = np.random.default_rng(3)
+    a = np.sort(rng.integers(0, 2 ** 32, 200, dtype=np.uint64))
+    u = [L.orc_u01_word(int(x)) for x in a]
+    assert all(p <= q for p, q in zip(u, u[1:]))
+    # step layouts: d <= 2 fits one step in two Philox blocks; d = 5 keeps pairs
+    assert L.orc_ball_words_per_step(1) == 8 and L.orc_ball_words_per_step(2) == 8
+    assert L.orc_ball_words_per_step(5) == 28
+
+
 # ----------------------------------------------------------------- walks
 def lattice_expected_L(x0, J, nstar):
     """Exact E[L] of the fixed-step 1-D walk (Eq. indexL) by a Markov chain on the
