@@ -93,6 +93,27 @@ def workload(args, rank=0):
     return wl
 
 
+def max_over_ranks(ms, device):
+    """The slowest rank's step time (ms): every rank's replica must finish
+    before the job's step is done.  One process per GPU; a no-op without a
+    process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, world, ms):
+    """Whole-job units per second: every rank processes its own replica of the
+    workload (weak scaling), so the job does world x the per-rank units in the
+    slowest rank's time."""
+    return units_per_rank_step * world / (ms / 1e3)
+
+
 def node_samples_per_solve(wl):
     S = wl.n_space ** wl.dim
     tot = 0
@@ -286,13 +307,9 @@ def run_ours(args):
     ms = sum(step_ms) / len(step_ms)
     st = plan.stats()
     plan.set_timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(ms, "cuda")
     per_step = sum(node_samples_per_interval(wl, r) for r in done) / len(done)
-    value = per_step * world / (ms / 1e3)
+    value = job_throughput(per_step, world, ms)
 
     # roofline of the dominant kernel of the sweep (by device time in the timed
     # region; every launch bracketed by CUDA events on the launching stream)
