@@ -182,7 +182,9 @@ class Plan:
                 "eval_launches": s.eval_launches}
 
     def autotune(self, interval: int = 0, stream=None) -> float:
-        """Pick the sweep's cohort width by timing one sweep per candidate (nodal values unchanged)."""
+        """Tune the forward sweep by timing one sweep per candidate setting: the
+        event sweep's batch size, or the cohort kernel's width (nodal values and
+        the point counters unchanged).  Returns the best sweep time in ms."""
         ms = C.c_double()
         L.check(L.lib.spmc_autotune(self._h, C.c_void_p(_stream_ptr(stream)), interval, C.byref(ms)), self._h)
         return ms.value
