@@ -28,8 +28,11 @@ def oracle_u0(O, wl, inst, spec):
 
 
 def parity_tol(ref):
-    """|gpu - oracle| bound for the FP64 path: 1e-12 relative per node, with the
-    node's magnitude floored at 1e-3 of the largest one (the two sides differ only
-    in summation order and in last-bit rounding of tables and transcendentals)."""
+    """|gpu - oracle| bound for the FP64 path: 1e-12 x max(|ref_i|, 1e-3 max|ref|).
+    That is 1e-12 relative for every node whose magnitude is at least 1e-3 of the
+    largest, and an absolute 1e-15 x max|ref| for the smaller ones (nodes near the
+    boundary of a sine profile, whose relative error is dominated by the rounding
+    of their larger neighbours' contributions).  The two sides differ only in
+    summation order and in last-bit rounding of tables and transcendentals."""
     ref = np.asarray(ref)
     return 1e-12 * np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
