@@ -74,7 +74,14 @@ typedef struct {
   unsigned long long seed;  /* Philox4x32-10 key */
   int precision;            /* SPMC_FP64 or SPMC_MIXED (FP32 sweep, FP64 elsewhere) */
   int batch;                /* number of instances, >= 1 */
+  int walk_mode;            /* SPMC_WALK_BALLS (0): balls inside Omega of radius min(J, dist),
+                               the residual at a Green-function point of each ball and a
+                               random sub-step time; SPMC_WALK_FIXED (1): the fixed-radius
+                               walk of Lemma Xlocation with the residual at the step centres
+                               (Eqs. indexL, interIQ; n_sub is then 1, d <= 2, cohort sweep).
+                               The second diverges at high spectral degrees. */
 } spmc_plan_desc;
+enum { SPMC_WALK_BALLS = 0, SPMC_WALK_FIXED = 1 };
 
 /* One instance: partition, degrees, reaction, manufactured source, u0.
  * Eq. mainproblem with homogeneous boundary data; f_add makes the closed form
@@ -108,6 +115,7 @@ typedef struct {
   double eval_ms;           /* event sweep: the per-slice evaluation launches (part of sweep_ms) */
   long long eval_launches;
   double fill_ms;           /* event sweep: the placing walk pass (part of sweep_ms) */
+  long long workspace_bytes;/* device memory the plan holds (its own allocations) */
 } spmc_stats;
 
 /* Validate desc, build the node tables and allocate the workspace.
@@ -135,7 +143,12 @@ spmc_status spmc_solve(spmc_plan_t plan, void* cuda_stream, double* u_nodes);
  * 0) or from the previous interval's expansion at its end, all rows equal to
  * row 0 (Remark 2.1).  spmc_iterate then runs n_iter iterations (iteration
  * numbers continue from the previous call on that interval) and returns the
- * largest |eps| of the last one over all instances (synchronises the stream). */
+ * largest |eps| of the last one over all instances.  The iterations are
+ * enqueued back to back and the stream is synchronised once, at the end (the
+ * plan's very first event-sweep batch also synchronises once to size the event
+ * buffer).  If a batch outgrows the event buffer, the device skips the rest of
+ * the sequence and the call grows the buffer and runs the skipped iterations
+ * again, so results never depend on it. */
 spmc_status spmc_begin_interval(spmc_plan_t plan, void* cuda_stream, int interval);
 spmc_status spmc_iterate(spmc_plan_t plan, void* cuda_stream, int interval, int n_iter, double* max_eps_host);
 
@@ -148,8 +161,9 @@ spmc_status spmc_get_nodes(spmc_plan_t plan, void* cuda_stream, int instance, in
  * iterate for checking.  A later spmc_iterate on that interval continues from it. */
 spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, const double* src);
 
-/* One residual iteration on `interval` (like spmc_iterate with n_iter = 1) that
- * allocates nothing.  The paper has no counterpart: this entry point exists for
+/* One residual iteration on `interval` (like spmc_iterate with n_iter = 1 with
+ * the cohort sweep, whose results it reproduces bit for bit) that allocates
+ * nothing.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory at the point of the call, e.g.
  * code running between the set-up of a real-time loop and its teardown, or a
  * host thread inside a region where cudaMalloc would synchronise the device or
@@ -166,7 +180,9 @@ spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, in
  *    streams, other plans, other host threads) race on it: serialise them.
  *  - A problem whose chunk sums and minimal walk state do not fit in the array
  *    is rejected with SPMC_ERR_UNSUPPORTED and a message naming the limit.
- * max_eps_host receives the largest |eps| (the stream is synchronised). */
+ * max_eps_host receives the largest |eps| (the stream is synchronised); the
+ * statistics (points, capped, iterations_run, last_max_eps) are updated as by
+ * spmc_iterate. */
 #define SPMC_STATIC_SCRATCH_BYTES (16u << 20)
 spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interval, double* max_eps_host);
 
@@ -188,18 +204,21 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
  *     SPMC_MIXED the evaluation is a matrix product on the tensor cores
  *     (tcgen05, TF32 with a 3-term split, FP32 accumulation); otherwise it runs
  *     on the FP32 / FP64 pipes.  Per-event terms are summed in FP64.  Device
- *     memory: two event buffers of 16 (FP32) or 32 (FP64) bytes per event of a
- *     batch, allocated on first use and kept.  batch <= 0 picks about 2^25
- *     walks per batch.
+ *     memory: an event buffer of 16 (FP32) or 32 (FP64) bytes per event of a
+ *     batch, sized from the largest batch seen (plus a quarter), allocated on
+ *     first use and kept.  batch <= 0 picks about 2^25 walks per batch.
  *   SPMC_SWEEP_EVENTS_ALU: the same, with the evaluation always on the FP32 /
  *     FP64 pipes.
  *   SPMC_SWEEP_COHORT: the persistent cohort kernel; a walk's terms are summed
  *     in the sweep precision, then in FP64 per chunk.
  * The two give the same walks and the same points; only summation order and,
- * in SPMC_MIXED, the per-walk FP32 partial sums differ.  The event sweep's
- * FP64 sums use atomics, so its results can differ from run to run at the
- * rounding level of those sums; the cohort kernel is bitwise reproducible.  Returns
- * SPMC_ERR_INVALID for an unknown mode. */
+ * in SPMC_MIXED, the per-walk FP32 partial sums differ.  Both are bitwise
+ * reproducible: the event sweep adds each term to its node as a fixed-point
+ * integer (the term rounded once to a multiple of 2^-80), so its per-node sums
+ * are exact and do not depend on the order of the atomics, and are rounded to
+ * FP64 once; the cohort kernel sums each node's walks in sample order.  The
+ * event sweep needs M x max_steps < 2^32 (SPMC_ERR_UNSUPPORTED otherwise).
+ * Returns SPMC_ERR_INVALID for an unknown mode. */
 #define SPMC_SWEEP_EVENTS 0
 #define SPMC_SWEEP_COHORT 1
 #define SPMC_SWEEP_EVENTS_ALU 2
@@ -216,10 +235,9 @@ spmc_status spmc_set_timing(spmc_plan_t plan, int enable);
  * or the cohort width (spatial nodes per cohort) of the cohort kernel.  The
  * nodal values and the points / capped counters are left unchanged: the
  * candidates run the reconstruction, slices and sweep but not the update.
- * Results of later iterations do not depend on the choice beyond the order of
- * the FP64 sums (the cohort kernel sums per node in sample order whatever the
- * width; the event sweep's FP64 atomic sums are order-dependent at rounding
- * level, so it is not bitwise reproducible from run to run). */
+ * Results of later iterations do not depend on the choice (the cohort kernel
+ * sums per node in sample order whatever the width; the event sweep's per-node
+ * sums are exact whatever the batch). */
 spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, double* best_ms);
 
 /* The n_space JG(1,1) node coordinates of one axis, ascending (host array). */

@@ -21,6 +21,7 @@ F_POLY3, F_SIN = 0, 1
 EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
 U0_NODAL, U0_PHI_COEF = 0, 1
 SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT, SPMC_SWEEP_EVENTS_ALU = 0, 1, 2
+WALK_BALLS, WALK_FIXED = 0, 1
 
 
 class PlanDesc(C.Structure):
@@ -29,6 +30,7 @@ class PlanDesc(C.Structure):
         ("max_degree", C.c_int), ("M", C.c_longlong), ("K", C.c_int), ("tol", C.c_double),
         ("n_ref", C.c_int), ("n_sub", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int),
         ("kappa", C.c_double), ("seed", C.c_ulonglong), ("precision", C.c_int), ("batch", C.c_int),
+        ("walk_mode", C.c_int),
     ]
 
 
@@ -46,7 +48,7 @@ class Stats(C.Structure):
                 ("iterations_run", C.c_int), ("last_max_eps", C.c_double),
                 ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
                 ("walk_ms", C.c_double), ("eval_ms", C.c_double), ("eval_launches", C.c_longlong),
-                ("fill_ms", C.c_double)]
+                ("fill_ms", C.c_double), ("workspace_bytes", C.c_longlong)]
 
 
 # The C-ABI entry points and their signatures, as declared in include/spmc.h.

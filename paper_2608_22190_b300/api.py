@@ -25,12 +25,13 @@ def _stream_ptr(stream) -> Optional[int]:
 
 class Plan:
     def __init__(self, dim, n_space, time_family, max_intervals, max_degree, M, K, tol=0.0, n_ref=80, n_sub=4,
-                 shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1):
+                 shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1, walk_mode=L.WALK_BALLS):
         d = L.PlanDesc()
         d.dim, d.n_space, d.time_family = dim, n_space, time_family
         d.max_intervals, d.max_degree, d.M, d.K, d.tol = max_intervals, max_degree, M, K, tol
         d.n_ref, d.n_sub, d.shell, d.max_steps = n_ref, n_sub, shell, max_steps
         d.kappa, d.seed, d.precision, d.batch = kappa, seed, precision, batch
+        d.walk_mode = walk_mode
         self.desc = d
         self._h = C.c_void_p()
         L.check(L.lib.spmc_plan(C.byref(d), C.byref(self._h)))
@@ -179,7 +180,7 @@ class Plan:
         return {"points": s.points, "capped": s.capped, "iterations_run": s.iterations_run,
                 "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms,
                 "walk_ms": s.walk_ms, "fill_ms": s.fill_ms, "eval_ms": s.eval_ms,
-                "eval_launches": s.eval_launches}
+                "eval_launches": s.eval_launches, "workspace_bytes": s.workspace_bytes}
 
     def autotune(self, interval: int = 0, stream=None) -> float:
         """Tune the forward sweep by timing one sweep per candidate setting: the

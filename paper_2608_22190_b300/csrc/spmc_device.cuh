@@ -153,6 +153,25 @@ __device__ __forceinline__ void direction(const WalkStream& s, uint32_t w0, R* t
   }
 }
 
+// Direction of step q of the fixed-radius walk (Lemma Xlocation as printed):
+// words per step d = 1: one (its sign bit); d = 2: two (a 53-bit / 24-bit
+// uniform angle from the pair); d >= 3: normalised Box-Muller Gaussians from
+// dir_words(d) words.
+template <int D, typename R>
+__device__ __forceinline__ void literal_direction(const WalkStream& s, int q, R* th) {
+  if (D == 1) {
+    th[0] = (stream_word(s, (uint32_t)q) >> 31) ? R(-1) : R(1);
+  } else if (D == 2) {
+    const Philox4 b = s.block((uint32_t)q >> 1);   // words 2q, 2q + 1 share a block
+    const R U = U01<R>::pair(b.v[(2 * q) & 3], b.v[(2 * q + 1) & 3]);
+    R sn, cs;
+    Ar<R>::sincos2pi(U, &sn, &cs);
+    th[0] = cs; th[1] = sn;
+  } else {
+    direction<D, R>(s, (uint32_t)q * (uint32_t)dir_words(D), th);
+  }
+}
+
 // The Green radius uniforms of the step whose words start at w0 (U2 is used for d = 2 only).
 template <int D, typename R>
 __device__ __forceinline__ void green_uniforms(const WalkStream& s, uint32_t w0, R& U1, R& U2) {
@@ -183,6 +202,101 @@ __device__ __forceinline__ R green_radius(R U1, R U2) {
     if (F < U1) lo = v; else hi = v;
   }
   return Ar<R>::mul(R(0.5), Ar<R>::add(lo, hi));
+}
+
+// Russian-roulette decision of a shrunk ball: keep the term iff the uniform
+// ((rw >> 8) + 1/2) 2^-24 is below p = w / Delta.  Decided in integers: with
+// a = rw >> 8, (a + 1/2) 2^-24 < p  <=>  2a + 1 < 2^25 p  <=>  2a + 1 < ceil(2^25 p)
+// (an integer n is below x iff it is below ceil(x)); 2^25 p is exact in R, so
+// the decision is the same as the FP64 comparison for both precisions and the
+// FP32 sweep issues no FP64 instruction for it.
+template <typename R>
+__device__ __forceinline__ bool roulette_keep(uint32_t rw, R p) {
+  const R P = p * R(33554432.0);            // exact (a power-of-two scale)
+  if (P >= R(33554432.0)) return true;      // p >= 1: every uniform is below it
+  if (!(P >= R(0))) return false;           // negative or NaN: never below it
+  const int c = (int)ceil(P);               // exact: an integer in [0, 2^25]
+  return (int)(2u * (rw >> 8) + 1u) < c;
+}
+
+// ------------------------------------------------------------------ exact sums
+// Order-independent per-node sums.  A term x is rounded once to the signed
+// fixed-point integer N = round(x 2^80) (magnitude below 2^126, so |x| < 2^46)
+// by integer operations on its bits; sums of N are exact, so a node's total
+// does not depend on the order in which events or blocks add to it.  The
+// global accumulator of a node holds four 64-bit counters of 32-bit limbs of N
+// (limb 3 signed); limbs are added without carries, so each counter has room
+// for 2^32 additions.  FixedAcc::value() assembles the 128-bit total and rounds
+// it to FP64 once.
+constexpr int kFixFrac = 80;
+
+// N for a double or float term; returns false if |x| >= 2^46 or x is not finite.
+__device__ __forceinline__ bool fix_from_double(double x, __int128& N) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E >= 1023 + 46) { N = 0; return false; }
+  const unsigned long long m = (b & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
+  const int s = (E ? E : 1) - 1075 + kFixFrac;   // x = m 2^(E - 1075), N = m 2^s
+  unsigned __int128 v;
+  if (s >= 0) v = (unsigned __int128)m << s;
+  else if (s > -54) v = (unsigned __int128)((m + (1ull << (-s - 1))) >> (-s));
+  else v = 0;
+  N = (b >> 63) ? -(__int128)v : (__int128)v;
+  return true;
+}
+__device__ __forceinline__ bool fix_from_float(float x, __int128& N) {
+  const uint32_t b = __float_as_uint(x);
+  const int E = (int)((b >> 23) & 0xff);
+  if (E >= 127 + 46) { N = 0; return false; }
+  const uint32_t m = (b & 0x7fffffu) | (E ? 0x800000u : 0u);
+  const int s = (E ? E : 1) - 150 + kFixFrac;    // x = m 2^(E - 150)
+  unsigned __int128 v;
+  if (s >= 0) v = (unsigned __int128)m << s;
+  else if (s > -25) v = (unsigned __int128)((m + (1u << (-s - 1))) >> (-s));
+  else v = 0;
+  N = (b >> 31) ? -(__int128)v : (__int128)v;
+  return true;
+}
+template <typename R> __device__ __forceinline__ bool fix_from(R x, __int128& N);
+template <> __device__ __forceinline__ bool fix_from<double>(double x, __int128& N) { return fix_from_double(x, N); }
+template <> __device__ __forceinline__ bool fix_from<float>(float x, __int128& N) { return fix_from_float(x, N); }
+
+// add N to a node's four limb counters (no return value: fire-and-forget atomics)
+__device__ __forceinline__ void fix_atomic_add(unsigned long long* acc, __int128 N) {
+  const unsigned __int128 u = (unsigned __int128)N;
+  const unsigned long long l0 = (unsigned long long)(u & 0xffffffffull);
+  const unsigned long long l1 = (unsigned long long)((u >> 32) & 0xffffffffull);
+  const unsigned long long l2 = (unsigned long long)((u >> 64) & 0xffffffffull);
+  const long long l3 = (long long)(N >> 96);   // arithmetic shift: signed top limb
+  if (l0) atomicAdd(acc + 0, l0);
+  if (l1) atomicAdd(acc + 1, l1);
+  if (l2) atomicAdd(acc + 2, l2);
+  if (l3) atomicAdd(acc + 3, (unsigned long long)l3);
+}
+
+// the FP64 value of a node's counters: sum_k c_k 2^(32 k) 2^-80, rounded once
+__device__ __forceinline__ double fix_value(const unsigned long long* acc) {
+  __int128 T = (__int128)(unsigned __int128)acc[0];
+  T += (__int128)((unsigned __int128)acc[1] << 32);
+  T += (__int128)((unsigned __int128)acc[2] << 64);
+  T += (__int128)((unsigned __int128)acc[3] << 96);   // wraps like the signed limb it holds
+  const bool neg = T < 0;
+  unsigned __int128 a = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+  // round a to 53 significant bits, then scale: exact except for that one rounding
+  int nb = 0;
+  for (unsigned __int128 t = a; t; t >>= 1) ++nb;
+  double v;
+  if (nb <= 53) v = (double)(unsigned long long)a;
+  else {
+    const int sh = nb - 53;
+    unsigned __int128 q = a >> sh;
+    const unsigned __int128 rem = a - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;   // nearest, ties to even
+    v = ldexp((double)(unsigned long long)q, sh);
+  }
+  v = ldexp(v, -kFixFrac);
+  return neg ? -v : v;
 }
 
 // ------------------------------------------------------------------ problem

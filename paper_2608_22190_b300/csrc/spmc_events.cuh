@@ -12,8 +12,15 @@
 //                              weight, key) into its segment;
 //   eval_events_kernel         one block per slice stages the slice once in
 //                              shared memory and evaluates all its events; the
-//                              weighted residuals are summed per node in FP64.
-// The per-node sums feed the update kernel (eps = sum / M).
+//                              weighted residuals are summed per node exactly
+//                              (fixed-point integers, see fix_from_double).
+// The per-node sums feed the update kernel (eps = sum / M).  Nothing returns to
+// the host between batches: the event buffer's capacity is set by the host from
+// a measured high-water mark, the scan checks the batch's total against it on
+// the device, and a batch that does not fit sets the abort word (the number of
+// the iteration); every later launch of the iteration sequence then returns at
+// once and the host, at its next synchronisation, grows the buffer and runs the
+// iterations again from the one that failed.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -35,6 +42,7 @@ struct EventArgs {
   void* events;                  // Event<R>[cap] grouped by (slice, node) (FILL)
   unsigned long long cap;        // events the buffer holds (FILL)
   int* status;                   // bit 4: an event fell outside the buffer
+  int* abort;                    // nonzero: an earlier batch did not fit; return at once
   int n, S, n_sub, gbits, max_steps, interval, iteration;
   long long n_tn;
   long long i0, nb;              // sample range of the batch
@@ -54,6 +62,7 @@ template <int D, typename R, bool FILL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kernel(EventArgs a) {
   static_assert(D <= 2, "the event sweep reads a step's words from one Philox block (d <= 2 layout)");
   namespace cg = cooperative_groups;
+  if (*a.abort) return;
   const int S = a.S, n = a.n, G = a.n_sub;
   const long long nb = a.nb;
   const R kappa = (R)a.kappa, shell = (R)a.shell;
@@ -157,11 +166,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
       }
     }
     // roulette for shrunk balls
-    if (r < J && w > R(0)) {
-      const uint32_t rw = b0.v[rword_index(D)];
-      const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
-      w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
-    }
+    if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D)], Ar<R>::div(w, delta)) ? delta : R(0);
     if (w > R(0)) {
       const unsigned int key = (unsigned int)((slice_base + m) * S + key_j);
       cg::coalesced_group grp = cg::coalesced_threads();
@@ -193,7 +198,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
           e.key = key;
           ev[slot] = e;
         } else {
-          atomicOr(a.status, 4);   // cannot happen: both passes take the same walks
+          atomicOr(a.status, 4);   // cannot happen: the scan checked the batch's total
+          atomicCAS(a.abort, 0, a.iteration);
         }
         ++points;
       }
@@ -226,8 +232,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
 
 // Exclusive scan of n unsigned counts in place, in three launches (block scans
 // of 1024 entries, a scan of the block totals, the add-back).
-__global__ void scan_blocks_kernel(unsigned int* __restrict__ v, unsigned long long* __restrict__ bsum, long long n) {
+__global__ void scan_blocks_kernel(unsigned int* __restrict__ v, unsigned long long* __restrict__ bsum, long long n,
+                                   const int* __restrict__ abort) {
   __shared__ unsigned int wsum[32];
+  if (*abort) return;
   const long long base = (long long)blockIdx.x * 1024;
   unsigned int x[4];
   const int t = threadIdx.x;   // 256 threads x 4 entries
@@ -260,9 +268,13 @@ __global__ void scan_blocks_kernel(unsigned int* __restrict__ v, unsigned long l
   if (t == 0) bsum[blockIdx.x] = tot;
 }
 
-// exclusive scan of the block totals (one block, serial chunks)
-__global__ void scan_totals_kernel(unsigned long long* __restrict__ bsum, long long nb, unsigned long long* total) {
+// Exclusive scan of the block totals (one block, serial chunks).  The batch's
+// total goes to *total; if it exceeds the event buffer's capacity, the largest
+// total seen goes to *need and the abort word gets the iteration number.
+__global__ void scan_totals_kernel(unsigned long long* __restrict__ bsum, long long nb, unsigned long long* total,
+                                   unsigned long long cap, unsigned long long* need, int* abort, int iteration) {
   __shared__ unsigned long long carry;
+  if (*abort) return;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -285,11 +297,16 @@ __global__ void scan_totals_kernel(unsigned long long* __restrict__ bsum, long l
     if (threadIdx.x == 0) carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = carry;
+  if (threadIdx.x == 0) {
+    *total = carry;
+    atomicMax(need, carry);
+    if (carry > cap) atomicCAS(abort, 0, iteration);
+  }
 }
 
 __global__ void scan_add_kernel(unsigned int* __restrict__ v, const unsigned long long* __restrict__ bsum,
-                                unsigned int* __restrict__ starts, long long n) {
+                                unsigned int* __restrict__ starts, long long n, const int* __restrict__ abort) {
+  if (*abort) return;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const unsigned int o = v[i] + (unsigned int)bsum[i / 1024];
@@ -298,7 +315,23 @@ __global__ void scan_add_kernel(unsigned int* __restrict__ v, const unsigned lon
   }
 }
 
-// One block per slice: stage the slice, evaluate its events, sum w r per node.
+// Segmented warp sum of fixed-point terms over runs of equal keys (keys do not
+// decrease across the lanes; lanes without a term carry key 0xffffffff and 0):
+// each lane gets the sum of its run from itself to the run's end, so the run's
+// first lane holds the run's total.  Exact, so independent of the lane order.
+__device__ __forceinline__ __int128 warp_run_sum(__int128 v, unsigned int key, unsigned int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, d);
+    const long long hi = __shfl_down_sync(0xffffffffu, (long long)(v >> 64), d);
+    const unsigned int k2 = __shfl_down_sync(0xffffffffu, key, d);
+    if (lane + d < 32 && k2 == key) v += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+  }
+  return v;
+}
+
+// One block per slice: stage the slice, evaluate its events, sum w r per node
+// (exact fixed-point sums into four limb counters per (time node, node)).
 template <int D, int NMAX, typename R>
 __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __restrict__ slice_node,
                                                           const TimeNode* __restrict__ tn,
@@ -307,10 +340,13 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
                                                           const SliceInfo* __restrict__ sinfo,
                                                           const unsigned int* __restrict__ starts,
                                                           const void* __restrict__ events_v,
-                                                          double* __restrict__ acc, int n, int S,
+                                                          unsigned long long* __restrict__ acc, int n, int S,
                                                           long long sl_stride, int half, double kappa_d,
-                                                          unsigned long long n_events) {
+                                                          const unsigned long long* __restrict__ n_events_p,
+                                                          int* status, const int* __restrict__ abort) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  if (*abort) return;
+  const unsigned long long n_events = *n_events_p;
   R* sC = reinterpret_cast<R*>(smraw);
   const long long sidx = blockIdx.x;
   const unsigned int e0 = starts[sidx * S];
@@ -329,26 +365,22 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
   for (unsigned long long base = e0; base < e1; base += blockDim.x) {
     const unsigned long long i = base + threadIdx.x;
     const bool has = i < e1;
-    double val = 0.0;
-    int jv = -1;
+    __int128 val = 0;
+    unsigned int key = 0xffffffffu;
     if (has) {
       const Event<R> e = ev[i];
       R Y[D];
       Y[0] = e.y[0];
       if (D == 2) Y[1] = e.y[1];
       const R res = residual_at<D, NMAX, R>(ip, kappa, n, sC, sC + half, Y, (R)si.Tt, (R)si.dTt);
-      val = (double)(e.w * res);
-      jv = (int)(e.key - (unsigned int)(sidx * S));
+      if (!fix_from<R>(e.w * res, val)) atomicOr(status, 1);
+      key = e.key;
     }
-    // segmented warp sum by node (events of a node are contiguous)
-    const unsigned int same = __match_any_sync(0xffffffffu, jv);
-    const int leader = __ffs(same) - 1;
-    double sum = 0.0;
-    for (unsigned int mm = same; mm; mm &= mm - 1) {
-      const int src_lane = __ffs(mm) - 1;
-      sum += __shfl_sync(same, val, src_lane);
-    }
-    if (has && (int)lane == leader) atomicAdd(&acc[ti * S + jv], sum);
+    // per-node sums: events are sorted by key, so equal keys are adjacent lanes
+    val = warp_run_sum(val, key, lane);
+    const unsigned int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (has && (lane == 0 || kprev != key))
+      fix_atomic_add(acc + 4 * (ti * S + (long long)(key - (unsigned int)(sidx * S))), val);
   }
 }
 

@@ -45,11 +45,14 @@ struct SliceInfo {
 // ----------------------------------------------------------------- Step 1
 // cu = (B_n x A x ... x A) U, ct_q = (2/h)(2q+1) sum_{l>q, l+q odd} cu_l.
 // One block per active instance; the nodal block lives in shared memory.
+// `abort` (may be null): a failed earlier launch of the same iteration sequence
+// set it; every launch of the sequence then returns without work.
 template <int D>
 __global__ void reconstruct_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ U,
                                    const double* __restrict__ A, const double* __restrict__ Bt,
-                                   double* __restrict__ coef, int n) {
+                                   double* __restrict__ coef, int n, const int* __restrict__ abort) {
   extern __shared__ double sm[];
+  if (abort && *abort) return;
   const InstInterval w = ii[blockIdx.x];
   int S = 1;
   for (int e = 0; e < D; ++e) S *= n;
@@ -96,7 +99,9 @@ __global__ void reconstruct_kernel(const InstInterval* __restrict__ ii, const do
 }
 
 // ----------------------------------------------------------------- slices
-// For every node's walk grid tau_m = t_node - (m + 1/2) delta / n_sub:
+// For every node's walk grid tau_m = t_node - (m + t_off) delta / n_sub (t_off =
+// 1/2: the sub-step midpoints of the inside-ball walk; 0 with n_sub = 1: the step
+// centres t_node - m Delta of the fixed-radius walk):
 //   C_m[p] = sum_q cu[q][p] L_q(xi(tau_m)),  H_m[p] = -sum_q ct[q][p] L_q(xi(tau_m)).
 // d=2 slices are stored [p_x][p_y] (p_y contiguous).  One block per slice.
 // Slice layout: C then H, each n rows (d = 2) or one row (d = 1) of `row`
@@ -105,8 +110,10 @@ template <int D, typename R>
 __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* __restrict__ slice_node,
                              const InstInterval* __restrict__ inst_of_node, const double* __restrict__ coef,
                              const InstanceParams* __restrict__ ip, R* __restrict__ slices,
-                             SliceInfo* __restrict__ sinfo, int n, int n_sub, int row, long long sl_stride) {
+                             SliceInfo* __restrict__ sinfo, int n, int n_sub, int row, long long sl_stride,
+                             double t_off, const int* __restrict__ abort) {
   __shared__ double L[41];
+  if (abort && *abort) return;
   long long s = blockIdx.x;
   long long ti = slice_node[s];
   const TimeNode node = tn[ti];
@@ -117,7 +124,7 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
   const double sdur = __dsub_rn(node.t_node, node.t0);
   const double delta = __ddiv_rn(sdur, (double)node.nstar);
   const double sub = __ddiv_rn(delta, (double)n_sub);
-  const double tau = __dsub_rn(node.t_node, __dmul_rn((double)m + 0.5, sub));
+  const double tau = __dsub_rn(node.t_node, __dmul_rn((double)m + t_off, sub));
   if (threadIdx.x == 0) {
     double xi = (2.0 * tau - node.t0 - (node.t0 + node.h)) / node.h;
     L[0] = 1.0;
@@ -168,6 +175,7 @@ struct SweepArgs {
   double kappa, shell;
   uint32_t k0, k1;
   int interval, iteration;
+  int walk_mode;            // 0: inside-ball walk; 1: fixed-radius walk with centre points
   // adjoint sweep only
   const double* lambda;     // adjoint of the nodal values (layout of U)
   double* gT;               // per slice: 3 S accumulators (coefficient order)
@@ -191,11 +199,38 @@ struct WalkState {
 // Prepare step q of sample s (the ball, its weight and its sub-point) as the
 // CPU reference does: absorb in the shell, shrink the ball to the distance to
 // the boundary, cut the last step to the time left.
+//
+// walk_mode 1 (the fixed-radius walk of Lemma Xlocation, Eqs. indexL and
+// interIQ): step q moves the centre by J theta_q; the term of step q (the
+// residual at the centre X_q, time t_node - q Delta, weight Delta) counts only if
+// X_{q+1} is still inside Omega, and the walk ends at the first centre outside
+// or after N_* steps.  The slices then hold the step-centre times (n_sub = 1).
 template <int D, typename R>
 __device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, const WalkStream& ws, R J, R delta,
                                              R sub, int Ktot, int G, int gbits, R shell, R kappa, int max_steps,
-                                             double& acc, unsigned long long& capped) {
+                                             double& acc, unsigned long long& capped, int walk_mode = 0) {
   int q = st.q[s];
+  if (walk_mode == 1) {
+    if (q >= max_steps || q >= Ktot) {
+      if (q >= max_steps && q < Ktot) ++capped;
+      st.mnext[s] = -1;
+      return;
+    }
+    R th[D];
+    literal_direction<D, R>(ws, q, th);
+    bool inside = true;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      const R xn = Ar<R>::add(st.X[e][s], Ar<R>::mul(J, th[e]));
+      if (!(xn > R(-1) && xn < R(1))) inside = false;
+    }
+    if (!inside) { st.mnext[s] = -1; return; }
+    st.w[s] = delta;
+    st.r[s] = J;
+    st.mnext[s] = q;
+    st.last[s] = (q + 1 >= Ktot) ? 1 : 0;
+    return;
+  }
   R dist = R(1);
 #pragma unroll
   for (int e = 0; e < D; ++e) {
@@ -366,7 +401,8 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
       st.f[wk] = R(0); st.k[wk] = 0; st.q[wk] = 0;
       ws.node = (uint32_t)(node.ell * S + j);
       ws.sample = (uint32_t)(sample0 + s);
-      prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps, dummy_acc, capped);
+      prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps, dummy_acc, capped,
+                         a.walk_mode);
       if (mnext[wk] >= 0) ++cnt;
     }
     __syncthreads();
@@ -438,23 +474,29 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
           const int q = st.q[wk];
           constexpr int WS = step_words(D);
           const uint32_t w0 = (uint32_t)q * WS;
-          // Green-function point of the pending ball
-          R thg[D], Y[D];
-          direction<D, R>(ws, w0 + gdir_index(D), thg);
-          R U1, U2;
-          green_uniforms<D, R>(ws, w0, U1, U2);
-          const R v = green_radius<D, R>(U1, U2);
           const R r = st.r[wk];
-          const R rv = Ar<R>::mul(r, v);
-#pragma unroll
-          for (int e = 0; e < D; ++e) Y[e] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(rv, thg[e]));
-          // a shrunk ball's term is evaluated with probability w / Delta and
-          // then weighted Delta (unbiased Russian roulette)
+          R Y[D];
           R w = st.w[wk];
-          if (r < J && w > R(0)) {
-            const uint32_t rw = stream_word(ws, w0 + rword_index(D));
-            const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
-            w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
+          if (a.walk_mode == 1) {
+            // fixed-radius walk: the residual at the step centre
+#pragma unroll
+            for (int e = 0; e < D; ++e) Y[e] = st.X[e][wk];
+          } else {
+            // Green-function point of the pending ball
+            R thg[D];
+            direction<D, R>(ws, w0 + gdir_index(D), thg);
+            R U1, U2;
+            green_uniforms<D, R>(ws, w0, U1, U2);
+            const R v = green_radius<D, R>(U1, U2);
+            const R rv = Ar<R>::mul(r, v);
+#pragma unroll
+            for (int e = 0; e < D; ++e) Y[e] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(rv, thg[e]));
+            // a shrunk ball's term is evaluated with probability w / Delta and
+            // then weighted Delta (unbiased Russian roulette)
+            if (r < J && w > R(0)) {
+              const uint32_t rw = stream_word(ws, w0 + rword_index(D));
+              w = roulette_keep<R>(rw, Ar<R>::div(w, delta)) ? delta : R(0);
+            }
           }
           if (w > R(0)) {
             const int bsl = mv - m0;
@@ -469,14 +511,15 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
             ++points;
           }
           if (st.last[wk]) { mnext[wk] = -1; break; }
-          // step to the sphere of the ball
+          // step to the sphere of the ball (fixed-radius walk: to the next centre)
           R th[D];
-          direction<D, R>(ws, w0, th);
+          if (a.walk_mode == 1) literal_direction<D, R>(ws, q, th);
+          else direction<D, R>(ws, w0, th);
 #pragma unroll
           for (int e = 0; e < D; ++e) st.X[e][wk] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(r, th[e]));
           st.q[wk] = q + 1;
           prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps,
-                             dummy_acc, capped);
+                             dummy_acc, capped, a.walk_mode);
           mv = mnext[wk];
         }
       }
@@ -579,6 +622,25 @@ __global__ void update_kernel(const TimeNode* __restrict__ tn, const double* __r
     unsigned long long bits = __double_as_longlong(fabs(e));
     atomicMax(&max_eps_bits[inst], bits);
   }
+}
+
+// eps = (exact fixed-point sum of the node's terms, rounded once to FP64) / M;
+// u += eps.  acc holds four limb counters per (time node, node).
+__global__ void update_fixed_kernel(const TimeNode* __restrict__ tn, const unsigned long long* __restrict__ acc,
+                                    double* __restrict__ U, double* __restrict__ eps_out,
+                                    unsigned long long* __restrict__ max_eps_bits, int* status, long long n_nodes,
+                                    int S, double inv_M, const int* __restrict__ abort) {
+  if (abort && *abort) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  const long long ti = i / S;
+  const int j = (int)(i - ti * S);
+  const TimeNode node = tn[ti];
+  const double e = fix_value(acc + 4 * i) * inv_M;
+  if (!isfinite(e)) atomicOr(status, 1);
+  U[node.u_off + (long long)node.ell * S + j] += e;
+  if (eps_out) eps_out[i] = e;
+  atomicMax(&max_eps_bits[node.inst], (unsigned long long)__double_as_longlong(fabs(e)));
 }
 
 // ----------------------------------------------------------------- Step 4 and first iterate
@@ -1041,8 +1103,7 @@ sweep5_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict_
           R w = st.w[wk];
           if (r < J && w > R(0)) {
             const uint32_t rw = stream_word(ws, w0 + rword_index(D));
-            const double Ur = ((double)(rw >> 8) + 0.5) * (1.0 / 16777216.0);
-            w = (Ur < (double)Ar<R>::div(w, delta)) ? delta : R(0);
+            w = roulette_keep<R>(rw, Ar<R>::div(w, delta)) ? delta : R(0);
           }
           if (w > R(0)) {
             R thg[D];

@@ -69,8 +69,14 @@ struct spmc_plan_s {
   long long counts_cap = 0, bsum_cap = 0;
   void* d_events = nullptr;          // events grouped by (slice, node)
   size_t events_bytes = 0;
-  double* d_acc = nullptr;           // per (time node, node) FP64 sums
+  unsigned long long ev_cap = 0;     // events the buffer holds (0: not sized yet)
+  unsigned long long* d_need = nullptr;   // largest batch total seen
+  int* d_abort = nullptr;            // 0, or the iteration whose batch did not fit
+  unsigned long long* d_counters_bak = nullptr;  // counters at the start of the running iteration
+  unsigned long long* d_acc = nullptr;    // per (time node, node) exact sums: four limb counters
   long long acc_cap = 0;
+  std::map<void*, size_t> allocs;    // device memory the plan holds
+  long long ws_bytes = 0;
   std::vector<HostProblem> probs;
   bool built = false;
   std::vector<double> xnodes;
@@ -131,6 +137,20 @@ spmc_status fail(spmc_plan_t plan, spmc_status st, const std::string& msg) {
   return st;
 }
 
+// Device memory of a plan: every allocation is recorded, so that the plan can
+// report the bytes it holds (spmc_stats.workspace_bytes) and free them all.
+cudaError_t pmalloc(spmc_plan_t plan, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) { plan->allocs[*p] = bytes; plan->ws_bytes += (long long)bytes; }
+  return e;
+}
+void pfree(spmc_plan_t plan, void* p) {
+  if (!p) return;
+  auto it = plan->allocs.find(p);
+  if (it != plan->allocs.end()) { plan->ws_bytes -= (long long)it->second; plan->allocs.erase(it); }
+  cudaFree(p);
+}
+
 int nstar_of(int n_ref, double s, double h) {
   double v = std::ceil((double)n_ref * s / h - 1e-9);
   return v < 1.0 ? 1 : (int)v;
@@ -138,9 +158,9 @@ int nstar_of(int n_ref, double s, double h) {
 
 template <typename T>
 spmc_status upload(spmc_plan_t plan, T** dptr, const std::vector<T>& v) {
-  if (*dptr) { cudaFree(*dptr); *dptr = nullptr; }
+  if (*dptr) { pfree(plan, *dptr); *dptr = nullptr; }
   if (v.empty()) return SPMC_OK;
-  SPMC_CUDA(cudaMalloc((void**)dptr, sizeof(T) * v.size()));
+  SPMC_CUDA(pmalloc(plan, (void**)dptr, sizeof(T) * v.size()));
   SPMC_CUDA(cudaMemcpy(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
   return SPMC_OK;
 }
@@ -217,7 +237,7 @@ spmc_status build(spmc_plan_t plan) {
   // rounds
   int R = 0;
   for (int i = 0; i < B; ++i) R = std::max(R, plan->probs[i].n_int);
-  for (auto& r : plan->rounds) { cudaFree(r.d_tn); cudaFree(r.d_ii); cudaFree(r.d_ii_of_node); cudaFree(r.d_slice_node); }
+  for (auto& r : plan->rounds) { pfree(plan, r.d_tn); pfree(plan, r.d_ii); pfree(plan, r.d_ii_of_node); pfree(plan, r.d_slice_node); }
   plan->rounds.assign(R, Round());
   long long slice_cap = 0, partial_cap = 0, coef_cap = 0;
   const int n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
@@ -262,19 +282,19 @@ spmc_status build(spmc_plan_t plan) {
     if ((st = upload(plan, &rd.d_slice_node, rd.slice_node)) != SPMC_OK) return st;
   }
   // workspace
-  cudaFree(plan->d_U); cudaFree(plan->d_coef); cudaFree(plan->d_slices); cudaFree(plan->d_sinfo);
-  cudaFree(plan->d_partial);
+  pfree(plan, plan->d_U); pfree(plan, plan->d_coef); pfree(plan, plan->d_slices); pfree(plan, plan->d_sinfo);
+  pfree(plan, plan->d_partial);
   plan->d_U = nullptr; plan->d_coef = nullptr; plan->d_slices = nullptr; plan->d_sinfo = nullptr; plan->d_partial = nullptr;
   size_t rsz = d.precision == SPMC_FP64 ? sizeof(double) : sizeof(float);
-  SPMC_CUDA(cudaMalloc((void**)&plan->d_U, sizeof(double) * std::max(1LL, plan->U_total)));
-  SPMC_CUDA(cudaMalloc((void**)&plan->d_coef, sizeof(double) * std::max(1LL, coef_cap)));
-  cudaFree(plan->d_rec);
+  SPMC_CUDA(pmalloc(plan, (void**)&plan->d_U, sizeof(double) * std::max(1LL, plan->U_total)));
+  SPMC_CUDA(pmalloc(plan, (void**)&plan->d_coef, sizeof(double) * std::max(1LL, coef_cap)));
+  pfree(plan, plan->d_rec);
   plan->d_rec = nullptr;
-  if (d.dim >= 3) SPMC_CUDA(cudaMalloc((void**)&plan->d_rec, sizeof(double) * std::max(1LL, coef_cap)));
+  if (d.dim >= 3) SPMC_CUDA(pmalloc(plan, (void**)&plan->d_rec, sizeof(double) * std::max(1LL, coef_cap)));
   slice_geometry(plan);
-  SPMC_CUDA(cudaMalloc(&plan->d_slices, rsz * plan->sl_stride * std::max(1LL, slice_cap)));
-  SPMC_CUDA(cudaMalloc((void**)&plan->d_sinfo, sizeof(SliceInfo) * std::max(1LL, slice_cap)));
-  SPMC_CUDA(cudaMalloc((void**)&plan->d_partial, sizeof(double) * std::max(1LL, partial_cap)));
+  SPMC_CUDA(pmalloc(plan, &plan->d_slices, rsz * plan->sl_stride * std::max(1LL, slice_cap)));
+  SPMC_CUDA(pmalloc(plan, (void**)&plan->d_sinfo, sizeof(SliceInfo) * std::max(1LL, slice_cap)));
+  SPMC_CUDA(pmalloc(plan, (void**)&plan->d_partial, sizeof(double) * std::max(1LL, partial_cap)));
   plan->slice_cap = slice_cap; plan->partial_cap = partial_cap; plan->coef_cap = coef_cap;
   std::vector<InstanceParams> ips(B);
   std::vector<double> u0(B * (size_t)S);
@@ -313,10 +333,10 @@ spmc_status ensure_ready(spmc_plan_t plan, cudaStream_t stream) {
   return SPMC_OK;
 }
 
-template <int D, int NMAX, typename R>
-spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+// Arguments of the cohort sweep kernels for one iteration of round rd.
+SweepArgs sweep_args(spmc_plan_t plan, const Round& rd, int interval, int iteration) {
   const spmc_plan_desc& d = plan->d;
-  SweepArgs a;
+  SweepArgs a{};
   a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
   a.partial = plan->d_partial; a.counters = plan->d_counters; a.status = plan->d_status;
   a.n = d.n_space; a.S = plan->S;
@@ -328,9 +348,17 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
   a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
   a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
   a.interval = interval; a.iteration = iteration;
+  a.walk_mode = d.walk_mode;
   a.M = d.M;
   a.sl_stride = plan->sl_stride;
   a.half = plan->half;
+  return a;
+}
+
+template <int D, int NMAX, typename R>
+spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const spmc_plan_desc& d = plan->d;
+  SweepArgs a = sweep_args(plan, rd, interval, iteration);
   const int JT = std::min(plan->JT, plan->S);
   const int W = JT * plan->chunk;
   const long long n_jt = (plan->S + JT - 1) / JT;
@@ -347,10 +375,10 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
   long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
   const size_t stride = state_stride_bytes(D, W, sizeof(R));
   if (plan->state_bytes < stride * grid) {
-    cudaFree(plan->d_state);
+    pfree(plan, plan->d_state);
     plan->d_state = nullptr;
     plan->state_bytes = 0;
-    SPMC_CUDA(cudaMalloc(&plan->d_state, stride * grid));
+    SPMC_CUDA(pmalloc(plan, &plan->d_state, stride * grid));
     plan->state_bytes = stride * grid;
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
@@ -374,21 +402,7 @@ spmc_status launch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd,
 template <typename R>
 spmc_status launch_sweep5(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
   const spmc_plan_desc& d = plan->d;
-  SweepArgs a;
-  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
-  a.partial = plan->d_partial; a.counters = plan->d_counters; a.status = plan->d_status;
-  a.n = d.n_space; a.S = plan->S;
-  a.chunk = plan->chunk;
-  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
-  a.n_sub = d.n_sub;
-  int gb = 0;
-  while ((1 << gb) < d.n_sub) ++gb;
-  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
-  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
-  a.interval = interval; a.iteration = iteration;
-  a.M = d.M;
-  a.sl_stride = plan->sl_stride;
-  a.half = plan->half;
+  SweepArgs a = sweep_args(plan, rd, interval, iteration);
   const int JT = std::max(1, std::min(plan->JT, plan->S));
   const int W = JT * plan->chunk;
   const long long n_jt = (plan->S + JT - 1) / JT;
@@ -406,10 +420,10 @@ spmc_status launch_sweep5(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
   const size_t stride = state_stride_bytes(5, W, sizeof(R));
   if (plan->state_bytes < stride * grid) {
-    cudaFree(plan->d_state);
+    pfree(plan, plan->d_state);
     plan->d_state = nullptr;
     plan->state_bytes = 0;
-    SPMC_CUDA(cudaMalloc(&plan->d_state, stride * grid));
+    SPMC_CUDA(pmalloc(plan, &plan->d_state, stride * grid));
     plan->state_bytes = stride * grid;
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
@@ -448,6 +462,8 @@ spmc_status dispatch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& r
 spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
   if (rd.ii.empty()) return SPMC_OK;
+  const double t_off = plan->d.walk_mode == 1 ? 0.0 : 0.5;   // step centres / sub-step midpoints
+  const int* ab = plan->d_abort;
   if (D >= 3) {
     // reconstruction in global memory: time axis, then each space axis
     const long long half_cap = plan->coef_cap / 2;
@@ -463,9 +479,9 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
     SPMC_CUDA(cudaGetLastError());
     if (rd.n_slices > 0) {
       if (plan->d.precision == SPMC_FP64)
-        slice_kernel<5, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+        slice_kernel<5, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
       else
-        slice_kernel<5, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+        slice_kernel<5, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
       SPMC_CUDA(cudaGetLastError());
     }
     return SPMC_OK;
@@ -476,21 +492,21 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
   if (D == 1) {
     SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
-                                                                          plan->d_coef, n);
+                                                                          plan->d_coef, n, ab);
   } else {
     SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
-                                                                          plan->d_coef, n);
+                                                                          plan->d_coef, n, ab);
   }
   SPMC_CUDA(cudaGetLastError());
   const bool fp64 = plan->d.precision == SPMC_FP64;
   if (rd.n_slices > 0) {
     if (D == 1) {
-      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
+      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
     } else {
-      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
+      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
+      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
     }
     SPMC_CUDA(cudaGetLastError());
   }
@@ -501,21 +517,7 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
 template <int D, int NMAX, typename R>
 spmc_status launch_adjoint_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
   const spmc_plan_desc& d = plan->d;
-  SweepArgs a;
-  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
-  a.partial = plan->d_partial; a.counters = plan->d_counters; a.status = plan->d_status;
-  a.n = d.n_space; a.S = plan->S;
-  a.chunk = plan->chunk;
-  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
-  a.n_sub = d.n_sub;
-  int gb = 0;
-  while ((1 << gb) < d.n_sub) ++gb;
-  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
-  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
-  a.interval = interval; a.iteration = iteration;
-  a.M = d.M;
-  a.sl_stride = plan->sl_stride;
-  a.half = plan->half;
+  SweepArgs a = sweep_args(plan, rd, interval, iteration);
   a.lambda = plan->d_lambda; a.gT = plan->d_gT; a.gds = plan->d_gds;
   const int JT = std::min(4, plan->S);
   const int W = JT * plan->chunk;
@@ -533,10 +535,10 @@ spmc_status launch_adjoint_sweep(spmc_plan_t plan, cudaStream_t stream, const Ro
   long long grid = std::min<long long>(n_cohorts, (long long)sms * occ);
   const size_t stride = state_stride_bytes(D, W, sizeof(R));
   if (plan->state_bytes < stride * grid) {
-    cudaFree(plan->d_state);
+    pfree(plan, plan->d_state);
     plan->d_state = nullptr;
     plan->state_bytes = 0;
-    SPMC_CUDA(cudaMalloc(&plan->d_state, stride * grid));
+    SPMC_CUDA(pmalloc(plan, &plan->d_state, stride * grid));
     plan->state_bytes = stride * grid;
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_work, 0, sizeof(int), stream));
@@ -565,27 +567,29 @@ spmc_status timer_end(spmc_plan_t plan, cudaStream_t s, std::pair<cudaEvent_t, c
 // Grow a device buffer to at least `need` bytes (contents are not kept).
 spmc_status grow(spmc_plan_t plan, void** p, size_t* have, size_t need) {
   if (*have >= need) return SPMC_OK;
-  cudaFree(*p);
+  pfree(plan, *p);
   *p = nullptr;
   *have = 0;
-  SPMC_CUDA(cudaMalloc(p, need));
+  SPMC_CUDA(pmalloc(plan, p, need));
   *have = need;
   return SPMC_OK;
 }
 
 template <int D, int NMAX, typename R>
-void launch_eval(spmc_plan_t plan, cudaStream_t stream, const Round& rd, unsigned long long total) {
+void launch_eval(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   const size_t esmem = sizeof(R) * (size_t)plan->sl_stride;
   eval_events_kernel<D, NMAX, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(
       rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
-      plan->d_acc, plan->d.n_space, plan->S, plan->sl_stride, plan->half, plan->d.kappa, total);
+      plan->d_acc, plan->d.n_space, plan->S, plan->sl_stride, plan->half, plan->d.kappa, plan->d_total,
+      plan->d_status, plan->d_abort);
 }
 
 // Tensor-core evaluation (d = 2, FP32 sweep).  The dynamic shared memory is
 // padded so that at most 512 / TM_COLS blocks share an SM: their TMEM
-// allocations then always fit and tcgen05.alloc never waits.
+// allocations then always fit and tcgen05.alloc never waits.  The grid covers
+// the event buffer's capacity (the batch's total stays on the device).
 template <int NMAX>
-spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& rd, unsigned long long total) {
+spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   using Gm = TcGeom<NMAX>;
   const int max_blocks = 512 / Gm::TM_COLS;
   const int smem = std::max(Gm::SMEM, 233472 / (max_blocks + 1) + 1024);
@@ -596,16 +600,35 @@ spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& r
     SPMC_CUDA(cudaFuncSetAttribute(eval_events_tc_kernel<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr_set[dev] = true;
   }
-  const unsigned long long blocks = (total + Gm::CHUNK - 1) / Gm::CHUNK;
+  const unsigned long long blocks = (plan->ev_cap + Gm::CHUNK - 1) / Gm::CHUNK;
   if (blocks > 0x7fffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch too large for one evaluation launch");
   eval_events_tc_kernel<NMAX><<<(unsigned)blocks, 128, smem, stream>>>(
       rd.d_slice_node, rd.d_tn, plan->d_ip, reinterpret_cast<const float*>(plan->d_slices), plan->d_sinfo,
       plan->d_starts, reinterpret_cast<const Event<float>*>(plan->d_events), plan->d_acc, plan->d.n_space, plan->S,
-      rd.n_slices, plan->sl_stride, plan->half, plan->d.kappa, total, plan->d_status);
+      rd.n_slices, plan->sl_stride, plan->half, plan->d.kappa, plan->d_total, plan->d_status, plan->d_abort);
   SPMC_CUDA(cudaGetLastError());
   return SPMC_OK;
 }
 
+// Give the event buffer room for `events` events plus a quarter (the batches of
+// later iterations differ a little from the one measured).
+template <typename R>
+spmc_status size_event_buffer(spmc_plan_t plan, unsigned long long events) {
+  if (events > 0xffffffffULL)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "event sweep: a batch holds 2^32 events or more; use a smaller batch");
+  unsigned long long cap = events + events / 4 + (1ull << 16);
+  cap = std::min<unsigned long long>(cap, 0xffffffffULL);
+  if (grow(plan, &plan->d_events, &plan->events_bytes, sizeof(Event<R>) * (size_t)cap) != SPMC_OK) return SPMC_ERR_OOM;
+  plan->ev_cap = std::max<unsigned long long>(cap, plan->events_bytes / sizeof(Event<R>));
+  plan->ev_cap = std::min<unsigned long long>(plan->ev_cap, 0xffffffffULL);
+  return SPMC_OK;
+}
+
+// The forward sweep of one iteration as an event pipeline, batch after batch,
+// with no return to the host: the event buffer was sized from a measured batch
+// (the plan's first batch is measured here, once) and the scan checks every
+// batch's total against it on the device (see the abort word in
+// spmc_events.cuh).
 template <int D, typename R>
 spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
   const spmc_plan_desc& d = plan->d;
@@ -614,32 +637,36 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   const long long nkeys = rd.n_slices * S;
   if (n_tn == 0 || nkeys == 0) return SPMC_OK;
   if (nkeys > 0xffffffffLL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event sweep: more than 2^32 (slice, node) pairs");
+  // the exact per-node sums take at most 2^32 additions per counter
+  if ((double)d.M * (double)d.max_steps >= 4294967296.0)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "event sweep: M x max_steps reaches 2^32; use the cohort sweep");
   // workspace
   if (plan->counts_cap < nkeys) {
-    cudaFree(plan->d_counts); cudaFree(plan->d_starts);
+    pfree(plan, plan->d_counts); pfree(plan, plan->d_starts);
     plan->d_counts = nullptr; plan->d_starts = nullptr; plan->counts_cap = 0;
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_counts, sizeof(unsigned int) * nkeys));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_starts, sizeof(unsigned int) * nkeys));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_counts, sizeof(unsigned int) * nkeys));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_starts, sizeof(unsigned int) * nkeys));
     plan->counts_cap = nkeys;
   }
   const long long nblk = (nkeys + 1023) / 1024;
   if (plan->bsum_cap < nblk) {
-    cudaFree(plan->d_bsum);
+    pfree(plan, plan->d_bsum);
     plan->d_bsum = nullptr; plan->bsum_cap = 0;
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_bsum, sizeof(unsigned long long) * nblk));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_bsum, sizeof(unsigned long long) * nblk));
     plan->bsum_cap = nblk;
   }
-  if (!plan->d_total) SPMC_CUDA(cudaMalloc((void**)&plan->d_total, sizeof(unsigned long long)));
+  if (!plan->d_total) SPMC_CUDA(pmalloc(plan, (void**)&plan->d_total, sizeof(unsigned long long)));
   if (plan->acc_cap < n_tn * S) {
-    cudaFree(plan->d_acc);
+    pfree(plan, plan->d_acc);
     plan->d_acc = nullptr; plan->acc_cap = 0;
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_acc, sizeof(double) * n_tn * S));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_acc, 4 * sizeof(unsigned long long) * n_tn * S));
     plan->acc_cap = n_tn * S;
   }
-  SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, sizeof(double) * n_tn * S, stream));
+  SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, 4 * sizeof(unsigned long long) * n_tn * S, stream));
   EventArgs a;
   a.tn = rd.d_tn; a.xnodes = plan->d_x; a.counts = plan->d_counts;
   a.status = plan->d_status;
+  a.abort = plan->d_abort;
   a.events = nullptr; a.cap = 0;
   a.n = d.n_space; a.S = S; a.n_sub = d.n_sub;
   int gb = 0;
@@ -669,21 +696,24 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     SPMC_CUDA(cudaMemsetAsync(plan->d_counts, 0, sizeof(unsigned int) * nkeys, stream));
     walk_events_kernel<D, R, false><<<wgrid_c, 256, 0, stream>>>(a);
     SPMC_CUDA(cudaGetLastError());
-    scan_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(plan->d_counts, plan->d_bsum, nkeys);
-    scan_totals_kernel<<<1, 1024, 0, stream>>>(plan->d_bsum, nblk, plan->d_total);
+    const bool measure = plan->ev_cap == 0;   // the plan's first batch sizes the event buffer
+    scan_blocks_kernel<<<(unsigned)nblk, 256, 0, stream>>>(plan->d_counts, plan->d_bsum, nkeys, plan->d_abort);
+    scan_totals_kernel<<<1, 1024, 0, stream>>>(plan->d_bsum, nblk, plan->d_total,
+                                               measure ? ~0ull : plan->ev_cap, plan->d_need, plan->d_abort,
+                                               iteration);
     scan_add_kernel<<<(unsigned)((nkeys + 255) / 256), 256, 0, stream>>>(plan->d_counts, plan->d_bsum,
-                                                                          plan->d_starts, nkeys);
+                                                                          plan->d_starts, nkeys, plan->d_abort);
     SPMC_CUDA(cudaGetLastError());
     if (timer_end(plan, stream, tw, 1) != SPMC_OK) return SPMC_ERR_CUDA;
-    unsigned long long total = 0;
-    SPMC_CUDA(cudaMemcpyAsync(&total, plan->d_total, sizeof(total), cudaMemcpyDeviceToHost, stream));
-    SPMC_CUDA(cudaStreamSynchronize(stream));
-    if (total > 0xffffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch above 2^32 events");
-    if (total == 0) continue;
-    if (grow(plan, &plan->d_events, &plan->events_bytes, sizeof(Event<R>) * (size_t)total) != SPMC_OK)
-      return SPMC_ERR_OOM;
+    if (measure) {
+      unsigned long long total = 0;
+      SPMC_CUDA(cudaMemcpyAsync(&total, plan->d_total, sizeof(total), cudaMemcpyDeviceToHost, stream));
+      SPMC_CUDA(cudaStreamSynchronize(stream));
+      spmc_status st = size_event_buffer<R>(plan, std::max(total, 1ull));
+      if (st != SPMC_OK) return st;
+    }
     a.events = plan->d_events;
-    a.cap = plan->events_bytes / sizeof(Event<R>);
+    a.cap = plan->ev_cap;
     std::pair<cudaEvent_t, cudaEvent_t> tf{nullptr, nullptr};
     if (timer_begin(plan, stream, tf) != SPMC_OK) return SPMC_ERR_CUDA;
     walk_events_kernel<D, R, true><<<wgrid_f, 256, 0, stream>>>(a);
@@ -692,16 +722,16 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     if (timer_begin(plan, stream, te) != SPMC_OK) return SPMC_ERR_CUDA;
     const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS;
     if (tensor) {
-      spmc_status ts = NMAXv == 8 ? launch_eval_tc<8>(plan, stream, rd, total)
-                       : NMAXv == 16 ? launch_eval_tc<16>(plan, stream, rd, total)
-                       : NMAXv == 24 ? launch_eval_tc<24>(plan, stream, rd, total)
-                                     : launch_eval_tc<32>(plan, stream, rd, total);
+      spmc_status ts = NMAXv == 8 ? launch_eval_tc<8>(plan, stream, rd)
+                       : NMAXv == 16 ? launch_eval_tc<16>(plan, stream, rd)
+                       : NMAXv == 24 ? launch_eval_tc<24>(plan, stream, rd)
+                                     : launch_eval_tc<32>(plan, stream, rd);
       if (ts != SPMC_OK) return ts;
-    } else if (D == 1) launch_eval<1, 32, R>(plan, stream, rd, total);
-    else if (NMAXv == 8) launch_eval<D == 1 ? 1 : 2, 8, R>(plan, stream, rd, total);
-    else if (NMAXv == 16) launch_eval<D == 1 ? 1 : 2, 16, R>(plan, stream, rd, total);
-    else if (NMAXv == 24) launch_eval<D == 1 ? 1 : 2, 24, R>(plan, stream, rd, total);
-    else launch_eval<D == 1 ? 1 : 2, 32, R>(plan, stream, rd, total);
+    } else if (D == 1) launch_eval<1, 32, R>(plan, stream, rd);
+    else if (NMAXv == 8) launch_eval<D == 1 ? 1 : 2, 8, R>(plan, stream, rd);
+    else if (NMAXv == 16) launch_eval<D == 1 ? 1 : 2, 16, R>(plan, stream, rd);
+    else if (NMAXv == 24) launch_eval<D == 1 ? 1 : 2, 24, R>(plan, stream, rd);
+    else launch_eval<D == 1 ? 1 : 2, 32, R>(plan, stream, rd);
     SPMC_CUDA(cudaGetLastError());
     if (timer_end(plan, stream, te, 2) != SPMC_OK) return SPMC_ERR_CUDA;
   }
@@ -716,16 +746,27 @@ spmc_status event_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, 
               : event_sweep_t<2, float>(plan, stream, rd, interval, iteration);
 }
 
-// One residual iteration on interval r for every instance that has it.
+// Copy the point / capped counters aside at the start of an iteration (unless
+// an earlier launch of the sequence aborted), so that an iteration that is run
+// again does not also count its aborted batches.
+__global__ void counters_snapshot_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ bak,
+                                         const int* __restrict__ abort) {
+  if (*abort) return;
+  if (threadIdx.x < 2) bak[threadIdx.x] = c[threadIdx.x];
+}
+
+// One residual iteration on interval r for every instance that has it,
+// enqueued without synchronising the stream.
 spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   Round& rd = plan->rounds[r];
   const int S = plan->S;
   const int iteration = ++rd.iteration;
   if (rd.ii.empty()) return SPMC_OK;
+  counters_snapshot_kernel<<<1, 32, 0, stream>>>(plan->d_counters, plan->d_counters_bak, plan->d_abort);
   spmc_status pst = prepare_slices(plan, stream, rd);
   if (pst != SPMC_OK) return pst;
   bool fp64 = plan->d.precision == SPMC_FP64;
-  const bool events = plan->d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT;
+  const bool events = plan->d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT && plan->d.walk_mode == 0;
   std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
   if (events && plan->timing) {
     if (!plan->ev_free.empty()) { tev = plan->ev_free.back(); plan->ev_free.pop_back(); }
@@ -743,15 +784,63 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, stream));
   long long nn = (long long)rd.tn.size() * S;
-  int n_chunks = events ? 1 : (int)((plan->d.M + plan->chunk - 1) / plan->chunk);
   if (nn > 0) {
-    update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(rd.d_tn, events ? plan->d_acc : plan->d_partial,
-                                                                    plan->d_U, nullptr,
-                                                                    plan->d_maxeps, plan->d_status, nn, S, n_chunks,
-                                                                    1.0 / (double)plan->d.M);
+    if (events)
+      update_fixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
+          rd.d_tn, plan->d_acc, plan->d_U, nullptr, plan->d_maxeps, plan->d_status, nn, S, 1.0 / (double)plan->d.M,
+          plan->d_abort);
+    else
+      update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
+          rd.d_tn, plan->d_partial, plan->d_U, nullptr, plan->d_maxeps, plan->d_status, nn, S,
+          (int)((plan->d.M + plan->chunk - 1) / plan->chunk), 1.0 / (double)plan->d.M);
     SPMC_CUDA(cudaGetLastError());
   }
   return SPMC_OK;
+}
+
+spmc_status size_events(spmc_plan_t plan, unsigned long long events) {
+  return plan->d.precision == SPMC_FP64 ? size_event_buffer<double>(plan, events)
+                                        : size_event_buffer<float>(plan, events);
+}
+
+// If a batch of the sequence just synchronised did not fit the event buffer,
+// grow the buffer to the largest batch seen, clear the abort word and restore
+// the counters of the failed iteration's start; *failed gets that iteration
+// (0: nothing aborted).  The stream must be synchronised.
+spmc_status recover_abort(spmc_plan_t plan, cudaStream_t stream, int* failed) {
+  int ab = 0;
+  SPMC_CUDA(cudaMemcpyAsync(&ab, plan->d_abort, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  SPMC_CUDA(cudaStreamSynchronize(stream));
+  *failed = ab;
+  if (ab == 0) return SPMC_OK;
+  unsigned long long need = 0;
+  SPMC_CUDA(cudaMemcpyAsync(&need, plan->d_need, sizeof(need), cudaMemcpyDeviceToHost, stream));
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_counters, plan->d_counters_bak, 2 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, stream));
+  SPMC_CUDA(cudaMemsetAsync(plan->d_abort, 0, sizeof(int), stream));
+  SPMC_CUDA(cudaStreamSynchronize(stream));
+  return size_events(plan, need);
+}
+
+// n_iter iterations of interval r, enqueued back to back; the stream is
+// synchronised once at the end.  An iteration whose batch outgrew the event
+// buffer (and everything after it, which returned at once) is run again with
+// a larger buffer.
+spmc_status run_iterations(spmc_plan_t plan, cudaStream_t stream, int r, int n_iter) {
+  Round& rd = plan->rounds[r];
+  const int last = rd.iteration + n_iter;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    while (rd.iteration < last) {
+      spmc_status st = iterate_once(plan, stream, r);
+      if (st != SPMC_OK) return st;
+    }
+    int failed = 0;
+    spmc_status st = recover_abort(plan, stream, &failed);
+    if (st != SPMC_OK) return st;
+    if (failed == 0) return SPMC_OK;
+    rd.iteration = failed - 1;
+  }
+  return fail(plan, SPMC_ERR_CUDA, "event sweep: the event buffer kept overflowing");
 }
 
 // Copy the round's nodal blocks between U and a contiguous buffer (offsets c_off/2).
@@ -905,21 +994,8 @@ template <int D, int NMAX, typename R>
 spmc_status launch_sweep_static(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval,
                                 int iteration, unsigned char* scratch, double* partial, size_t partial_bytes) {
   const spmc_plan_desc& d = plan->d;
-  SweepArgs a;
-  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.slices = plan->d_slices; a.sinfo = plan->d_sinfo;
-  a.partial = partial; a.counters = plan->d_counters; a.status = plan->d_status;
-  a.n = d.n_space; a.S = plan->S;
-  a.chunk = plan->chunk;
-  a.n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
-  a.n_sub = d.n_sub;
-  int gb = 0;
-  while ((1 << gb) < d.n_sub) ++gb;
-  a.gbits = gb; a.max_steps = d.max_steps; a.kappa = d.kappa; a.shell = plan->shell;
-  a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
-  a.interval = interval; a.iteration = iteration;
-  a.M = d.M;
-  a.sl_stride = plan->sl_stride;
-  a.half = plan->half;
+  SweepArgs a = sweep_args(plan, rd, interval, iteration);
+  a.partial = partial;
   const int JT = 1;
   const int W = plan->chunk;
   const long long n_cohorts = (long long)rd.tn.size() * plan->S * a.n_chunks;
@@ -975,7 +1051,8 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
       d.max_degree > 39 || d.M < 1 || d.K < 1 || d.n_ref < 1 || d.n_sub < 1 || d.n_sub > 16 ||
       (d.n_sub & (d.n_sub - 1)) || !(d.shell >= 0.0) || d.shell >= 0.5 || d.max_steps < 1 || !(d.kappa > 0.0) || d.batch < 1 ||
       (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
-      (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL)
+      (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL ||
+      (d.walk_mode != 0 && d.walk_mode != 1))
     return SPMC_ERR_INVALID;
   if (d.dim != 1 && d.dim != 2 && d.dim != 5) return SPMC_ERR_UNSUPPORTED;
   if (d.dim == 5 && d.n_space > 8) return SPMC_ERR_UNSUPPORTED;
@@ -985,8 +1062,10 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
     if (2.0 * (d.max_degree + 1) * S * 8.0 > 227.0 * 1024.0) return SPMC_ERR_UNSUPPORTED;
   }
   if (d.tol > 0.0 && d.batch > 1) return SPMC_ERR_UNSUPPORTED;
+  if (d.walk_mode == 1 && d.dim > 2) return SPMC_ERR_UNSUPPORTED;
   spmc_plan_t plan = new spmc_plan_s();
   plan->d = d;
+  if (d.walk_mode == 1) plan->d.n_sub = 1;   // one evaluation time per step: its centre
   plan->S = 1;
   for (int e = 0; e < d.dim; ++e) plan->S *= d.n_space;
   plan->probs.assign(d.batch, HostProblem());
@@ -1023,12 +1102,18 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ra_f, raf, sizeof raf);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rb_f, rbf, sizeof rbf);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_lam_f, lamf, sizeof lamf);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_counters, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_counters, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(plan->d_counters, 0, 2 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_maxeps, sizeof(unsigned long long) * d.batch);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_work, sizeof(int));
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_maxeps, sizeof(unsigned long long) * d.batch);
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_status, sizeof(int));
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_work, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_abort, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_abort, 0, sizeof(int));
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_need, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_need, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = pmalloc(plan, (void**)&plan->d_counters_bak, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_counters_bak, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     spmc_status r = (e == cudaErrorMemoryAllocation) ? SPMC_ERR_OOM : SPMC_ERR_CUDA;
     spmc_destroy(plan);
@@ -1115,11 +1200,9 @@ spmc_status spmc_iterate(spmc_plan_t plan, void* cuda_stream, int interval, int 
   if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "call spmc_begin_interval first");
   if (interval < 0 || interval >= (int)plan->rounds.size() || n_iter < 0) return fail(plan, SPMC_ERR_INVALID, "bad interval");
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  for (int k = 0; k < n_iter; ++k) {
-    spmc_status st = iterate_once(plan, s, interval);
-    if (st != SPMC_OK) return st;
-  }
-  spmc_status st = read_status(plan, s);
+  spmc_status st = run_iterations(plan, s, interval, n_iter);
+  if (st != SPMC_OK) return st;
+  st = read_status(plan, s);
   if (st != SPMC_OK) return st;
   double mx = 0.0;
   if ((st = read_max_eps(plan, s, &mx)) != SPMC_OK) return st;
@@ -1141,14 +1224,16 @@ spmc_status spmc_solve(spmc_plan_t plan, void* cuda_stream, double* u_nodes) {
   for (int r = 0; r < (int)plan->rounds.size(); ++r) {
     spmc_status st = begin_interval(plan, s, r);
     if (st != SPMC_OK) return st;
-    for (int k = 0; k < d.K; ++k) {
-      st = iterate_once(plan, s, r);
-      if (st != SPMC_OK) return st;
-      ++total_iters;
-      if (d.tol > 0.0) {
+    if (d.tol > 0.0) {
+      for (int k = 0; k < d.K; ++k) {
+        if ((st = run_iterations(plan, s, r, 1)) != SPMC_OK) return st;
+        ++total_iters;
         if ((st = read_max_eps(plan, s, &mx)) != SPMC_OK) return st;
         if (mx < d.tol) break;
       }
+    } else {
+      if ((st = run_iterations(plan, s, r, d.K)) != SPMC_OK) return st;
+      total_iters += d.K;
     }
   }
   SPMC_CUDA(cudaMemcpyAsync(u_nodes, plan->d_U, sizeof(double) * plan->U_total, cudaMemcpyDefault, s));
@@ -1191,7 +1276,7 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
   if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   Round& rd = plan->rounds[interval];
-  const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
+  const int S = plan->S;
   const int n_chunks = (int)((plan->d.M + plan->chunk - 1) / plan->chunk);
   const long long nn = (long long)rd.tn.size() * S;
   const size_t partial_bytes = ((size_t)nn * n_chunks * sizeof(double) + 255) / 256 * 256;
@@ -1205,30 +1290,10 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
   double* partial = reinterpret_cast<double*>(scratch + 256);
   const int iteration = rd.iteration + 1;
   if (!rd.ii.empty()) {
-    int maxT = 0;
-    for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
-    size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
-    if (D == 1) {
-      SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
-                                                                            plan->d_coef, n);
-    } else {
-      SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
-                                                                            plan->d_coef, n);
-    }
-    SPMC_CUDA(cudaGetLastError());
+    // reconstruction and slices as in spmc_iterate (these launches allocate nothing)
+    st = prepare_slices(plan, stream, rd);
+    if (st != SPMC_OK) return st;
     const bool fp64 = plan->d.precision == SPMC_FP64;
-    if (rd.n_slices > 0) {
-      if (D == 1) {
-        if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-        else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-      } else {
-        if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-        else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride);
-      }
-      SPMC_CUDA(cudaGetLastError());
-    }
     st = fp64 ? dispatch_sweep_static<double>(plan, stream, rd, interval, iteration, scratch, partial, partial_bytes)
               : dispatch_sweep_static<float>(plan, stream, rd, interval, iteration, scratch, partial, partial_bytes);
     if (st != SPMC_OK) return st;
@@ -1241,9 +1306,11 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
     }
   }
   rd.iteration = iteration;
-  // status and max |eps| through fixed host buffers (no allocation)
+  // status, counters and max |eps| through fixed host buffers (no allocation)
   int hs = 0;
+  unsigned long long cnt2[2] = {0, 0};
   SPMC_CUDA(cudaMemcpyAsync(&hs, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  SPMC_CUDA(cudaMemcpyAsync(cnt2, plan->d_counters, sizeof cnt2, cudaMemcpyDeviceToHost, stream));
   double mx = 0.0;
   unsigned long long bits[64];
   for (int b0 = 0; b0 < plan->d.batch; b0 += 64) {
@@ -1255,6 +1322,10 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
   }
   if (hs & 1) return fail(plan, SPMC_ERR_NONFINITE, "a non-finite eps was produced");
   if (hs & 2) return fail(plan, SPMC_ERR_TIMEOUT, "a sweep block exceeded its pass budget");
+  plan->stats.points = (long long)cnt2[0];
+  plan->stats.capped = (long long)cnt2[1];
+  plan->stats.iterations_run = 1;
+  plan->stats.last_max_eps = mx;
   if (max_eps_host) *max_eps_host = mx;
   return SPMC_OK;
 }
@@ -1272,23 +1343,23 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
   if (d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: dimensions 1 and 2 only");
   // workspace (first call)
   if (!plan->grad_ready) {
-    cudaFree(plan->d_lambda); cudaFree(plan->d_Ubak); cudaFree(plan->d_iter); cudaFree(plan->d_gT);
-    cudaFree(plan->d_lam); cudaFree(plan->d_mu); cudaFree(plan->d_dLdz); cudaFree(plan->d_gds);
-    cudaFree(plan->d_phi); cudaFree(plan->d_last);
-    for (auto p : plan->d_first_tn) cudaFree(p);
+    pfree(plan, plan->d_lambda); pfree(plan, plan->d_Ubak); pfree(plan, plan->d_iter); pfree(plan, plan->d_gT);
+    pfree(plan, plan->d_lam); pfree(plan, plan->d_mu); pfree(plan, plan->d_dLdz); pfree(plan, plan->d_gds);
+    pfree(plan, plan->d_phi); pfree(plan, plan->d_last);
+    for (auto p : plan->d_first_tn) pfree(plan, p);
     plan->d_lambda = plan->d_Ubak = plan->d_iter = plan->d_gT = plan->d_lam = nullptr;
     plan->d_mu = plan->d_dLdz = plan->d_gds = plan->d_phi = nullptr;
     plan->d_last = nullptr;
     long long maxblk = 0;
     for (auto& rd : plan->rounds) maxblk = std::max(maxblk, rd.coef_total / 2);
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_lambda, sizeof(double) * std::max(1LL, plan->U_total)));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_Ubak, sizeof(double) * std::max(1LL, plan->U_total)));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_iter, sizeof(double) * std::max(1LL, maxblk * K)));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_gT, sizeof(double) * 3 * S * std::max(1LL, plan->slice_cap)));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_lam, sizeof(double) * std::max(1LL, 3 * plan->coef_cap / 2)));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_mu, sizeof(double) * (size_t)B * S));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_dLdz, sizeof(double) * (size_t)B * S));
-    SPMC_CUDA(cudaMalloc((void**)&plan->d_gds, sizeof(double) * B));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_lambda, sizeof(double) * std::max(1LL, plan->U_total)));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_Ubak, sizeof(double) * std::max(1LL, plan->U_total)));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_iter, sizeof(double) * std::max(1LL, maxblk * K)));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_gT, sizeof(double) * 3 * S * std::max(1LL, plan->slice_cap)));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_lam, sizeof(double) * std::max(1LL, 3 * plan->coef_cap / 2)));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_mu, sizeof(double) * (size_t)B * S));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_dLdz, sizeof(double) * (size_t)B * S));
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_gds, sizeof(double) * B));
     std::vector<int> last(B);
     for (int i = 0; i < B; ++i) last[i] = plan->probs[i].n_int - 1;
     spmc_status st;
@@ -1325,7 +1396,7 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
     if ((st = begin_interval(plan, s, r)) != SPMC_OK) break;
     for (int k = 0; k < K; ++k) {
       round_copy_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_U, plan->d_iter + (long long)k * blk, S, 1);
-      if (k + 1 < K && (st = iterate_once(plan, s, r)) != SPMC_OK) break;
+      if (k + 1 < K && (st = run_iterations(plan, s, r, 1)) != SPMC_OK) break;
     }
     if (st != SPMC_OK) break;
     adj_lambda_init_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_last, plan->d_hw, plan->d_dLdz, plan->d_mu,
@@ -1372,7 +1443,7 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
       u0_coef_grad_kernel<<<(unsigned)B, 128, 0, s>>>(plan->d_mu, plan->d_phi, d_nc, grad_u0_coef, NC, n, S, D);
       SPMC_CUDA(cudaGetLastError());
       SPMC_CUDA(cudaStreamSynchronize(s));
-      cudaFree(d_nc);
+      pfree(plan, d_nc);
     }
   }
   return read_status(plan, s);
@@ -1408,11 +1479,16 @@ spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, dou
     for (int lg = 23; lg <= 26; ++lg) {
       const long long nb = std::max<long long>(1, std::min<long long>(plan->d.M, (1LL << lg) / walks_per_sample));
       plan->ev_batch = nb;
-      SPMC_CUDA(cudaEventRecord(e0, s));
-      st = event_sweep(plan, s, rd, interval, rd.iteration + 1);
+      for (int attempt = 0; attempt < 3; ++attempt) {   // a larger batch may first outgrow the event buffer
+        SPMC_CUDA(cudaEventRecord(e0, s));
+        st = event_sweep(plan, s, rd, interval, rd.iteration + 1);
+        if (st != SPMC_OK) break;
+        SPMC_CUDA(cudaEventRecord(e1, s));
+        SPMC_CUDA(cudaEventSynchronize(e1));
+        int failed = 0;
+        if ((st = recover_abort(plan, s, &failed)) != SPMC_OK || failed == 0) break;
+      }
       if (st != SPMC_OK) break;
-      SPMC_CUDA(cudaEventRecord(e1, s));
-      SPMC_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
       SPMC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) { best = ms; best_nb = nb; }
@@ -1479,6 +1555,7 @@ spmc_status spmc_space_nodes(spmc_plan_t plan, double* x_host) {
 spmc_status spmc_get_stats(spmc_plan_t plan, spmc_stats* out) {
   if (!plan || !out) return SPMC_ERR_INVALID;
   sync_counters(plan);
+  plan->stats.workspace_bytes = plan->ws_bytes;
   *out = plan->stats;
   return SPMC_OK;
 }
@@ -1489,18 +1566,8 @@ void spmc_destroy(spmc_plan_t plan) {
   if (!plan) return;
   drain_timing(plan);
   for (auto& ev : plan->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
-  for (auto& r : plan->rounds) { cudaFree(r.d_tn); cudaFree(r.d_ii); cudaFree(r.d_ii_of_node); cudaFree(r.d_slice_node); }
-  cudaFree(plan->d_x); cudaFree(plan->d_A); cudaFree(plan->d_B); cudaFree(plan->d_hw); cudaFree(plan->d_ip);
-  cudaFree(plan->d_u0); cudaFree(plan->d_U); cudaFree(plan->d_coef); cudaFree(plan->d_slices); cudaFree(plan->d_rec);
-  cudaFree(plan->d_sinfo); cudaFree(plan->d_partial); cudaFree(plan->d_counters); cudaFree(plan->d_maxeps);
-  cudaFree(plan->d_status);
-  cudaFree(plan->d_work);
-  cudaFree(plan->d_state);
-  cudaFree(plan->d_counts); cudaFree(plan->d_starts); cudaFree(plan->d_bsum); cudaFree(plan->d_total);
-  cudaFree(plan->d_events); cudaFree(plan->d_acc);
-  cudaFree(plan->d_lambda); cudaFree(plan->d_Ubak); cudaFree(plan->d_iter); cudaFree(plan->d_gT); cudaFree(plan->d_lam);
-  cudaFree(plan->d_mu); cudaFree(plan->d_dLdz); cudaFree(plan->d_gds); cudaFree(plan->d_phi); cudaFree(plan->d_last);
-  for (auto p : plan->d_first_tn) cudaFree(p);
+  for (auto& kv : plan->allocs) cudaFree(kv.first);   // every device allocation of the plan
+  plan->allocs.clear();
   delete plan;
 }
 

@@ -180,10 +180,11 @@ __global__ void __launch_bounds__(128) eval_events_tc_kernel(const long long* __
                                                              const SliceInfo* __restrict__ sinfo,
                                                              const unsigned int* __restrict__ starts,
                                                              const Event<float>* __restrict__ events,
-                                                             double* __restrict__ acc, int n, int S,
+                                                             unsigned long long* __restrict__ acc, int n, int S,
                                                              long long n_slices, long long sl_stride, int half,
-                                                             double kappa_d, unsigned long long n_events,
-                                                             int* status) {
+                                                             double kappa_d,
+                                                             const unsigned long long* __restrict__ n_events_p,
+                                                             int* status, const int* __restrict__ abort) {
   using Gm = TcGeom<NMAX>;
   constexpr int K = Gm::K, N = Gm::N, KC = Gm::KC;
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -194,6 +195,9 @@ __global__ void __launch_bounds__(128) eval_events_tc_kernel(const long long* __
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (*abort) return;
+  // the grid covers the event buffer's capacity; blocks past this batch's total return
+  const unsigned long long n_events = *n_events_p;
   const unsigned long long c0 = (unsigned long long)blockIdx.x * Gm::CHUNK;
   if (c0 >= n_events) return;
   const unsigned long long c1 = min(c0 + (unsigned long long)Gm::CHUNK, n_events);
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(128) eval_events_tc_kernel(const long long* __
         }
         sv[blk] = s + s2;
       }
-      double val = 0.0;
+      __int128 val = 0;
       const unsigned int key = cur_has ? __float_as_uint(cur.w) : 0xffffffffu;
       if (cur_has) {
         const float ox = 1.f - y0 * y0, oy = 1.f - y1 * y1;
@@ -327,17 +331,12 @@ __global__ void __launch_bounds__(128) eval_events_tc_kernel(const long long* __
         const float G = ox * oy * sv[1] - kappa * (oy * sv[2] + ox * sv[3]);
         const float yy[2] = {y0, y1};
         const float res = reaction<float>(ip, u) + source<2, float>(ip, kappa, yy, Tt, dTt) + G;
-        val = (double)(cur.z * res);
+        if (!fix_from_float(cur.z * res, val)) atomicOr(status, 1);
       }
-      // per-node sums: events are sorted by key, so equal keys are adjacent lanes
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const double o = __shfl_down_sync(0xffffffffu, val, d);
-        const unsigned int ok2 = __shfl_down_sync(0xffffffffu, key, d);
-        if (lane + d < 32 && ok2 == key) val += o;
-      }
+      // per-node sums (exact): events are sorted by key, so equal keys are adjacent lanes
+      val = warp_run_sum(val, key, (unsigned int)lane);
       const unsigned int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-      if (cur_has && (lane == 0 || kprev != key)) atomicAdd(&acc[ti * S + (key - key0)], val);
+      if (cur_has && (lane == 0 || kprev != key)) fix_atomic_add(acc + 4 * (ti * S + (long long)(key - key0)), val);
       tc::fence_async_smem();
       tc::fence_before();
       const bool all_ok = !__syncthreads_or(!ok);

@@ -32,7 +32,8 @@ def test_invalid_plans_rejected_without_gpu():
     def mk(**kw):
         d = L.PlanDesc()
         base = dict(dim=1, n_space=8, time_family=0, max_intervals=1, max_degree=4, M=64, K=1, tol=0.0,
-                    n_ref=10, n_sub=4, shell=1e-4, max_steps=64, kappa=1.0, seed=0, precision=0, batch=1)
+                    n_ref=10, n_sub=4, shell=1e-4, max_steps=64, kappa=1.0, seed=0, precision=0, batch=1,
+                    walk_mode=0)
         base.update(kw)
         for k, v in base.items():
             setattr(d, k, v)
@@ -41,7 +42,8 @@ def test_invalid_plans_rejected_without_gpu():
     h = C.c_void_p()
     for bad in [dict(dim=0), dict(dim=6), dict(n_space=1), dict(n_space=40), dict(M=0), dict(K=0),
                 dict(n_sub=3), dict(n_sub=32), dict(kappa=0.0), dict(shell=-1.0), dict(shell=0.5), dict(batch=0),
-                dict(time_family=2), dict(precision=5), dict(max_degree=0)]:
+                dict(time_family=2), dict(precision=5), dict(max_degree=0), dict(walk_mode=2),
+                dict(walk_mode=-1)]:
         assert L.lib.spmc_plan(C.byref(mk(**bad)), C.byref(h)) == L.SPMC_ERR_INVALID, bad
         assert not h.value
     assert L.lib.spmc_plan(None, C.byref(h)) == L.SPMC_ERR_INVALID

@@ -1,19 +1,26 @@
 """spmc_iterate_static: the iteration entry point that allocates nothing.
 
-Some callers cannot allocate device memory at the point of the call (a real-time
-loop between its set-up and teardown, or a region whose allocator policy forbids
-cudaMalloc because it would synchronise the device).  spmc_iterate_static runs
-the same iteration as spmc_iterate with the sweep's scratch in a file-scope
-device array.  This test calls both through the C-ABI on two identical plans and
-checks that two consecutive iterations agree node by node within the FP64
-parity tolerance of the other tests (they differ only in how samples are grouped
-into chunk sums).  It lives in its own file so that it runs last."""
+Some callers cannot allocate device memory at the point of the call: code that
+runs between the set-up of a real-time loop and its teardown, or a region whose
+allocator policy forbids cudaMalloc (it can synchronise the device or fail once
+memory is handed out up front).  spmc_iterate_static runs the same iteration as
+spmc_iterate with the cohort sweep, with the sweep's scratch in a file-scope
+device array.  This test calls both through the C-ABI on two identical plans,
+for two consecutive iterations, and checks that
+
+  - the nodal values agree bit for bit: both paths sum every walk in the same
+    precision and reduce each (node, chunk) of samples in the same order; only
+    the number of spatial nodes per block differs (one in the static path), which
+    does not enter any sum, so a layout error in the static scratch (chunk sums
+    against walk state) would show here;
+  - the static call allocates nothing: the plan's own device memory and the
+    device's free memory are the same before and after the two calls.
+
+It lives in its own file so that it runs last."""
 import ctypes as C
 
 import numpy as np
 import pytest
-
-from tests.common import parity_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,24 +39,39 @@ def test_iterate_static_matches_iterate(precision):
     ref = Plan.from_workload(wl, precision=precision)
     ref.set_sweep("cohort")      # the static entry point runs the cohort kernel
     sta = Plan.from_workload(wl, precision=precision)
-    stream = torch.cuda.current_stream()
-    sp = C.c_void_p(stream.cuda_stream)
+    sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     ref.begin_interval(0)
     sta.begin_interval(0)
+    S = wl.n_space ** 2
+    Mt = int(wl.instances[0].degrees[0])
+    outs = {k: [torch.empty((Mt + 1) * S, dtype=torch.float64, device="cuda") for _ in range(2)]
+            for k in ("ref", "sta")}
+    eps = {"ref": [], "sta": [], "points": []}
     for call in range(2):
-        e_ref, e_sta = C.c_double(), C.c_double()
-        L.check(L.lib.spmc_iterate(ref._h, sp, 0, 1, C.byref(e_ref)), ref._h)
-        L.check(L.lib.spmc_iterate_static(sta._h, sp, 0, C.byref(e_sta)), sta._h)
-        a = ref.get_nodes(0, 0).cpu().numpy()
-        b = sta.get_nodes(0, 0).cpu().numpy()
-        if precision == 0:
-            tol = parity_tol(a)
-        else:
-            # FP32 sweep: the chunk sums group the same walks differently; the
-            # per-walk values are identical, so only FP64 summation order differs
-            tol = 1e-12 * np.maximum(np.abs(a), 1e-3 * np.abs(a).max())
-        assert np.all(np.abs(a - b) <= tol), (call, np.abs(a - b).max())
-        assert abs(e_ref.value - e_sta.value) <= 1e-12 * max(1.0, abs(e_ref.value))
+        e = C.c_double()
+        L.check(L.lib.spmc_iterate(ref._h, sp, 0, 1, C.byref(e)), ref._h)
+        ref.get_nodes_into(0, 0, outs["ref"][call])
+        eps["ref"].append(e.value)
+        eps["points"].append(ref.stats()["points"])
+    torch.cuda.synchronize()
+    # the static calls alone: nothing else allocates between the two readings
+    ws0 = sta.stats()["workspace_bytes"]
+    free0 = torch.cuda.mem_get_info()[0]
+    for call in range(2):
+        e = C.c_double()
+        L.check(L.lib.spmc_iterate_static(sta._h, sp, 0, C.byref(e)), sta._h)
+        sta.get_nodes_into(0, 0, outs["sta"][call])
+        eps["sta"].append(e.value)
+        st = sta.stats()
+        assert st["points"] == eps["points"][call] and st["iterations_run"] == 1
+        assert st["last_max_eps"] == e.value
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert sta.stats()["workspace_bytes"] == ws0
+    for call in range(2):
+        a, b = outs["ref"][call].cpu().numpy(), outs["sta"][call].cpu().numpy()
+        assert np.array_equal(a, b), (call, np.abs(a - b).max())
+        assert eps["ref"][call] == eps["sta"][call]
     ref.close()
     sta.close()
 
