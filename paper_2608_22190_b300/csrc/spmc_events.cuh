@@ -22,8 +22,6 @@
 // once and the host, at its next synchronisation, grows the buffer and runs the
 // iterations again from the one that failed.
 #pragma once
-#include <cooperative_groups.h>
-
 #include "spmc_kernels.cuh"
 
 namespace spmc {
@@ -51,38 +49,101 @@ struct EventArgs {
   unsigned long long* counters;  // [0] points, [1] capped
 };
 
-// Every walk of the batch, lane by lane: a lane takes the next walk when its
-// current one ends, so the lanes of a warp stay busy.  Walk ids run sample
-// fastest (consecutive lanes share a node and mostly a slice); a thread steps
-// through its walk ids by a fixed stride, kept as (time node, node, sample)
-// counters.  COUNT counts the evaluation events per (slice, node); FILL runs
-// the same walks again (pure functions of their Philox streams) and writes each
-// event into its place.  Lanes with the same key share one atomic.
+// Per-warp queue of pending evaluation events of the placing pass: what the
+// Green point and the slot need (centre, radius, weight, key, the step's stream
+// coordinates and its Green-direction word).
+template <typename R>
+struct EmitQueue {
+  static constexpr int CAP = 64;          // two warps' worth: 32 are flushed at a time
+  R x0[CAP], x1[CAP], r[CAP], w[CAP];
+  uint32_t key[CAP], w0[CAP], sample[CAP], node[CAP], tag[CAP], gdir[CAP];
+};
+
+// Every walk of the batch, lane by lane.  Walk ids are (ti * S + j) * nb + il
+// (sample fastest); block b owns the ids b, b + G, b + 2G, ... (G = grid size),
+// an even mix of every time node and node, and its lanes take them one at a
+// time from a shared counter as their walks end, so no lane waits for a fixed
+// list of long walks.  COUNT counts the evaluation events per (slice, node);
+// FILL runs the same walks again (pure functions of their Philox streams) and
+// writes each event into its place.
+//
+// The loop is warp-synchronous: its condition is a warp vote, so every lane
+// runs every iteration, and each iteration is a fixed sequence of predicated
+// stages -- take a new walk (lanes whose walk ended), prepare the step (ball,
+// weight, sub-point, roulette), record the event, move to the sphere.  COUNT
+// adds each event to its (slice, node) count at once (lanes with the same key
+// share one atomic).  FILL appends it to its warp's queue; once 32 are queued
+// the whole warp computes their Green points (a second Philox block, the radial
+// law, the direction), claims their slots and stores them, all lanes together.
 template <int D, typename R, bool FILL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kernel(EventArgs a) {
   static_assert(D <= 2, "the event sweep reads a step's words from one Philox block (d <= 2 layout)");
-  namespace cg = cooperative_groups;
   if (*a.abort) return;
+  __shared__ unsigned long long s_next;
+  __shared__ EmitQueue<R> s_q[FILL ? 8 : 1];   // one queue per warp of the 256-thread block
   const int S = a.S, n = a.n, G = a.n_sub;
   const long long nb = a.nb;
   const R kappa = (R)a.kappa, shell = (R)a.shell;
   Event<R>* ev = reinterpret_cast<Event<R>*>(a.events);
   unsigned long long capped = 0, points = 0;
+  const unsigned int lane = threadIdx.x & 31;
+  const unsigned int lt_mask = (1u << lane) - 1u;
+  EmitQueue<R>& Q = s_q[FILL ? (threadIdx.x >> 5) : 0];
+  int qn = 0;   // entries in this warp's queue (warp-uniform)
 
-  // walk id = (ti * S + j) * nb + il; the stride decomposed the same way
   const long long total = a.n_tn * S * nb;
-  long long wid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
   const long long per_tn = (long long)S * nb;
-  long long ti = wid / per_tn;
-  int j = (int)((wid - ti * per_tn) / nb);
-  long long il = wid - ti * per_tn - (long long)j * nb;
-  const long long st_t = stride / per_tn;
-  const int st_j = (int)((stride - st_t * per_tn) / nb);
-  const long long st_i = stride - st_t * per_tn - (long long)st_j * nb;
+  const long long mine = total > (long long)blockIdx.x ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) s_next = 0;
+  __syncthreads();
+
+  // the placing pass's queue flush: lanes < cnt take entries 0..cnt-1
+  auto flush = [&](int cnt) {
+    __syncwarp();
+    const bool has = (int)lane < cnt;
+    const unsigned int fmask = __ballot_sync(0xffffffffu, has);
+    if (has) {
+      WalkStream w2;
+      w2.k0 = a.k0; w2.k1 = a.k1;
+      w2.sample = Q.sample[lane]; w2.node = Q.node[lane]; w2.tag = Q.tag[lane];
+      const uint32_t key = Q.key[lane];
+      const unsigned int peers = __match_any_sync(fmask, key);
+      const int leader = __ffs(peers) - 1;
+      unsigned int slot = 0;
+      if ((int)lane == leader) slot = atomicAdd(&a.counts[key], (unsigned int)__popc(peers));
+      R thg[D];
+      const uint32_t gd = Q.gdir[lane];
+      if (D == 1) {
+        thg[0] = (gd >> 31) ? R(-1) : R(1);
+      } else {
+        const R U = U01<R>::one(gd);
+        R sn, cs;
+        Ar<R>::sincos2pi(U, &sn, &cs);
+        thg[0] = cs; thg[1] = sn;
+      }
+      R U1, U2;
+      green_uniforms<D, R>(w2, Q.w0[lane], U1, U2);
+      const R v = green_radius<D, R>(U1, U2);
+      const R rv = Ar<R>::mul(Q.r[lane], v);
+      Event<R> e;
+      e.y[0] = Ar<R>::add(Q.x0[lane], Ar<R>::mul(rv, thg[0]));
+      e.y[1] = (D == 2) ? Ar<R>::add(Q.x1[lane], Ar<R>::mul(rv, thg[1])) : R(0);
+      e.w = Q.w[lane];
+      e.key = key;
+      slot = __shfl_sync(peers, slot, leader) + __popc(peers & lt_mask);   // the round trip overlaps the Green point
+      if ((unsigned long long)slot < a.cap) {
+        ev[slot] = e;
+      } else {
+        atomicOr(a.status, 4);   // cannot happen: the scan checked the batch's total
+        atomicCAS(a.abort, 0, a.iteration);
+      }
+      ++points;
+    }
+    __syncwarp();
+  };
 
   // walk state
-  bool live = false;
+  bool live = false, more = true;
   R X[D], f = R(0), delta = R(0), J = R(0), sub = R(0);
   int k = 0, q = 0, Ktot = 0, key_j = 0;
   long long slice_base = 0, cached_ti = -1;
@@ -90,140 +151,172 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
   WalkStream ws;
   ws.k0 = a.k0; ws.k1 = a.k1;
   constexpr int WS = step_words(D);
-  while (true) {
-    if (!live) {
-      if (wid >= total) break;
-      if (ti != cached_ti) {   // time-node parameters, as the CPU reference computes them
-        const TimeNode node = a.tn[ti];
-        const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
-        delta = Ar<R>::div(sdur, (R)node.nstar);
-        J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
-        sub = Ar<R>::div(delta, (R)G);
-        Ktot = G * node.nstar;
-        slice_base = node.slice_base;
-        node_ell = (uint32_t)node.ell;
-        ws.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
-                 (uint32_t)(a.iteration & 0x3ff);
-        cached_ti = ti;
-      }
-      int jr = j;
-#pragma unroll
-      for (int e = 0; e < D; ++e) { X[e] = (R)a.xnodes[jr % n]; jr /= n; }
-      f = R(0); k = 0; q = 0;
-      key_j = j;
-      ws.node = node_ell * (uint32_t)S + (uint32_t)j;
-      ws.sample = (uint32_t)(a.i0 + il);
-      live = true;
-      // advance to this thread's next walk id
-      wid += stride;
-      il += st_i;
-      if (il >= nb) { il -= nb; ++j; }
-      j += st_j;
-      if (j >= S) { j -= S; ++ti; }
-      ti += st_t;
-    }
-    // ---- one step, as the CPU reference: absorb, ball, weight, sub-point
-    R dist = R(1);
-#pragma unroll
-    for (int e = 0; e < D; ++e) {
-      R de = Ar<R>::sub(R(1), fabs(X[e]));
-      if (de < dist) dist = de;
-    }
-    if (q >= a.max_steps || dist < shell) {
-      if (q >= a.max_steps) ++capped;
-      live = false;
-      continue;
-    }
-    const uint32_t w0 = (uint32_t)q * WS;   // a multiple of 8 (d <= 2)
-    // direction, Green direction, sub-point and roulette words: one block
-    const Philox4 b0 = ws.block(w0 >> 2);
-    const uint32_t gword = b0.v[gword_index(D)];
-    const int g = a.gbits ? (int)(gword >> (32 - a.gbits)) : 0;
-    R left = Ar<R>::sub(Ar<R>::mul((R)(Ktot - k), sub), f);
-    R w, r;
-    int m, last = 0;
-    if (J <= dist) {
-      r = J;
-      w = delta;
-      if (k + G >= Ktot) {
-        const int ahead = Ktot - k;
-        m = k + (a.gbits ? (int)(((unsigned long long)gword * (unsigned long long)ahead) >> 32) : 0);
-        w = left;
-        last = 1;
-      } else {
-        m = k + g;
-        k += G;
-      }
-    } else {
-      r = dist;
-      w = Ar<R>::div(Ar<R>::mul(r, r), Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa));
-      m = k;
-      if (w >= left) { w = left; last = 1; }
-      else {
-        f = Ar<R>::add(f, w);
-        while (f >= sub) { f = Ar<R>::sub(f, sub); ++k; }
-        if (k >= Ktot) last = 1;
-      }
-    }
-    // roulette for shrunk balls
-    if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D)], Ar<R>::div(w, delta)) ? delta : R(0);
-    if (w > R(0)) {
-      const unsigned int key = (unsigned int)((slice_base + m) * S + key_j);
-      cg::coalesced_group grp = cg::coalesced_threads();
-      cg::coalesced_group same = cg::labeled_partition(grp, key);
-      if (!FILL) {
-        if (same.thread_rank() == 0) atomicAdd(&a.counts[key], same.size());
-      } else {
-        unsigned int slot = 0;
-        if (same.thread_rank() == 0) slot = atomicAdd(&a.counts[key], same.size());
-        R thg[D];
-        if (D == 1) {
-          thg[0] = (b0.v[gdir_index(D)] >> 31) ? R(-1) : R(1);
+  while (__any_sync(0xffffffffu, live || more)) {
+    // ---- stage 1: lanes without a walk take the block's next one
+    const unsigned int need = __ballot_sync(0xffffffffu, !live && more);
+    if (need) {
+      unsigned long long base = 0;
+      if ((int)lane == __ffs(need) - 1) base = atomicAdd(&s_next, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, __ffs(need) - 1);
+      if (!live && more) {
+        const unsigned long long kk = base + __popc(need & lt_mask);
+        if ((long long)kk >= mine) {
+          more = false;
         } else {
-          const R U = U01<R>::one(b0.v[gdir_index(D)]);
+          const long long wid = (long long)blockIdx.x + (long long)kk * gridDim.x;
+          long long ti, il;
+          int j;
+          if (total < (1ll << 32)) {   // 32-bit division (the usual case: about 2^25 walks per batch)
+            const uint32_t w32 = (uint32_t)wid, pt = (uint32_t)per_tn, nb32 = (uint32_t)nb;
+            const uint32_t t32 = w32 / pt, rem = w32 - t32 * pt, j32 = rem / nb32;
+            ti = t32; j = (int)j32; il = rem - j32 * nb32;
+          } else {
+            ti = wid / per_tn;
+            const long long rem = wid - ti * per_tn;
+            j = (int)(rem / nb);
+            il = rem - (long long)j * nb;
+          }
+          if (ti != cached_ti) {   // time-node parameters, as the CPU reference computes them
+            const TimeNode node = a.tn[ti];
+            const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
+            delta = Ar<R>::div(sdur, (R)node.nstar);
+            J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
+            sub = Ar<R>::div(delta, (R)G);
+            Ktot = G * node.nstar;
+            slice_base = node.slice_base;
+            node_ell = (uint32_t)node.ell;
+            ws.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+                     (uint32_t)(a.iteration & 0x3ff);
+            cached_ti = ti;
+          }
+          int jr = j;
+#pragma unroll
+          for (int e = 0; e < D; ++e) { X[e] = (R)a.xnodes[jr % n]; jr /= n; }
+          f = R(0); k = 0; q = 0;
+          key_j = j;
+          ws.node = node_ell * (uint32_t)S + (uint32_t)j;
+          ws.sample = (uint32_t)(a.i0 + il);
+          live = true;
+        }
+      }
+    }
+    // ---- stage 2: the step, as the CPU reference: absorb, ball, weight, sub-point, roulette
+    bool emit = false, last = false;
+    R w = R(0), r = R(0);
+    unsigned int key = 0;
+    Philox4 b0;
+    uint32_t w0 = 0;
+    if (live) {
+      R dist = R(1);
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        const R de = Ar<R>::sub(R(1), fabs(X[e]));
+        if (de < dist) dist = de;
+      }
+      if (q >= a.max_steps || dist < shell) {
+        if (q >= a.max_steps) ++capped;
+        live = false;
+      } else {
+        w0 = (uint32_t)q * WS;   // a multiple of 8 (d <= 2)
+        // direction, Green direction, sub-point and roulette words: one block
+        b0 = ws.block(w0 >> 2);
+        const uint32_t gword = b0.v[gword_index(D)];
+        const int g = a.gbits ? (int)(gword >> (32 - a.gbits)) : 0;
+        const R left = Ar<R>::sub(Ar<R>::mul((R)(Ktot - k), sub), f);
+        int m;
+        if (J <= dist) {
+          r = J;
+          w = delta;
+          if (k + G >= Ktot) {
+            const int ahead = Ktot - k;
+            m = k + (a.gbits ? (int)__umulhi(gword, (uint32_t)ahead) : 0);
+            w = left;
+            last = true;
+          } else {
+            m = k + g;
+            k += G;
+          }
+        } else {
+          r = dist;
+          w = Ar<R>::div(Ar<R>::mul(r, r), Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa));
+          m = k;
+          if (w >= left) { w = left; last = true; }
+          else {
+            f = Ar<R>::add(f, w);
+            while (f >= sub) { f = Ar<R>::sub(f, sub); ++k; }
+            if (k >= Ktot) last = true;
+          }
+        }
+        // roulette for shrunk balls
+        if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D)], Ar<R>::div(w, delta)) ? delta : R(0);
+        emit = w > R(0);
+        // keys fit 32 bits (the host checks n_slices S < 2^32)
+        key = ((uint32_t)slice_base + (uint32_t)m) * (uint32_t)S + (uint32_t)key_j;
+      }
+    }
+    // ---- stage 3: the event
+    const unsigned int emask = __ballot_sync(0xffffffffu, emit);
+    if (!FILL) {
+      if (emit) {
+        const unsigned int peers = __match_any_sync(emask, key);
+        if ((int)lane == __ffs(peers) - 1) atomicAdd(&a.counts[key], (unsigned int)__popc(peers));
+      }
+    } else if (emask) {
+      if (emit) {
+        const int pos = qn + __popc(emask & lt_mask);
+        Q.x0[pos] = X[0]; Q.x1[pos] = (D == 2) ? X[D - 1] : R(0);
+        Q.r[pos] = r; Q.w[pos] = w; Q.key[pos] = key; Q.w0[pos] = w0;
+        Q.sample[pos] = ws.sample; Q.node[pos] = ws.node; Q.tag[pos] = ws.tag;
+        Q.gdir[pos] = b0.v[gdir_index(D)];
+      }
+      qn += __popc(emask);
+      if (qn >= 32) {
+        flush(32);
+        // move the entries beyond the first 32 down
+        const int rest = qn - 32;
+        R t0 = R(0), t1 = R(0), t2 = R(0), t3 = R(0);
+        uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0, u4 = 0, u5 = 0;
+        if ((int)lane < rest) {
+          const int src = 32 + lane;
+          t0 = Q.x0[src]; t1 = Q.x1[src]; t2 = Q.r[src]; t3 = Q.w[src];
+          u0 = Q.key[src]; u1 = Q.w0[src]; u2 = Q.sample[src]; u3 = Q.node[src]; u4 = Q.tag[src]; u5 = Q.gdir[src];
+        }
+        __syncwarp();
+        if ((int)lane < rest) {
+          Q.x0[lane] = t0; Q.x1[lane] = t1; Q.r[lane] = t2; Q.w[lane] = t3;
+          Q.key[lane] = u0; Q.w0[lane] = u1; Q.sample[lane] = u2; Q.node[lane] = u3; Q.tag[lane] = u4;
+          Q.gdir[lane] = u5;
+        }
+        __syncwarp();
+        qn = rest;
+      }
+    }
+    // ---- stage 4: the walk ends, or moves to the sphere of its ball
+    if (live) {
+      if (last) {
+        live = false;
+      } else {
+        if (D == 1) {
+          const R th = (b0.v[0] >> 31) ? R(-1) : R(1);
+          X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, th));
+        } else {
+          const R U = U01<R>::one(b0.v[0]);
           R sn, cs;
           Ar<R>::sincos2pi(U, &sn, &cs);
-          thg[0] = cs; thg[1] = sn;
+          X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, cs));
+          X[D - 1] = Ar<R>::add(X[D - 1], Ar<R>::mul(r, sn));
         }
-        R U1, U2;
-        green_uniforms<D, R>(ws, w0, U1, U2);
-        const R v = green_radius<D, R>(U1, U2);
-        const R rv = Ar<R>::mul(r, v);
-        slot = same.shfl(slot, 0) + same.thread_rank();   // the atomic's round trip overlaps the Green point
-        if ((unsigned long long)slot < a.cap) {
-          Event<R> e;
-          e.y[0] = Ar<R>::add(X[0], Ar<R>::mul(rv, thg[0]));
-          e.y[1] = (D == 2) ? Ar<R>::add(X[1], Ar<R>::mul(rv, thg[1])) : R(0);
-          e.w = w;
-          e.key = key;
-          ev[slot] = e;
-        } else {
-          atomicOr(a.status, 4);   // cannot happen: the scan checked the batch's total
-          atomicCAS(a.abort, 0, a.iteration);
-        }
-        ++points;
+        ++q;
       }
     }
-    if (last) { live = false; continue; }
-    // step to the sphere of the ball
-    if (D == 1) {
-      const R th = (b0.v[0] >> 31) ? R(-1) : R(1);
-      X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, th));
-    } else {
-      const R U = U01<R>::one(b0.v[0]);
-      R sn, cs;
-      Ar<R>::sincos2pi(U, &sn, &cs);
-      X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, cs));
-      X[D - 1] = Ar<R>::add(X[D - 1], Ar<R>::mul(r, sn));
-    }
-    ++q;
   }
   if (FILL) {
+    if (qn > 0) flush(qn);
     for (int o = 16; o > 0; o >>= 1) {
       points += __shfl_xor_sync(0xffffffffu, points, o);
       capped += __shfl_xor_sync(0xffffffffu, capped, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       if (points) atomicAdd(&a.counters[0], points);
       if (capped) atomicAdd(&a.counters[1], capped);
     }
