@@ -157,7 +157,11 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     alu_peak = 148 * 128 * sm_max * 1e6 / 1e12          # lane-ops/s (one FP32 or INT32 lane op per cycle)
     tf32_ratio = 1.1 / 2.25                               # nominal dense TF32 / BF16 (recipe table)
-    bf16_sus = peaks.get("bf16_tflops_sustained", 1375.3)
+    # measured sustained cuBLAS BF16 rate; without the measurement file, the
+    # recipe's fallback (1.4 PFLOP/s sustained on an earlier B300)
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1400.0)
+    bf16_src = "bf16_tflops_sustained (MEASURED_PEAKS.json, of measured)" if "bf16_tflops_sustained" in peaks \
+        else "fallback 1400 TFLOP/s sustained BF16 (no measured peaks file, of fallback)"
     kern = {}
     t_count, t_fill, t_eval = st["walk_ms"] / 1e3, st["fill_ms"] / 1e3, st["eval_ms"] / 1e3
     per_ev_c, per_ev_f = walk_ops_per_event(wl.dim, False), walk_ops_per_event(wl.dim, True)
@@ -177,7 +181,7 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
             kern["eval_tc"] = {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                                "ms": t_eval * 1e3 / steps, "flops_per_event": fpe,
                                "executed_tensor_tflops": 3 * a,
-                               "peak_source": "bf16_tflops_sustained (MEASURED_PEAKS.json) x nominal TF32/BF16 1.1/2.25"}
+                               "peak_source": bf16_src + " x nominal TF32/BF16 1.1/2.25"}
         else:
             fpe = flops_per_point(wl.dim, n)
             peak = 1.25 if prec == L.FP64 else alu_peak * 2
@@ -317,9 +321,10 @@ def run_ours(args):
     peaks = measured_peaks()
     roof, kernels = sweep_roofline(wl, prec, points, st, peaks, args.steps, ms)
     batches = st["eval_launches"]
-    # per step: hand-off (or first iterate); per iteration: reconstruction,
-    # slices, update; per batch: count walk, three scan kernels, fill walk, evaluation
-    launches = args.steps * (1 + 3 * wl.K) + 6 * batches
+    # per step: hand-off (or first iterate); per iteration: counter snapshot,
+    # reconstruction, slices, update; per batch: count walk, three scan kernels,
+    # fill walk, evaluation
+    launches = args.steps * (1 + 4 * wl.K) + 6 * batches
 
     line = {"metric": "node-samples/sec & time to L-inf err 1e-6: batched mixed vs plain FP64, 1 B300",
             "value": value, "unit": "node-samples/s", "n_gpus": world, "steps": args.steps,
@@ -339,6 +344,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         line["e2e"] = e2e_leg(args, wl, prec)
         line["fp64_path"] = fp64_leg(args)
+        line["fp64_path"]["ratio_mixed_over_fp64"] = value / line["fp64_path"]["value"]
         line["time_to_1e-6"] = time_to_tol_legs(args)
         line["batch_w3"] = batch_leg(args)
         line["cpu_baseline"] = cpu_baseline(wl)
@@ -386,16 +392,20 @@ def e2e_leg(args, wl, prec):
 
 
 def fp64_leg(args):
-    """The plain FP64 path on a bounded run of the same workload: one interval,
-    K = 8 iterations, M = 8192 samples per node (node-samples/s)."""
+    """The plain FP64 path on the headline's workload and M (2-D long-time, 24 x 24
+    x 16, M = 65536), L2 flushed before the timed region.  One step here is one
+    iteration of the first interval: a full interval of eight FP64 iterations
+    takes several minutes on B300, whose FP64 pipe is 1/64 of its FP32 rate.
+    Node-samples/s is per node-sample, so it compares with the headline."""
     import torch
     from paper_2608_22190_b300 import _lib as L
     from paper_2608_22190_b300 import workloads as W
     from paper_2608_22190_b300.api import Plan
-    wl = W.w2(M=4096, n_intervals=1, K=2)
+    wl = W.w2(M=args.M, n_intervals=1, K=1)
     plan = Plan.from_workload(wl, precision=L.FP64)
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     plan.begin_interval(0)
-    plan.iterate(0, 1)
+    flush_l2(l2)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
@@ -404,62 +414,140 @@ def fp64_leg(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     plan.close()
-    ns = node_samples_per_interval(wl, 0) / wl.K
-    return {"value": ns / (ms / 1e3), "unit": "node-samples/s",
-            "sample": "one iteration of the first interval of the 2-D workload at M=4096 (FP64 sweep)", "ms": ms}
+    ns = node_samples_per_interval(wl, 0)
+    return {"value": ns / (ms / 1e3), "unit": "node-samples/s", "ms": ms,
+            "config": {"workload": f"w2-2d-long-time: 24x24 JG x 16 LGL, h=1, M={args.M}",
+                       "step": "one FP64 iteration of interval 1", "l2": "flushed before the timed region"}}
+
+
+def hp_time_to_tol(wl, prec, tol, kmax):
+    """Time until every node of every interval is within tol of the closed form:
+    the hp solve interval by interval (hand-off, then iterations until the
+    interval's L-inf error <= tol, at most kmax).  GPU time of the hand-offs and
+    iterations (CUDA events around each call); the error is read between calls,
+    outside the events."""
+    import numpy as np
+    import torch
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    inst = wl.instances[0]
+    plan = Plan.from_workload(wl, precision=prec)
+    grid = plan.node_grid()
+    ms_total, iters, errs = 0.0, [], []
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    for r in range(len(inst.degrees)):
+        ex = W.exact_block(wl, inst, grid, r)
+        ms_total += timed(lambda: plan.begin_interval(r))
+        err, k = float("inf"), 0
+        while k < kmax and err > tol:
+            ms_total += timed(lambda: plan.iterate(r, 1))
+            k += 1
+            err = float(np.abs(plan.get_nodes(0, r).cpu().numpy() - ex).max())
+        iters.append(k)
+        errs.append(err)
+    plan.close()
+    return {"reached": bool(max(errs) <= tol), "ms": ms_total, "linf": max(errs), "iterations": iters,
+            "linf_by_interval": errs, "M": wl.M, "n_ref": wl.n_ref, "k_max": kmax}
 
 
 def time_to_tol_legs(args, tol=1e-6):
-    """Time until the L-inf error against the closed form reaches tol: the 1-D
-    single-interval workload (its full size, both precisions) and the first
-    interval of the 2-D long-time workload (mixed).  GPU time of the iterations
-    (CUDA events); the error is read after every iteration, outside the events."""
+    """Time to L-inf error 1e-6 against the closed form.
+      w2_full_mixed / w2_full_mixed_M2048 / w2_full_fp64: the 2-D long-time
+        workload, all 20 intervals; mixed at the headline's M = 65536 and at
+        M = 2048, plain FP64 at M = 2048 (the FP64 pipe would take about an hour
+        at 65536), so mixed and FP64 also compare at equal M;
+      w1_mixed / w1_fp64: the 1-D single-interval workload at its full size
+        (M = 4096), with the L-inf distance of every iterate from the FP64
+        oracle's iterate on the same streams (computed on the host cores
+        meanwhile)."""
+    import os
     import numpy as np
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2608_22190_b300 import _lib as L
     from paper_2608_22190_b300 import workloads as W
     from paper_2608_22190_b300.api import Plan
+    from oracle import oracle as O
     out = {}
-    cases = [("w1_mixed", W.w1(), L.MIXED, 12), ("w1_fp64", W.w1(), L.FP64, 12),
-             ("w2_first_interval_mixed", W.w2(M=args.M, n_intervals=1), L.MIXED, 10)]
-    for name, wl, prec, kmax in cases:
-        inst = wl.instances[0]
+    kmax1 = 12
+    # the oracle's iterates of the 1-D workload, on the host cores while the GPU runs
+    wl1 = W.w1()
+    inst1 = wl1.instances[0]
+    spec1 = O.Spec(dim=1, n_space=wl1.n_space, time_family=wl1.time_family, n_ref=wl1.n_ref, M=wl1.M,
+                   kappa=wl1.kappa, seed=wl1.seed, f_kind=inst1.f_kind, f_coef=tuple(inst1.f_coef),
+                   f_scale=inst1.f_scale, ex_kind=inst1.ex_kind, ex_beta=inst1.ex_beta, n_sub=wl1.n_sub,
+                   shell=wl1.shell, max_steps=wl1.max_steps, n_threads=os.cpu_count() or 1)
+    Mt1 = int(inst1.degrees[0])
+
+    def oracle_iterates():
+        U = np.tile(W.u0_nodal(inst1, O.space_nodes_grid(spec1)), (Mt1 + 1, 1)).copy()
+        res = []
+        for k in range(kmax1):
+            O.iterate(spec1, 0, inst1.t_breaks[0], inst1.t_breaks[1], Mt1, U, k + 1, 1)
+            res.append(U.copy())
+        return res
+
+    pool = ThreadPoolExecutor(1)
+    fut = pool.submit(oracle_iterates)
+    gpu_iterates = {}
+    for name, prec in (("w1_mixed", L.MIXED), ("w1_fp64", L.FP64)):
+        wl = W.w1()
         plan = Plan.from_workload(wl, precision=prec)
-        ex = W.exact_block(wl, inst, plan.node_grid(), 0)
+        ex = W.exact_block(wl, wl.instances[0], plan.node_grid(), 0)
         plan.begin_interval(0)
-        ms_total, errs, reached = 0.0, [], None
-        for k in range(kmax):
+        ms_total, errs, reached, its = 0.0, [], None, []
+        for k in range(kmax1):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             plan.iterate(0, 1)
             b.record()
             torch.cuda.synchronize()
             ms_total += a.elapsed_time(b)
-            err = float(np.abs(plan.get_nodes(0, 0).cpu().numpy() - ex).max())
-            errs.append(err)
-            if reached is None and err <= tol:
+            U = plan.get_nodes(0, 0).cpu().numpy()
+            its.append(U)
+            errs.append(float(np.abs(U - ex).max()))
+            if reached is None and errs[-1] <= tol:
                 reached = {"iterations": k + 1, "ms": ms_total}
-        out[name] = {"reached": reached, "linf_by_iteration": errs, "ms_per_iteration": ms_total / kmax,
+        gpu_iterates[name] = its
+        out[name] = {"reached": reached, "linf_by_iteration": errs, "ms_per_iteration": ms_total / kmax1,
                      "n_ref": wl.n_ref, "M": wl.M}
         plan.close()
+    out["w2_full_mixed"] = hp_time_to_tol(W.w2(M=args.M), L.MIXED, tol, 12)
+    out["w2_full_mixed_M2048"] = hp_time_to_tol(W.w2(M=2048), L.MIXED, tol, 16)
+    out["w2_full_fp64"] = hp_time_to_tol(W.w2(M=2048), L.FP64, tol, 16)
+    ref = fut.result()
+    pool.shutdown()
+    for name in ("w1_mixed", "w1_fp64"):
+        out[name]["linf_vs_oracle_by_iteration"] = [float(np.abs(g - r).max())
+                                                     for g, r in zip(gpu_iterates[name], ref)]
+    fp = out["w2_full_fp64"]
+    for name in ("w2_full_mixed", "w2_full_mixed_M2048"):
+        if out[name]["reached"] and fp["reached"]:
+            out[name]["speedup_over_fp64_M2048"] = fp["ms"] / out[name]["ms"]
     return out
 
 
 def batch_leg(args):
-    """Batched uneven instances (initial-singularity workload shape) in one plan:
-    64 instances with 8-16 geometric intervals and degrees 4 + 2k, M = 4096,
-    K = 8, first two intervals (node-samples/s, mixed)."""
+    """The batched initial-singularity workload at its full size: 256 uneven
+    instances (8-16 geometric intervals, degrees 4 + 2k, reaction scales in
+    [0.5, 2]) in one plan, M = 32768, K = 8, mixed; the first round of intervals
+    (every instance's interval 1, degree 4) in node-samples/s."""
     import torch
     from paper_2608_22190_b300 import _lib as L
     from paper_2608_22190_b300 import workloads as W
     from paper_2608_22190_b300.api import Plan
-    wl = W.w3(M=4096, batch=64)
+    wl = W.w3()
     plan = Plan.from_workload(wl, precision=L.MIXED)
-    plan.begin_interval(0)
-    plan.iterate(0, 1)
-    torch.cuda.synchronize()
     ns, ms = 0, 0.0
-    for r in range(2):
+    for r in range(1):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         plan.begin_interval(r)
@@ -468,10 +556,9 @@ def batch_leg(args):
         torch.cuda.synchronize()
         ms += a.elapsed_time(b)
         ns += sum(int(i.degrees[r]) * wl.n_space * wl.M * wl.K for i in wl.instances if r < len(i.degrees))
-    st = plan.stats()
     plan.close()
-    return {"value": ns / (ms / 1e3), "unit": "node-samples/s", "instances": len(wl.instances),
-            "sample": "intervals 1-2 of 64 uneven instances, M=4096, K=8", "ms": ms}
+    return {"value": ns / (ms / 1e3), "unit": "node-samples/s", "instances": len(wl.instances), "M": wl.M,
+            "sample": "interval 1 of all 256 instances (full workload size), K = 8", "ms": ms}
 
 
 def run_reference(args):
