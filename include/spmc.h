@@ -116,6 +116,7 @@ typedef struct {
   long long eval_launches;
   double fill_ms;           /* event sweep: the placing walk pass (part of sweep_ms) */
   long long workspace_bytes;/* device memory the plan holds (its own allocations) */
+  long long graph_launches; /* intervals spmc_solve ran as one captured CUDA graph */
 } spmc_stats;
 
 /* Validate desc, build the node tables and allocate the workspace.
@@ -135,7 +136,11 @@ spmc_status spmc_solution_layout(spmc_plan_t plan, int instance, long long* offs
 /* Algorithm 1 for every instance: all intervals, K iterations each (or until
  * max|eps| < tol), hand-off of u*(., t_n) between intervals (Step 4).
  * u_nodes: caller-owned device buffer of spmc_solution_layout's total size;
- * receives every interval's nodal values. */
+ * receives every interval's nodal values.  With a fixed K, the event sweep,
+ * timing off and graphs on (the default, spmc_set_graphs), every interval after
+ * the first -- its hand-off and K iterations -- is captured on the caller's
+ * stream as one CUDA graph and launched at once; the stream is synchronised once
+ * per interval.  Results are the same bit for bit either way. */
 spmc_status spmc_solve(spmc_plan_t plan, void* cuda_stream, double* u_nodes);
 
 /* Stepwise driver.  spmc_begin_interval sets the first iterate of interval
@@ -223,6 +228,10 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
 #define SPMC_SWEEP_COHORT 1
 #define SPMC_SWEEP_EVENTS_ALU 2
 spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch);
+
+/* Enable (1, the default) or disable (0) spmc_solve's capture of each interval
+ * as a CUDA graph.  The caller's stream must not be capturing already. */
+spmc_status spmc_set_graphs(spmc_plan_t plan, int enable);
 
 /* Enable (1) or disable (0) CUDA-event timing of every sweep kernel launch; the
  * totals accumulate in spmc_stats.sweep_ms / sweep_launches (reset on enable). */

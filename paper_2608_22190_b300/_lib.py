@@ -48,7 +48,7 @@ class Stats(C.Structure):
                 ("iterations_run", C.c_int), ("last_max_eps", C.c_double),
                 ("sweep_launches", C.c_longlong), ("sweep_ms", C.c_double),
                 ("walk_ms", C.c_double), ("eval_ms", C.c_double), ("eval_launches", C.c_longlong),
-                ("fill_ms", C.c_double), ("workspace_bytes", C.c_longlong)]
+                ("fill_ms", C.c_double), ("workspace_bytes", C.c_longlong), ("graph_launches", C.c_longlong)]
 
 
 # The C-ABI entry points and their signatures, as declared in include/spmc.h.
@@ -65,6 +65,7 @@ _SIGNATURES = {
     "spmc_iterate_static": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spmc_set_timing": (C.c_int, [_PLAN, C.c_int]),
+    "spmc_set_graphs": (C.c_int, [_PLAN, C.c_int]),
     "spmc_set_sweep": (C.c_int, [_PLAN, C.c_int, C.c_longlong]),
     "spmc_autotune": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_space_nodes": (C.c_int, [_PLAN, C.POINTER(C.c_double)]),

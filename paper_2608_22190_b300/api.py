@@ -180,7 +180,8 @@ class Plan:
         return {"points": s.points, "capped": s.capped, "iterations_run": s.iterations_run,
                 "last_max_eps": s.last_max_eps, "sweep_launches": s.sweep_launches, "sweep_ms": s.sweep_ms,
                 "walk_ms": s.walk_ms, "fill_ms": s.fill_ms, "eval_ms": s.eval_ms,
-                "eval_launches": s.eval_launches, "workspace_bytes": s.workspace_bytes}
+                "eval_launches": s.eval_launches, "workspace_bytes": s.workspace_bytes,
+                "graph_launches": s.graph_launches}
 
     def autotune(self, interval: int = 0, stream=None) -> float:
         """Tune the forward sweep by timing one sweep per candidate setting: the
@@ -196,6 +197,10 @@ class Plan:
         m = {"events": L.SPMC_SWEEP_EVENTS, "cohort": L.SPMC_SWEEP_COHORT,
              "events_alu": L.SPMC_SWEEP_EVENTS_ALU}[mode]
         L.check(L.lib.spmc_set_sweep(self._h, m, int(batch)), self._h)
+
+    def set_graphs(self, enable: bool):
+        """solve(): run each interval after the first as one captured CUDA graph (default on)."""
+        L.check(L.lib.spmc_set_graphs(self._h, 1 if enable else 0), self._h)
 
     def set_timing(self, enable: bool):
         L.check(L.lib.spmc_set_timing(self._h, 1 if enable else 0), self._h)

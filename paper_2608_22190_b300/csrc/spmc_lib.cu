@@ -77,6 +77,8 @@ struct spmc_plan_s {
   long long acc_cap = 0;
   std::map<void*, size_t> allocs;    // device memory the plan holds
   long long ws_bytes = 0;
+  bool use_graphs = true;            // spmc_solve: each interval as one captured CUDA graph
+  cudaStream_t cap_stream = nullptr; // the plan's own stream for capturing (any caller stream may launch)
   std::vector<HostProblem> probs;
   bool built = false;
   std::vector<double> xnodes;
@@ -843,6 +845,59 @@ spmc_status run_iterations(spmc_plan_t plan, cudaStream_t stream, int r, int n_i
   return fail(plan, SPMC_ERR_CUDA, "event sweep: the event buffer kept overflowing");
 }
 
+spmc_status begin_interval(spmc_plan_t plan, cudaStream_t stream, int r);
+
+// One interval of spmc_solve -- the hand-off (or first iterate) and K
+// iterations, about a thousand launches -- captured as one CUDA graph and
+// launched at once.  Used for the event sweep once the plan's buffers hold this
+// round (nothing is allocated or synchronised while capturing); otherwise, or
+// if the capture fails, *done stays false and the caller runs the interval
+// launch by launch.  A batch that outgrows the event buffer is handled as in
+// run_iterations: the iterations from the failed one on run again eagerly.
+spmc_status run_interval_graph(spmc_plan_t plan, cudaStream_t s, int r, int K, bool* done) {
+  *done = false;
+  Round& rd = plan->rounds[r];
+  const spmc_plan_desc& d = plan->d;
+  const bool events = d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT && d.walk_mode == 0;
+  if (!plan->use_graphs || plan->timing || !events || rd.ii.empty() || plan->ev_cap == 0 ||
+      plan->counts_cap < rd.n_slices * plan->S || plan->acc_cap < (long long)rd.tn.size() * plan->S ||
+      plan->bsum_cap < (rd.n_slices * plan->S + 1023) / 1024 || !plan->d_total)
+    return SPMC_OK;
+  // capture on the plan's own stream (the caller's may be the legacy default
+  // stream, which cannot be captured); nothing runs while capturing, and the
+  // graph is launched on the caller's stream
+  if (!plan->cap_stream && cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    plan->cap_stream = nullptr;
+    return SPMC_OK;
+  }
+  cudaStream_t cs = plan->cap_stream;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) { cudaGetLastError(); return SPMC_OK; }
+  spmc_status st = begin_interval(plan, cs, r);
+  for (int k = 0; k < K && st == SPMC_OK; ++k) st = iterate_once(plan, cs, r);
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaGraphExec_t x = nullptr;
+  if (st != SPMC_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    plan->err.clear();
+    rd.iteration = 0;
+    return SPMC_OK;   // run it launch by launch instead
+  }
+  cudaGraphDestroy(g);
+  const cudaError_t le = cudaGraphLaunch(x, s);
+  cudaGraphExecDestroy(x);   // freed once the launch completes
+  if (le != cudaSuccess) return fail(plan, SPMC_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(le));
+  plan->stats.graph_launches += 1;
+  *done = true;
+  int failed = 0;
+  if ((st = recover_abort(plan, s, &failed)) != SPMC_OK) return st;
+  if (failed == 0) return SPMC_OK;
+  rd.iteration = failed - 1;
+  return run_iterations(plan, s, r, K - (failed - 1));
+}
+
 // Copy the round's nodal blocks between U and a contiguous buffer (offsets c_off/2).
 __global__ void round_copy_kernel(const InstInterval* __restrict__ ii, double* __restrict__ U,
                                   double* __restrict__ buf, int S, int to_buf) {
@@ -1222,7 +1277,13 @@ spmc_status spmc_solve(spmc_plan_t plan, void* cuda_stream, double* u_nodes) {
   int total_iters = 0;
   double mx = 0.0;
   for (int r = 0; r < (int)plan->rounds.size(); ++r) {
-    spmc_status st = begin_interval(plan, s, r);
+    spmc_status st;
+    if (d.tol <= 0.0) {
+      bool done = false;
+      if ((st = run_interval_graph(plan, s, r, d.K, &done)) != SPMC_OK) return st;
+      if (done) { total_iters += d.K; continue; }
+    }
+    st = begin_interval(plan, s, r);
     if (st != SPMC_OK) return st;
     if (d.tol > 0.0) {
       for (int k = 0; k < d.K; ++k) {
@@ -1535,6 +1596,12 @@ spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch) {
   return SPMC_OK;
 }
 
+spmc_status spmc_set_graphs(spmc_plan_t plan, int enable) {
+  if (!plan) return SPMC_ERR_INVALID;
+  plan->use_graphs = enable != 0;
+  return SPMC_OK;
+}
+
 spmc_status spmc_set_timing(spmc_plan_t plan, int enable) {
   if (!plan) return SPMC_ERR_INVALID;
   drain_timing(plan);
@@ -1566,6 +1633,7 @@ void spmc_destroy(spmc_plan_t plan) {
   if (!plan) return;
   drain_timing(plan);
   for (auto& ev : plan->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
   for (auto& kv : plan->allocs) cudaFree(kv.first);   // every device allocation of the plan
   plan->allocs.clear();
   delete plan;

@@ -19,7 +19,8 @@ Workloads (sizes as the benchmarks state them; Section 4 examples they stand in 
       8 JG nodes per axis x 8 LGL, M = 16384, K = 6              (Ex. 4 shape)
   w5  adjoint: 2-D u_t = 0.01 Delta u + a (u - u^3), T = 5 in 10 intervals,
       16 x 16 JG x 12 LGL, M = 16384, u0 = sum_{i,j<8} c_ij phi_i phi_j with
-      c_ij = z_ij / (1+i+j)^2, z ~ N(0,1); 128 instances
+      c_ij = z_ij / (1+i+j)^2, z ~ N(0,1), scaled down to max |u0| = 1 where the
+      draw exceeds it (the phase variable's range); 128 instances
 The paper uses no public dataset; these synthetic inputs stand in for its
 examples (its data is only available on request).
 """
@@ -119,12 +120,29 @@ def w5(M: int = 16384, K: int = 8, seed: int = 0, batch: int = 128, n_space: int
     insts = []
     i = np.arange(n_coef)
     decay = 1.0 / (1.0 + i[:, None] + i[None, :]) ** 2
+    # u0 on a fine grid of the square, for the amplitude cap below
+    g = np.linspace(-1.0, 1.0, 129)
+    phi = np.stack([phi_values(p, g) for p in range(n_coef)])          # [p, point]
     for b in range(batch):
-        z = rng.standard_normal((n_coef, n_coef))
+        c = rng.standard_normal((n_coef, n_coef)) * decay
+        # Allen-Cahn's phase variable lies in [-1, 1]; draws whose initial data
+        # leave it are scaled back to max |u0| = 1 (then |f'(u)| <= 2 and h |f'| <= 1)
+        amp = np.abs(phi.T @ c @ phi).max()
+        if amp > 1.0:
+            c = c / amp
         insts.append(Instance(t_breaks=uniform_mesh(T, n_intervals), degrees=np.full(n_intervals, degree),
                               f_coef=(0, 1.0, 0, -1.0), f_scale=1.0, ex_kind=EX_NONE, u0_kind="phi_coef",
-                              u0_coef=z * decay))
+                              u0_coef=c))
     return Workload("w5-2d-adjoint-batch", 2, n_space, TIME_LGL, M, K, kappa=0.01, seed=seed, instances=insts)
+
+
+def phi_values(p: int, x: np.ndarray) -> np.ndarray:
+    """phi_p(x) = 2(p+1)/(2p+3) (L_p(x) - L_{p+2}(x)) (Section 2.3), for building
+    initial data from coefficients."""
+    from numpy.polynomial import legendre as npleg
+    c = np.zeros(p + 3)
+    c[p], c[p + 2] = 1.0, -1.0
+    return 2.0 * (p + 1) / (2 * p + 3) * npleg.legval(x, c)
 
 
 def uniform_points(n: int, dim: int, seed: int) -> np.ndarray:

@@ -44,8 +44,15 @@ def api():
     return A
 
 
-@pytest.mark.parametrize("precision,h,rtol", [(0, 1e-5, 1e-6), (1, 1e-3, 2e-3)])
+@pytest.mark.parametrize("precision,h,rtol", [(0, 1e-5, 1e-6), (1, 1e-5, 1e-5)])
 def test_grad_matches_central_differences(api, precision, h, rtol):
+    """Central differences of the FP64 solve on the same Philox streams (a smooth
+    function of the parameters: the walks do not depend on them).  The mixed
+    path's adjoint (FP32 walks and basis values, FP64 accumulation) is compared
+    with the same FP64 differences: it differs from them by FP32 rounding of the
+    walk and of the basis (about 1e-7 relative) and by the rare walks whose
+    decisions flip between FP32 and FP64, well inside 1e-5.  (Differences of the
+    mixed solve itself would carry its FP32 rounding divided by h.)"""
     wl = _workload()
     scales = np.array([i.f_scale for i in wl.instances])
     coefs = np.array([i.u0_coef for i in wl.instances])
@@ -60,7 +67,7 @@ def test_grad_matches_central_differences(api, precision, h, rtol):
         def loss_at(ds, dc):
             s2 = scales.copy(); s2[b] += ds
             c2 = coefs.copy(); c2[b] += dc
-            p, f = _solve(api, wl, precision, s2, c2)
+            p, f = _solve(api, wl, 0, s2, c2)
             v, _ = _loss_and_z(p, f)
             p.close()
             return v

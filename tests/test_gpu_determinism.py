@@ -58,3 +58,22 @@ def test_event_sweep_recovers_from_a_full_event_buffer(api):
         plan.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_as_graphs_matches_launch_by_launch(api, precision):
+    """spmc_solve runs every interval after the first as one captured CUDA graph
+    (hand-off and K iterations); the result equals the launch-by-launch solve
+    bit for bit, and the graphs were really launched."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w2(M=1500, K=3, n_space=8, degree=4, n_intervals=3, h=0.4)
+    wl.n_ref = 24
+    out = {}
+    for graphs in (True, False):
+        plan = api.Plan.from_workload(wl, precision=precision)
+        plan.set_graphs(graphs)
+        flat = plan.solve()
+        out[graphs] = (flat.cpu().numpy(), plan.stats()["graph_launches"])
+        plan.close()
+    assert out[True][1] == 2 and out[False][1] == 0
+    assert np.array_equal(out[True][0], out[False][0])
