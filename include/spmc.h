@@ -191,6 +191,31 @@ spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, in
 #define SPMC_STATIC_SCRATCH_BYTES (16u << 20)
 spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interval, double* max_eps_host);
 
+/* Node-sharded iterations, for running one batch of instances on several GPUs
+ * (the sampled nodes of a sweep are independent; Algorithm 1, Step 2 parallel
+ * over nodes).  Every rank holds the same plan and nodal values and
+ * reconstructs redundantly; each samples its share of the round's
+ * (time node, spatial node) pairs and the eps of all pairs are exchanged once
+ * per iteration.
+ *  - spmc_round_nodes: the number of pairs of interval `interval`: n_pairs =
+ *    (sum over its instances of M_n) x n_space^d; pair i = ti n_space^d + j, ti
+ *    running over the instances (in order) and their time nodes l = 1..M_n.
+ *  - spmc_iterate_shard: the sweep of the next iteration for the pairs
+ *    [n rank / world, n (rank + 1) / world) only; writes their eps to
+ *    eps_pairs[i] (device, n_pairs doubles; other entries untouched) and does
+ *    not change the nodal values.  Event sweep only (d <= 2, inside-ball walk):
+ *    SPMC_ERR_UNSUPPORTED otherwise.  Per-pair eps are exact sums, so the
+ *    shards' eps equal those of an unsharded iteration bit for bit.
+ *  - spmc_apply_eps: u += eps for every pair of the interval (eps_pairs on the
+ *    device, e.g. after an all-reduce of the ranks' zero-filled buffers) and
+ *    advance the iteration count; returns the largest |eps|.
+ * The stream is synchronised by each call. */
+spmc_status spmc_round_nodes(spmc_plan_t plan, int interval, long long* n_pairs);
+spmc_status spmc_iterate_shard(spmc_plan_t plan, void* cuda_stream, int interval, int rank, int world,
+                               double* eps_pairs);
+spmc_status spmc_apply_eps(spmc_plan_t plan, void* cuda_stream, int interval, const double* eps_pairs,
+                           double* max_eps_host);
+
 /* Reverse-mode gradient of L(u(T)) for every instance: given dL/du at the
  * spatial nodes at t = T (device, batch x n_space^d doubles), returns
  * dL/d(f_scale) (device, batch doubles) and dL/d(u0 coefficients) (device,

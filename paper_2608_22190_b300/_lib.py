@@ -66,6 +66,9 @@ _SIGNATURES = {
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spmc_set_timing": (C.c_int, [_PLAN, C.c_int]),
     "spmc_set_graphs": (C.c_int, [_PLAN, C.c_int]),
+    "spmc_round_nodes": (C.c_int, [_PLAN, C.c_int, C.POINTER(C.c_longlong)]),
+    "spmc_iterate_shard": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "spmc_apply_eps": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "spmc_set_sweep": (C.c_int, [_PLAN, C.c_int, C.c_longlong]),
     "spmc_autotune": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_space_nodes": (C.c_int, [_PLAN, C.POINTER(C.c_double)]),

@@ -129,6 +129,27 @@ class Plan:
         L.check(L.lib.spmc_iterate(self._h, C.c_void_p(_stream_ptr(stream)), interval, n_iter, C.byref(mx)), self._h)
         return mx.value
 
+    def round_nodes(self, interval: int) -> int:
+        """Number of (time node, spatial node) pairs sampled on `interval`."""
+        n = C.c_longlong()
+        L.check(L.lib.spmc_round_nodes(self._h, interval, C.byref(n)), self._h)
+        return n.value
+
+    def iterate_shard(self, interval: int, rank: int, world: int, eps: torch.Tensor, stream=None):
+        """The next iteration's sweep for this rank's share of the pairs; writes
+        their eps into `eps` (float64, device, round_nodes(interval) entries)."""
+        assert eps.dtype == torch.float64 and eps.is_cuda and eps.numel() >= self.round_nodes(interval)
+        L.check(L.lib.spmc_iterate_shard(self._h, C.c_void_p(_stream_ptr(stream)), interval, rank, world,
+                                         C.c_void_p(eps.data_ptr())), self._h)
+
+    def apply_eps(self, interval: int, eps: torch.Tensor, stream=None) -> float:
+        """u += eps for every pair of `interval`; returns max |eps|."""
+        assert eps.dtype == torch.float64 and eps.is_cuda
+        mx = C.c_double()
+        L.check(L.lib.spmc_apply_eps(self._h, C.c_void_p(_stream_ptr(stream)), interval,
+                                     C.c_void_p(eps.data_ptr()), C.byref(mx)), self._h)
+        return mx.value
+
     def final_values(self, flat: torch.Tensor) -> torch.Tensor:
         """u(T) at the spatial nodes for every instance: the last row of each
         instance's last interval (LGL time nodes end at t_n), shape (batch, S)."""

@@ -44,6 +44,7 @@ struct EventArgs {
   int n, S, n_sub, gbits, max_steps, interval, iteration;
   long long n_tn;
   long long i0, nb;              // sample range of the batch
+  long long node_lo, node_cnt;   // the (time node, spatial node) pairs walked: ti S + j in [node_lo, node_lo + node_cnt)
   double kappa, shell;
   uint32_t k0, k1;
   unsigned long long* counters;  // [0] points, [1] capped
@@ -59,8 +60,8 @@ struct EmitQueue {
   uint32_t key[CAP], w0[CAP], sample[CAP], node[CAP], tag[CAP], gdir[CAP];
 };
 
-// Every walk of the batch, lane by lane.  Walk ids are (ti * S + j) * nb + il
-// (sample fastest); block b owns the ids b, b + G, b + 2G, ... (G = grid size),
+// Every walk of the batch, lane by lane.  Walk ids are (node - node_lo) nb + il
+// with node = ti S + j (sample fastest); block b owns the ids b, b + G, b + 2G, ... (G = grid size),
 // an even mix of every time node and node, and its lanes take them one at a
 // time from a shared counter as their walks end, so no lane waits for a fixed
 // list of long walks.  COUNT counts the evaluation events per (slice, node);
@@ -91,8 +92,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
   EmitQueue<R>& Q = s_q[FILL ? (threadIdx.x >> 5) : 0];
   int qn = 0;   // entries in this warp's queue (warp-uniform)
 
-  const long long total = a.n_tn * S * nb;
-  const long long per_tn = (long long)S * nb;
+  const long long total = a.node_cnt * nb;
   const long long mine = total > (long long)blockIdx.x ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
@@ -164,18 +164,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
           more = false;
         } else {
           const long long wid = (long long)blockIdx.x + (long long)kk * gridDim.x;
-          long long ti, il;
-          int j;
+          long long node, il;
           if (total < (1ll << 32)) {   // 32-bit division (the usual case: about 2^25 walks per batch)
-            const uint32_t w32 = (uint32_t)wid, pt = (uint32_t)per_tn, nb32 = (uint32_t)nb;
-            const uint32_t t32 = w32 / pt, rem = w32 - t32 * pt, j32 = rem / nb32;
-            ti = t32; j = (int)j32; il = rem - j32 * nb32;
+            const uint32_t w32 = (uint32_t)wid, nb32 = (uint32_t)nb;
+            const uint32_t q32 = w32 / nb32;
+            node = q32; il = w32 - q32 * nb32;
           } else {
-            ti = wid / per_tn;
-            const long long rem = wid - ti * per_tn;
-            j = (int)(rem / nb);
-            il = rem - (long long)j * nb;
+            node = wid / nb;
+            il = wid - node * nb;
           }
+          node += a.node_lo;
+          const long long ti = node / S;
+          const int j = (int)(node - ti * S);
           if (ti != cached_ti) {   // time-node parameters, as the CPU reference computes them
             const TimeNode node = a.tn[ti];
             const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);

@@ -643,6 +643,31 @@ __global__ void update_fixed_kernel(const TimeNode* __restrict__ tn, const unsig
   atomicMax(&max_eps_bits[node.inst], (unsigned long long)__double_as_longlong(fabs(e)));
 }
 
+// The node-sharded iteration: eps of the pairs i in [lo, hi) from their exact
+// sums (no update), and the update of every pair from a gathered eps array.
+__global__ void eps_out_kernel(const unsigned long long* __restrict__ acc, double* __restrict__ eps, long long lo,
+                               long long hi, double inv_M, int* status, const int* __restrict__ abort) {
+  if (*abort) return;
+  const long long i = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
+  const double e = fix_value(acc + 4 * i) * inv_M;
+  if (!isfinite(e)) atomicOr(status, 1);
+  eps[i] = e;
+}
+__global__ void apply_eps_kernel(const TimeNode* __restrict__ tn, const double* __restrict__ eps,
+                                 double* __restrict__ U, unsigned long long* __restrict__ max_eps_bits, int* status,
+                                 long long n_nodes, int S) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  const long long ti = i / S;
+  const int j = (int)(i - ti * S);
+  const TimeNode node = tn[ti];
+  const double e = eps[i];
+  if (!isfinite(e)) atomicOr(status, 1);
+  U[node.u_off + (long long)node.ell * S + j] += e;
+  atomicMax(&max_eps_bits[node.inst], (unsigned long long)__double_as_longlong(fabs(e)));
+}
+
 // ----------------------------------------------------------------- Step 4 and first iterate
 // row 0 of interval 0 from u0; every other row equal to row 0.
 __global__ void init_first_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ u0,

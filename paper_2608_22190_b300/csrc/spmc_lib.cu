@@ -632,7 +632,8 @@ spmc_status size_event_buffer(spmc_plan_t plan, unsigned long long events) {
 // batch's total against it on the device (see the abort word in
 // spmc_events.cuh).
 template <int D, typename R>
-spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration,
+                          long long node_lo, long long node_cnt) {
   const spmc_plan_desc& d = plan->d;
   const int S = plan->S;
   const long long n_tn = (long long)rd.tn.size();
@@ -677,6 +678,7 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   a.n_tn = n_tn; a.kappa = d.kappa; a.shell = plan->shell;
   a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
   a.counters = plan->d_counters;
+  a.node_lo = node_lo; a.node_cnt = node_cnt;
   int dev = 0, sms = 0;
   SPMC_CUDA(cudaGetDevice(&dev));
   SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -740,12 +742,16 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   return SPMC_OK;
 }
 
-spmc_status event_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+// The event sweep over the (time node, spatial node) pairs ti S + j in
+// [node_lo, node_lo + node_cnt) of round rd (node_cnt < 0: all of them).
+spmc_status event_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration,
+                        long long node_lo = 0, long long node_cnt = -1) {
+  if (node_cnt < 0) node_cnt = (long long)rd.tn.size() * plan->S - node_lo;
   const bool fp64 = plan->d.precision == SPMC_FP64;
-  if (plan->d.dim == 1) return fp64 ? event_sweep_t<1, double>(plan, stream, rd, interval, iteration)
-                                    : event_sweep_t<1, float>(plan, stream, rd, interval, iteration);
-  return fp64 ? event_sweep_t<2, double>(plan, stream, rd, interval, iteration)
-              : event_sweep_t<2, float>(plan, stream, rd, interval, iteration);
+  if (plan->d.dim == 1) return fp64 ? event_sweep_t<1, double>(plan, stream, rd, interval, iteration, node_lo, node_cnt)
+                                    : event_sweep_t<1, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
+  return fp64 ? event_sweep_t<2, double>(plan, stream, rd, interval, iteration, node_lo, node_cnt)
+              : event_sweep_t<2, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
 }
 
 // Copy the point / capped counters aside at the start of an iteration (unless
@@ -1388,6 +1394,70 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
   plan->stats.iterations_run = 1;
   plan->stats.last_max_eps = mx;
   if (max_eps_host) *max_eps_host = mx;
+  return SPMC_OK;
+}
+
+spmc_status spmc_round_nodes(spmc_plan_t plan, int interval, long long* n_pairs) {
+  if (!plan || !n_pairs) return SPMC_ERR_INVALID;
+  if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "plan not built");
+  if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  *n_pairs = (long long)plan->rounds[interval].tn.size() * plan->S;
+  return SPMC_OK;
+}
+
+spmc_status spmc_iterate_shard(spmc_plan_t plan, void* cuda_stream, int interval, int rank, int world,
+                               double* eps_pairs) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built || plan->params_dirty) return fail(plan, SPMC_ERR_INVALID, "call spmc_begin_interval first");
+  if (interval < 0 || interval >= (int)plan->rounds.size() || world < 1 || rank < 0 || rank >= world || !eps_pairs)
+    return fail(plan, SPMC_ERR_INVALID, "bad interval, rank or output");
+  if (plan->d.dim > 2 || plan->sweep_mode == SPMC_SWEEP_COHORT || plan->d.walk_mode != 0)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_iterate_shard: the event sweep only (d <= 2, inside-ball walk)");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Round& rd = plan->rounds[interval];
+  const long long n = (long long)rd.tn.size() * plan->S;
+  const long long lo = n * rank / world, hi = n * (rank + 1) / world;
+  if (rd.ii.empty() || hi <= lo) return SPMC_OK;
+  const int iteration = rd.iteration + 1;   // spmc_apply_eps advances the count
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    counters_snapshot_kernel<<<1, 32, 0, s>>>(plan->d_counters, plan->d_counters_bak, plan->d_abort);
+    spmc_status st = prepare_slices(plan, s, rd);
+    if (st == SPMC_OK) st = event_sweep(plan, s, rd, interval, iteration, lo, hi - lo);
+    if (st != SPMC_OK) return st;
+    eps_out_kernel<<<(unsigned)((hi - lo + 255) / 256), 256, 0, s>>>(plan->d_acc, eps_pairs, lo, hi,
+                                                                   1.0 / (double)plan->d.M, plan->d_status,
+                                                                   plan->d_abort);
+    SPMC_CUDA(cudaGetLastError());
+    int failed = 0;
+    if ((st = recover_abort(plan, s, &failed)) != SPMC_OK) return st;
+    if (failed == 0) return read_status(plan, s);
+  }
+  return fail(plan, SPMC_ERR_CUDA, "event sweep: the event buffer kept overflowing");
+}
+
+spmc_status spmc_apply_eps(spmc_plan_t plan, void* cuda_stream, int interval, const double* eps_pairs,
+                           double* max_eps_host) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "call spmc_begin_interval first");
+  if (interval < 0 || interval >= (int)plan->rounds.size() || !eps_pairs)
+    return fail(plan, SPMC_ERR_INVALID, "bad interval or input");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Round& rd = plan->rounds[interval];
+  rd.iteration += 1;
+  const long long n = (long long)rd.tn.size() * plan->S;
+  SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, s));
+  if (n > 0) {
+    apply_eps_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rd.d_tn, eps_pairs, plan->d_U, plan->d_maxeps,
+                                                                 plan->d_status, n, plan->S);
+    SPMC_CUDA(cudaGetLastError());
+  }
+  spmc_status st = read_status(plan, s);
+  if (st != SPMC_OK) return st;
+  double mx = 0.0;
+  if ((st = read_max_eps(plan, s, &mx)) != SPMC_OK) return st;
+  if (max_eps_host) *max_eps_host = mx;
+  plan->stats.iterations_run = 1;
+  plan->stats.last_max_eps = mx;
   return SPMC_OK;
 }
 

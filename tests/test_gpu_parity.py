@@ -323,3 +323,60 @@ def test_mixed_eps_matches_oracle_at_benchmark_geometry(O, api):
     assert abs(pts_mx - pts_64) <= 1e-6 * pts_64, (pts_mx, pts_64)
     assert worst <= 1e-6 + 5e-5, worst
     assert d_all <= 1e-6 + 3 * 5e-5, d_all
+
+
+def test_fp64_batch_full_size_sampled_instances(O, api):
+    """The initial-singularity batch at its full size (256 instances with 8-16
+    geometric intervals, degrees 4 + 2k, M = 32768) in one plan, FP64: the first
+    iteration of intervals 1 and 2 (the second after the hand-off of Algorithm 1,
+    Step 4) at sampled nodes of two sampled instances, each recomputed by the
+    oracle from that instance's first iterate on the same Philox streams."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w3()
+    plan = api.Plan.from_workload(wl, precision=0)
+    rng = np.random.default_rng(31)
+    picks = [int(b) for b in rng.choice(len(wl.instances), 2, replace=False)]
+    for r in (0, 1):
+        plan.begin_interval(r)
+        U0 = {b: plan.get_nodes(b, r).cpu().numpy() for b in picks}
+        plan.iterate(r, 1)
+        for b in picks:
+            inst = wl.instances[b]
+            U1 = plan.get_nodes(b, r).cpu().numpy()
+            spec = oracle_spec(O, wl, inst, instance=b)
+            Mt = int(inst.degrees[r])
+            t0, h = float(inst.t_breaks[r]), float(inst.t_breaks[r + 1] - inst.t_breaks[r])
+            cu, ct = O.reconstruct(spec, Mt, h, U0[b])
+            tol = parity_tol(U1)
+            for _ in range(2):
+                l = int(rng.integers(1, Mt + 1))
+                j = int(rng.integers(0, wl.n_space))
+                e = O.node_eps(spec, Mt, t0, h, cu, ct, j, l, interval=r, iteration=1)
+                assert abs(U1[l, j] - (U0[b][l, j] + e)) <= tol[l, j], (r, b, l, j, U1[l, j] - U0[b][l, j] - e)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sharded_iterations_equal_unsharded(api, precision):
+    """The node-sharded iteration on one GPU, shard after shard (three ranks'
+    shares run in turn, no rank waits on another), then one application of the
+    assembled eps: bit for bit the unsharded iteration, twice in a row."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w2(M=900, K=2, n_space=7, degree=4, n_intervals=1, h=0.5)
+    wl.n_ref = 16
+    ref = api.Plan.from_workload(wl, precision=precision)
+    shd = api.Plan.from_workload(wl, precision=precision)
+    ref.begin_interval(0)
+    shd.begin_interval(0)
+    n = shd.round_nodes(0)
+    assert n == 4 * 49
+    for _ in range(2):
+        e_ref = ref.iterate(0, 1)
+        eps = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for rank in range(3):
+            shd.iterate_shard(0, rank, 3, eps)
+        e_shd = shd.apply_eps(0, eps)
+        assert np.array_equal(ref.get_nodes(0, 0).cpu().numpy(), shd.get_nodes(0, 0).cpu().numpy())
+        assert e_ref == e_shd
+    ref.close()
+    shd.close()
