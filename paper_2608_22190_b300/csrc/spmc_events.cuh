@@ -33,6 +33,16 @@ struct Event {
   unsigned int key;   // (slice, spatial node) = slice * S + j
 };
 
+// A 5-D event (Green point, weight, key).
+template <typename R>
+struct Event5 {
+  R y[5];
+  R w;
+  unsigned int key;
+};
+template <int D, typename R> struct EventOf { using type = Event<R>; };
+template <typename R> struct EventOf<5, R> { using type = Event5<R>; };
+
 struct EventArgs {
   const TimeNode* tn;
   const double* xnodes;
@@ -53,10 +63,10 @@ struct EventArgs {
 // Per-warp queue of pending evaluation events of the placing pass: what the
 // Green point and the slot need (centre, radius, weight, key, the step's stream
 // coordinates and its Green-direction word).
-template <typename R>
+template <int D, typename R>
 struct EmitQueue {
   static constexpr int CAP = 64;          // two warps' worth: 32 are flushed at a time
-  R x0[CAP], x1[CAP], r[CAP], w[CAP];
+  R x[D][CAP], r[CAP], w[CAP];
   uint32_t key[CAP], w0[CAP], sample[CAP], node[CAP], tag[CAP], gdir[CAP];
 };
 
@@ -76,20 +86,27 @@ struct EmitQueue {
 // share one atomic).  FILL appends it to its warp's queue; once 32 are queued
 // the whole warp computes their Green points (a second Philox block, the radial
 // law, the direction), claims their slots and stores them, all lanes together.
+//
+// Word layouts (one step): d <= 2, eight words -- [direction, Green direction,
+// sub-point, roulette | Green radius uniforms] -- so the words every step needs
+// sit in one Philox block; d = 5, 28 words -- [direction 12 | Green direction
+// 12 | radius pair, sub-point, roulette] -- so a step reads its sub-point and
+// roulette words from its seventh block and its direction from its first three.
 template <int D, typename R, bool FILL>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kernel(EventArgs a) {
-  static_assert(D <= 2, "the event sweep reads a step's words from one Philox block (d <= 2 layout)");
+__global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_events_kernel(EventArgs a) {
+  static_assert(D <= 2 || D == 5, "event sweep: d = 1, 2 or 5");
+  using Ev = typename EventOf<D, R>::type;
   if (*a.abort) return;
   __shared__ unsigned long long s_next;
-  __shared__ EmitQueue<R> s_q[FILL ? 8 : 1];   // one queue per warp of the 256-thread block
+  __shared__ EmitQueue<D, R> s_q[FILL ? 8 : 1];   // one queue per warp of the 256-thread block
   const int S = a.S, n = a.n, G = a.n_sub;
   const long long nb = a.nb;
   const R kappa = (R)a.kappa, shell = (R)a.shell;
-  Event<R>* ev = reinterpret_cast<Event<R>*>(a.events);
+  Ev* ev = reinterpret_cast<Ev*>(a.events);
   unsigned long long capped = 0, points = 0;
   const unsigned int lane = threadIdx.x & 31;
   const unsigned int lt_mask = (1u << lane) - 1u;
-  EmitQueue<R>& Q = s_q[FILL ? (threadIdx.x >> 5) : 0];
+  EmitQueue<D, R>& Q = s_q[FILL ? (threadIdx.x >> 5) : 0];
   int qn = 0;   // entries in this warp's queue (warp-uniform)
 
   const long long total = a.node_cnt * nb;
@@ -113,21 +130,28 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
       if ((int)lane == leader) slot = atomicAdd(&a.counts[key], (unsigned int)__popc(peers));
       R thg[D];
       const uint32_t gd = Q.gdir[lane];
-      if (D == 1) {
+      if constexpr (D == 1) {
         thg[0] = (gd >> 31) ? R(-1) : R(1);
-      } else {
+      } else if constexpr (D == 2) {
         const R U = U01<R>::one(gd);
         R sn, cs;
         Ar<R>::sincos2pi(U, &sn, &cs);
         thg[0] = cs; thg[1] = sn;
+      } else {
+        direction<D, R>(w2, Q.w0[lane] + gdir_index(D), thg);
       }
       R U1, U2;
       green_uniforms<D, R>(w2, Q.w0[lane], U1, U2);
       const R v = green_radius<D, R>(U1, U2);
       const R rv = Ar<R>::mul(Q.r[lane], v);
-      Event<R> e;
-      e.y[0] = Ar<R>::add(Q.x0[lane], Ar<R>::mul(rv, thg[0]));
-      e.y[1] = (D == 2) ? Ar<R>::add(Q.x1[lane], Ar<R>::mul(rv, thg[1])) : R(0);
+      Ev e;
+      if constexpr (D == 1) {
+        e.y[0] = Ar<R>::add(Q.x[0][lane], Ar<R>::mul(rv, thg[0]));
+        e.y[1] = R(0);
+      } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) e.y[d] = Ar<R>::add(Q.x[d][lane], Ar<R>::mul(rv, thg[d]));
+      }
       e.w = Q.w[lane];
       e.key = key;
       slot = __shfl_sync(peers, slot, leader) + __popc(peers & lt_mask);   // the round trip overlaps the Green point
@@ -217,10 +241,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
         if (q >= a.max_steps) ++capped;
         live = false;
       } else {
-        w0 = (uint32_t)q * WS;   // a multiple of 8 (d <= 2)
-        // direction, Green direction, sub-point and roulette words: one block
-        b0 = ws.block(w0 >> 2);
-        const uint32_t gword = b0.v[gword_index(D)];
+        w0 = (uint32_t)q * WS;   // a multiple of 4
+        // the block of the sub-point and roulette words (d <= 2: also the
+        // direction and Green-direction words)
+        b0 = ws.block((w0 + gword_index(D)) >> 2);
+        const uint32_t gword = b0.v[gword_index(D) & 3];
         const int g = a.gbits ? (int)(gword >> (32 - a.gbits)) : 0;
         const R left = Ar<R>::sub(Ar<R>::mul((R)(Ktot - k), sub), f);
         int m;
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
           }
         }
         // roulette for shrunk balls
-        if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D)], Ar<R>::div(w, delta)) ? delta : R(0);
+        if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D) & 3], Ar<R>::div(w, delta)) ? delta : R(0);
         emit = w > R(0);
         // keys fit 32 bits (the host checks n_slices S < 2^32)
         key = ((uint32_t)slice_base + (uint32_t)m) * (uint32_t)S + (uint32_t)key_j;
@@ -264,26 +289,31 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
     } else if (emask) {
       if (emit) {
         const int pos = qn + __popc(emask & lt_mask);
-        Q.x0[pos] = X[0]; Q.x1[pos] = (D == 2) ? X[D - 1] : R(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) Q.x[d][pos] = X[d];
         Q.r[pos] = r; Q.w[pos] = w; Q.key[pos] = key; Q.w0[pos] = w0;
         Q.sample[pos] = ws.sample; Q.node[pos] = ws.node; Q.tag[pos] = ws.tag;
-        Q.gdir[pos] = b0.v[gdir_index(D)];
+        Q.gdir[pos] = (D <= 2) ? b0.v[gdir_index(D) & 3] : 0u;
       }
       qn += __popc(emask);
       if (qn >= 32) {
         flush(32);
         // move the entries beyond the first 32 down
         const int rest = qn - 32;
-        R t0 = R(0), t1 = R(0), t2 = R(0), t3 = R(0);
+        R tx[D], t2 = R(0), t3 = R(0);
         uint32_t u0 = 0, u1 = 0, u2 = 0, u3 = 0, u4 = 0, u5 = 0;
         if ((int)lane < rest) {
           const int src = 32 + lane;
-          t0 = Q.x0[src]; t1 = Q.x1[src]; t2 = Q.r[src]; t3 = Q.w[src];
+#pragma unroll
+          for (int d = 0; d < D; ++d) tx[d] = Q.x[d][src];
+          t2 = Q.r[src]; t3 = Q.w[src];
           u0 = Q.key[src]; u1 = Q.w0[src]; u2 = Q.sample[src]; u3 = Q.node[src]; u4 = Q.tag[src]; u5 = Q.gdir[src];
         }
         __syncwarp();
         if ((int)lane < rest) {
-          Q.x0[lane] = t0; Q.x1[lane] = t1; Q.r[lane] = t2; Q.w[lane] = t3;
+#pragma unroll
+          for (int d = 0; d < D; ++d) Q.x[d][lane] = tx[d];
+          Q.r[lane] = t2; Q.w[lane] = t3;
           Q.key[lane] = u0; Q.w0[lane] = u1; Q.sample[lane] = u2; Q.node[lane] = u3; Q.tag[lane] = u4;
           Q.gdir[lane] = u5;
         }
@@ -296,15 +326,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) walk_events_kerne
       if (last) {
         live = false;
       } else {
-        if (D == 1) {
+        if constexpr (D == 1) {
           const R th = (b0.v[0] >> 31) ? R(-1) : R(1);
           X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, th));
-        } else {
+        } else if constexpr (D == 2) {
           const R U = U01<R>::one(b0.v[0]);
           R sn, cs;
           Ar<R>::sincos2pi(U, &sn, &cs);
           X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, cs));
-          X[D - 1] = Ar<R>::add(X[D - 1], Ar<R>::mul(r, sn));
+          X[1] = Ar<R>::add(X[1], Ar<R>::mul(r, sn));
+        } else {
+          R th[D];
+          direction<D, R>(ws, w0, th);
+#pragma unroll
+          for (int d = 0; d < D; ++d) X[d] = Ar<R>::add(X[d], Ar<R>::mul(r, th[d]));
         }
         ++q;
       }

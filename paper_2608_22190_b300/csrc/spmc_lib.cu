@@ -16,6 +16,7 @@
 #include "spmc_kernels.cuh"
 #include "spmc_events.cuh"
 #include "spmc_tc.cuh"
+#include "spmc_tc5.cuh"
 #include "spmc_tables.h"
 
 using namespace spmc;
@@ -78,6 +79,8 @@ struct spmc_plan_s {
   std::map<void*, size_t> allocs;    // device memory the plan holds
   long long ws_bytes = 0;
   bool use_graphs = true;            // spmc_solve: each interval as one captured CUDA graph
+  void* d_tc5 = nullptr;             // d = 5 mixed event sweep: slices in the tensor-core layout
+  size_t tc5_bytes = 0;
   cudaStream_t cap_stream = nullptr; // the plan's own stream for capturing (any caller stream may launch)
   std::vector<HostProblem> probs;
   bool built = false;
@@ -460,6 +463,15 @@ spmc_status dispatch_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& r
   return fail(plan, SPMC_ERR_UNSUPPORTED, "dimension not built");
 }
 
+// The forward sweep is the event pipeline: d <= 2, or d = 5 in mixed precision
+// (tensor-core evaluation), with the inside-ball walk and unless the cohort
+// kernel is chosen.
+bool uses_events(spmc_plan_t plan) {
+  const spmc_plan_desc& d = plan->d;
+  return (d.dim <= 2 || (d.dim == 5 && d.precision == SPMC_MIXED)) && plan->sweep_mode != SPMC_SWEEP_COHORT &&
+         d.walk_mode == 0;
+}
+
 // Reconstruction (Step 1) and time slices of the current nodal values of round rd.
 spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
@@ -479,6 +491,23 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
     }
     coef_finish_kernel<<<grid, 256, 0, stream>>>(rd.d_ii, buf[cur], plan->d_coef, S);
     SPMC_CUDA(cudaGetLastError());
+    if (rd.n_slices > 0 && uses_events(plan)) {
+      // the slices of the tensor-core evaluation: [C | Lam_1 C | Lam_2 C | H], TF32 hi / lo
+      const size_t need = Tc5::SLICE_BYTES * (size_t)rd.n_slices;
+      if (plan->tc5_bytes < need) {
+        pfree(plan, plan->d_tc5);
+        plan->d_tc5 = nullptr;
+        plan->tc5_bytes = 0;
+        SPMC_CUDA(pmalloc(plan, &plan->d_tc5, need));
+        plan->tc5_bytes = need;
+      }
+      slice5_tc_kernel<<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node,
+                                                                   plan->d_coef, plan->d_ip,
+                                                                   (unsigned char*)plan->d_tc5, plan->d_sinfo, n,
+                                                                   plan->d.n_sub, t_off, ab);
+      SPMC_CUDA(cudaGetLastError());
+      return SPMC_OK;
+    }
     if (rd.n_slices > 0) {
       if (plan->d.precision == SPMC_FP64)
         slice_kernel<5, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
@@ -614,15 +643,41 @@ spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& r
 
 // Give the event buffer room for `events` events plus a quarter (the batches of
 // later iterations differ a little from the one measured).
-template <typename R>
+// bytes of one event record of the plan's event sweep
+size_t event_bytes(spmc_plan_t plan) {
+  if (plan->d.dim == 5) return sizeof(Event5<float>);
+  return plan->d.precision == SPMC_FP64 ? sizeof(Event<double>) : sizeof(Event<float>);
+}
+
 spmc_status size_event_buffer(spmc_plan_t plan, unsigned long long events) {
   if (events > 0xffffffffULL)
     return fail(plan, SPMC_ERR_UNSUPPORTED, "event sweep: a batch holds 2^32 events or more; use a smaller batch");
+  const size_t eb = event_bytes(plan);
   unsigned long long cap = events + events / 4 + (1ull << 16);
   cap = std::min<unsigned long long>(cap, 0xffffffffULL);
-  if (grow(plan, &plan->d_events, &plan->events_bytes, sizeof(Event<R>) * (size_t)cap) != SPMC_OK) return SPMC_ERR_OOM;
-  plan->ev_cap = std::max<unsigned long long>(cap, plan->events_bytes / sizeof(Event<R>));
+  if (grow(plan, &plan->d_events, &plan->events_bytes, eb * (size_t)cap) != SPMC_OK) return SPMC_ERR_OOM;
+  plan->ev_cap = std::max<unsigned long long>(cap, plan->events_bytes / eb);
   plan->ev_cap = std::min<unsigned long long>(plan->ev_cap, 0xffffffffULL);
+  return SPMC_OK;
+}
+
+// The 5-D tensor-core evaluation: one block per SM (196 KB of shared memory,
+// 256 TMEM columns); the grid covers the event buffer's capacity.
+spmc_status launch_eval5_tc(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  if (dev < 64 && !attr_set[dev]) {
+    SPMC_CUDA(cudaFuncSetAttribute(eval5_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Tc5::SMEM));
+    attr_set[dev] = true;
+  }
+  const unsigned long long blocks = (plan->ev_cap + Tc5::EV_CHUNK - 1) / Tc5::EV_CHUNK;
+  if (blocks > 0x7fffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch too large for one evaluation launch");
+  eval5_tc_kernel<<<(unsigned)blocks, 128, Tc5::SMEM, stream>>>(
+      rd.d_slice_node, rd.d_tn, plan->d_ip, reinterpret_cast<const unsigned char*>(plan->d_tc5), plan->d_sinfo,
+      plan->d_starts, reinterpret_cast<const Event5<float>*>(plan->d_events), plan->d_acc, plan->d.n_space, plan->S,
+      rd.n_slices, plan->d.kappa, plan->d_total, plan->d_status, plan->d_abort);
+  SPMC_CUDA(cudaGetLastError());
   return SPMC_OK;
 }
 
@@ -713,7 +768,7 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
       unsigned long long total = 0;
       SPMC_CUDA(cudaMemcpyAsync(&total, plan->d_total, sizeof(total), cudaMemcpyDeviceToHost, stream));
       SPMC_CUDA(cudaStreamSynchronize(stream));
-      spmc_status st = size_event_buffer<R>(plan, std::max(total, 1ull));
+      spmc_status st = size_event_buffer(plan, std::max(total, 1ull));
       if (st != SPMC_OK) return st;
     }
     a.events = plan->d_events;
@@ -725,17 +780,20 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     if (timer_end(plan, stream, tf, 3) != SPMC_OK) return SPMC_ERR_CUDA;
     if (timer_begin(plan, stream, te) != SPMC_OK) return SPMC_ERR_CUDA;
     const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS;
-    if (tensor) {
+    if constexpr (D == 5) {
+      spmc_status ts = launch_eval5_tc(plan, stream, rd);
+      if (ts != SPMC_OK) return ts;
+    } else if (tensor) {
       spmc_status ts = NMAXv == 8 ? launch_eval_tc<8>(plan, stream, rd)
                        : NMAXv == 16 ? launch_eval_tc<16>(plan, stream, rd)
                        : NMAXv == 24 ? launch_eval_tc<24>(plan, stream, rd)
                                      : launch_eval_tc<32>(plan, stream, rd);
       if (ts != SPMC_OK) return ts;
-    } else if (D == 1) launch_eval<1, 32, R>(plan, stream, rd);
-    else if (NMAXv == 8) launch_eval<D == 1 ? 1 : 2, 8, R>(plan, stream, rd);
-    else if (NMAXv == 16) launch_eval<D == 1 ? 1 : 2, 16, R>(plan, stream, rd);
-    else if (NMAXv == 24) launch_eval<D == 1 ? 1 : 2, 24, R>(plan, stream, rd);
-    else launch_eval<D == 1 ? 1 : 2, 32, R>(plan, stream, rd);
+    } else if constexpr (D == 1) launch_eval<1, 32, R>(plan, stream, rd);
+    else if (NMAXv == 8) launch_eval<2, 8, R>(plan, stream, rd);
+    else if (NMAXv == 16) launch_eval<2, 16, R>(plan, stream, rd);
+    else if (NMAXv == 24) launch_eval<2, 24, R>(plan, stream, rd);
+    else launch_eval<2, 32, R>(plan, stream, rd);
     SPMC_CUDA(cudaGetLastError());
     if (timer_end(plan, stream, te, 2) != SPMC_OK) return SPMC_ERR_CUDA;
   }
@@ -748,6 +806,7 @@ spmc_status event_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, 
                         long long node_lo = 0, long long node_cnt = -1) {
   if (node_cnt < 0) node_cnt = (long long)rd.tn.size() * plan->S - node_lo;
   const bool fp64 = plan->d.precision == SPMC_FP64;
+  if (plan->d.dim == 5) return event_sweep_t<5, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
   if (plan->d.dim == 1) return fp64 ? event_sweep_t<1, double>(plan, stream, rd, interval, iteration, node_lo, node_cnt)
                                     : event_sweep_t<1, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
   return fp64 ? event_sweep_t<2, double>(plan, stream, rd, interval, iteration, node_lo, node_cnt)
@@ -774,7 +833,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   spmc_status pst = prepare_slices(plan, stream, rd);
   if (pst != SPMC_OK) return pst;
   bool fp64 = plan->d.precision == SPMC_FP64;
-  const bool events = plan->d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT && plan->d.walk_mode == 0;
+  const bool events = uses_events(plan);
   std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
   if (events && plan->timing) {
     if (!plan->ev_free.empty()) { tev = plan->ev_free.back(); plan->ev_free.pop_back(); }
@@ -806,10 +865,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   return SPMC_OK;
 }
 
-spmc_status size_events(spmc_plan_t plan, unsigned long long events) {
-  return plan->d.precision == SPMC_FP64 ? size_event_buffer<double>(plan, events)
-                                        : size_event_buffer<float>(plan, events);
-}
+spmc_status size_events(spmc_plan_t plan, unsigned long long events) { return size_event_buffer(plan, events); }
 
 // If a batch of the sequence just synchronised did not fit the event buffer,
 // grow the buffer to the largest batch seen, clear the abort word and restore
@@ -1602,7 +1658,7 @@ spmc_status spmc_autotune(spmc_plan_t plan, void* cuda_stream, int interval, dou
   const bool timing = plan->timing;
   plan->timing = false;
   float best = 1e30f;
-  if (plan->d.dim <= 2 && plan->sweep_mode != SPMC_SWEEP_COHORT) {
+  if (uses_events(plan)) {
     // event sweep: samples per batch for 2^23 .. 2^26 walks per batch
     const long long keep = plan->ev_batch;
     long long best_nb = keep;

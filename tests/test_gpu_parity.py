@@ -380,3 +380,42 @@ def test_sharded_iterations_equal_unsharded(api, precision):
         assert e_ref == e_shd
     ref.close()
     shd.close()
+
+
+@pytest.mark.parametrize("n,Mt,M", [(4, 3, 96), (8, 7, 8)])
+def test_5d_tensor_core_events_match_cohort_and_oracle(O, api, n, Mt, M):
+    """d = 5, mixed: the event sweep with the tensor-core evaluation (stage 1 of
+    the sum-factorised contraction as a tcgen05 TF32 product, 3-term split)
+    against the cohort kernel (FP32 pipe) on the same walks, and against the
+    FP64 oracle at sampled nodes.  The walks and their points are the same; eps
+    differ by FP32 / TF32-split rounding of terms whose magnitudes sum to about
+    |f_add| + |d_t u| + |Delta u| ~ 30 over a walk time <= 0.5: 2^-20 x 15 ~ 2e-5.
+    n = 8 is the 5-D workload's full geometry (8^5 nodes x 8 LGL)."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w4(M=M, K=1, n_space=n, degree=Mt)
+    wl.n_ref = 16
+    inst = wl.instances[0]
+    out = {}
+    for sweep in ("events", "cohort"):
+        plan = api.Plan.from_workload(wl, precision=1)
+        plan.set_sweep(sweep)
+        plan.begin_interval(0)
+        U0 = plan.get_nodes(0, 0).cpu().numpy()
+        p0 = plan.stats()["points"]
+        plan.iterate(0, 1)
+        out[sweep] = (plan.get_nodes(0, 0).cpu().numpy() - U0, plan.stats()["points"] - p0, U0)
+        plan.close()
+    (ee, pe, U0), (ec, pc, _) = out["events"], out["cohort"]
+    d = np.abs(ee - ec).max()
+    print(f"n={n}: max|eps_tc - eps_cohort| = {d:.3e}, max|eps| = {np.abs(ec).max():.3e}, points {pe} / {pc}")
+    assert pe == pc
+    assert d <= 2e-5, d
+    if n == 4:
+        spec = oracle_spec(O, wl, inst)
+        cu, ct = O.reconstruct(spec, Mt, 0.5, np.ascontiguousarray(U0))
+        rng = np.random.default_rng(8)
+        for _ in range(3):
+            l = int(rng.integers(1, Mt + 1))
+            j = int(rng.integers(0, n ** 5))
+            ref = O.node_eps(spec, Mt, 0.0, 0.5, cu, ct, j, l, interval=0, iteration=1)
+            assert abs(ee[l, j] - ref) <= 2e-5, (l, j, ee[l, j], ref)
