@@ -347,6 +347,7 @@ def run_ours(args):
         line["fp64_path"]["ratio_mixed_over_fp64"] = value / line["fp64_path"]["value"]
         line["time_to_1e-6"] = time_to_tol_legs(args)
         line["batch_w3"] = batch_leg(args)
+        line["w4_5d"] = w4_leg(args, peaks)
         line["cpu_baseline"] = cpu_baseline(wl)
     plan.close()
     if rank == 0:
@@ -559,6 +560,65 @@ def batch_leg(args):
     plan.close()
     return {"value": ns / (ms / 1e3), "unit": "node-samples/s", "instances": len(wl.instances), "M": wl.M,
             "sample": "interval 1 of all 256 instances (full workload size), K = 8", "ms": ms}
+
+
+def w4_leg(args, peaks, tol=1e-6):
+    """The 5-D workload (8^5 JG nodes x 8 LGL, T = 0.5 in one interval, mixed:
+    FP32 walks, tensor-core evaluation).  At M = 1024: iterations until the
+    L-inf error against the closed form is <= tol (at most 12), GPU time of the
+    iterations.  Then one iteration at the full M = 16384 for the throughput
+    (node-samples/s) and the tensor-core roofline of the evaluation kernel: 4
+    tensors x 2 x 64 x 512 = 262144 algorithmic flops per evaluation event
+    (stage 1 of the sum-factorised contraction; the split executes 3x that)."""
+    import numpy as np
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    out = {}
+    wl = W.w4(M=1024, K=12)
+    plan = Plan.from_workload(wl, precision=L.MIXED)
+    ex = W.exact_block(wl, wl.instances[0], plan.node_grid(), 0)
+    plan.begin_interval(0)
+    ms_total, errs = 0.0, []
+    while len(errs) < 12 and (not errs or errs[-1] > tol):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.iterate(0, 1)
+        b.record()
+        torch.cuda.synchronize()
+        ms_total += a.elapsed_time(b)
+        errs.append(float(np.abs(plan.get_nodes(0, 0).cpu().numpy() - ex).max()))
+    plan.close()
+    out["time_to_1e-6"] = {"reached": errs[-1] <= tol, "ms": ms_total, "iterations": len(errs),
+                           "linf_by_iteration": errs, "M": 1024}
+    wl = W.w4(M=16384, K=1)
+    plan = Plan.from_workload(wl, precision=L.MIXED)
+    plan.begin_interval(0)
+    plan.set_timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plan.iterate(0, 1)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st = plan.stats()
+    plan.close()
+    ns = node_samples_per_interval(wl, 0)
+    fpe = 4 * 2 * 64 * 512
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1400.0)
+    peak = bf16_sus * 1.1 / 2.25
+    ach = st["points"] * fpe / (st["eval_ms"] / 1e3) / 1e12 if st["eval_ms"] > 0 else None
+    out["full_M"] = {"value": ns / (ms / 1e3), "unit": "node-samples/s", "ms_per_iteration": ms, "M": wl.M,
+                     "events": st["points"], "eval_ms": st["eval_ms"], "fill_ms": st["fill_ms"],
+                     "count_ms": st["walk_ms"],
+                     "roofline_eval5_tc": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                           "frac": ach / peak if ach else None, "flops_per_event": fpe,
+                                           "peak_source": ("bf16_tflops_sustained (of measured)" if
+                                                           "bf16_tflops_sustained" in peaks else
+                                                           "fallback 1400 TFLOP/s sustained BF16 (of fallback)")
+                                           + " x nominal TF32/BF16 1.1/2.25"}}
+    return out
 
 
 def run_reference(args):
