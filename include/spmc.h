@@ -254,6 +254,18 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
 #define SPMC_SWEEP_EVENTS_ALU 2
 spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch);
 
+/* Acceleration of the residual iteration (the Remark after Algorithm 1 on
+ * Aitken-weighted Picard iteration; the paper gives no formula).
+ * SPMC_ACCEL_AITKEN: Aitken's dynamic relaxation per instance,
+ *   u_{k+1} = u_k + omega_k eps_k,  omega_1 = 1 on each interval,
+ *   omega_k = -omega_{k-1} <eps_{k-1}, eps_k - eps_{k-1}> / |eps_k - eps_{k-1}|^2,
+ * kept in [1/2, 2] (once eps is Monte Carlo noise, successive residuals are
+ * uncorrelated and the unbounded factor would halve at each step).  The sums
+ * run in a fixed order.  Not combined with the sharded iteration.
+ * SPMC_ACCEL_NONE (default): u_{k+1} = u_k + eps_k. */
+enum { SPMC_ACCEL_NONE = 0, SPMC_ACCEL_AITKEN = 1 };
+spmc_status spmc_set_acceleration(spmc_plan_t plan, int mode);
+
 /* Enable (1, the default) or disable (0) spmc_solve's capture of each interval
  * as a CUDA graph.  The caller's stream must not be capturing already. */
 spmc_status spmc_set_graphs(spmc_plan_t plan, int enable);

@@ -83,6 +83,9 @@ def lib():
             "orc_iterate": (C.c_int, [P, C.c_int, C.c_double, C.c_double, C.c_int, D, C.c_int,
                                       C.c_int, C.c_double, D, D]),
             "orc_handoff": (None, [P, C.c_int, D, D]),
+            "orc_aitken_omega": (C.c_double, [C.c_int64, D, D, C.c_double]),
+            "orc_iterate_aitken": (C.c_int, [P, C.c_int, C.c_double, C.c_double, C.c_int, D, C.c_int, C.c_int, D, D,
+                                             D]),
             "orc_solve": (None, [P, C.c_int, D, I, C.c_int, C.c_double, D, D, I]),
             "orc_solve_tangent": (None, [P, C.c_int, D, I, C.c_int, D, D, C.c_double, D, D]),
         }
@@ -284,6 +287,30 @@ def iterate(spec: Spec, interval, t0, t1, Mt, U, first_iteration=1, n_iter=1, to
     it = lib().orc_iterate(C.byref(p), interval, t0, t1, Mt, _dp(U), first_iteration, n_iter, tol,
                            _dp(mx), _dp(eps))
     return it, mx[:it], eps
+
+
+def aitken_omega(r_prev, r_cur, omega_prev):
+    a = np.ascontiguousarray(r_prev, dtype=np.float64).ravel()
+    b = np.ascontiguousarray(r_cur, dtype=np.float64).ravel()
+    return lib().orc_aitken_omega(a.size, _dp(a), _dp(b), float(omega_prev))
+
+
+class AitkenState:
+    """The previous residual and factor of an Aitken-relaxed iteration sequence."""
+    def __init__(self, spec: Spec, Mt: int):
+        self.eps_prev = np.zeros(Mt * n_nodes(spec))
+        self.omega = C.c_double(1.0)
+
+
+def iterate_aitken(spec: Spec, interval, t0, t1, Mt, U, state: AitkenState, first_iteration=1, n_iter=1):
+    """Residual iterations with Aitken relaxation, in place on U; returns max |eps| per iteration."""
+    S = n_nodes(spec)
+    assert U.shape == (Mt + 1, S) and U.dtype == np.float64 and U.flags["C_CONTIGUOUS"]
+    mx = np.zeros(n_iter)
+    p = spec.struct()
+    lib().orc_iterate_aitken(C.byref(p), interval, t0, t1, Mt, _dp(U), first_iteration, n_iter,
+                             _dp(state.eps_prev), C.byref(state.omega), _dp(mx))
+    return mx
 
 
 def handoff(spec: Spec, Mt, U):

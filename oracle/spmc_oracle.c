@@ -797,7 +797,67 @@ int orc_iterate(const orc_problem* pb, int interval, double t0, double t1, int M
   return done;
 }
 
-/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:
+/* ------------------------------------------------------------------------- */
+/* Aitken acceleration (the Remark after Algorithm 1: Aitken-weighted Picard  */
+/* iteration).  The paper gives no formula; this follows Aitken's dynamic     */
+/* relaxation of a fixed-point iteration U <- G(U) with residual r = G(U) - U */
+/* (here r = eps): U_{k+1} = U_k + omega_k r_k, omega_1 = 1 and               */
+/*   omega_k = -omega_{k-1} <r_{k-1}, r_k - r_{k-1}> / |r_k - r_{k-1}|^2,      */
+/* the secant estimate of the iteration's contraction along the last step,   */
+/* kept in [1/2, 2]: once r_k is Monte Carlo noise, successive residuals are  */
+/* uncorrelated and the unbounded factor would halve at every step.          */
+/* ------------------------------------------------------------------------- */
+double orc_aitken_omega(int64_t n, const double* r_prev, const double* r_cur, double omega_prev) {
+  double num = 0.0, den = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double dr = r_cur[i] - r_prev[i];
+    num += r_prev[i] * dr;
+    den += dr * dr;
+  }
+  if (!(den > 0.0)) return omega_prev;
+  double w = -omega_prev * num / den;
+  if (w < 0.5) w = 0.5;
+  if (w > 2.0) w = 2.0;
+  return w;
+}
+
+/* orc_iterate with Aitken relaxation.  eps_prev (Mt S values, rows l >= 1) and
+ * *omega carry the previous iteration's residual and factor between calls;
+ * first_iteration == 1 starts a fresh sequence (omega = 1).  max_eps[k] is
+ * the largest |eps| (the residual), not the applied step. */
+int orc_iterate_aitken(const orc_problem* pb, int interval, double t0, double t1, int Mt, double* U,
+                       int first_iteration, int n_iter, double* eps_prev, double* omega, double* max_eps) {
+  int d = pb->dim, n = pb->n_space;
+  int64_t S = ipow(n, d);
+  double h = t1 - t0;
+  int64_t nn = S * Mt;
+  double* cu = (double*)malloc(sizeof(double) * S * (Mt + 1));
+  double* ct = (double*)malloc(sizeof(double) * S * (Mt + 1));
+  double* eps = (double*)malloc(sizeof(double) * nn);
+  for (int k = 0; k < n_iter; ++k) {
+    int it = first_iteration + k;
+    orc_reconstruct(pb, Mt, h, U, cu, ct);
+    orc_interval_ctx ic = {Mt, t0, h, cu, ct, interval, it};
+#ifdef _OPENMP
+    int nt = pb->n_threads > 0 ? pb->n_threads : 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int64_t a = 0; a < nn; ++a) eps[a] = orc_node_eps(pb, &ic, a % S, 1 + (int)(a / S));
+    double w = (it == 1) ? 1.0 : orc_aitken_omega(nn, eps_prev, eps, *omega);
+    double mx = 0.0;
+    for (int64_t a = 0; a < nn; ++a) {
+      U[S + a] += w * eps[a];
+      if (fabs(eps[a]) > mx) mx = fabs(eps[a]);
+      eps_prev[a] = eps[a];
+    }
+    *omega = w;
+    if (max_eps) max_eps[k] = mx;
+  }
+  free(cu); free(ct); free(eps);
+  return n_iter;
+}
+
+/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:
  * u*(x_j, t_n) = sum_q sum_k b_qk U[k][j] L_q(1)  (Algorithm 1, Step 4). */
 void orc_handoff(const orc_problem* pb, int Mt, const double* U, double* row) {
   int64_t S = ipow(pb->n_space, pb->dim);

@@ -22,6 +22,7 @@ EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
 U0_NODAL, U0_PHI_COEF = 0, 1
 SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT, SPMC_SWEEP_EVENTS_ALU = 0, 1, 2
 WALK_BALLS, WALK_FIXED = 0, 1
+ACCEL_NONE, ACCEL_AITKEN = 0, 1
 
 
 class PlanDesc(C.Structure):
@@ -66,6 +67,7 @@ _SIGNATURES = {
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spmc_set_timing": (C.c_int, [_PLAN, C.c_int]),
     "spmc_set_graphs": (C.c_int, [_PLAN, C.c_int]),
+    "spmc_set_acceleration": (C.c_int, [_PLAN, C.c_int]),
     "spmc_round_nodes": (C.c_int, [_PLAN, C.c_int, C.POINTER(C.c_longlong)]),
     "spmc_iterate_shard": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "spmc_apply_eps": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_double)]),

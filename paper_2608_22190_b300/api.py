@@ -219,6 +219,11 @@ class Plan:
              "events_alu": L.SPMC_SWEEP_EVENTS_ALU}[mode]
         L.check(L.lib.spmc_set_sweep(self._h, m, int(batch)), self._h)
 
+    def set_acceleration(self, mode: str = "none"):
+        """"aitken": Aitken's dynamic relaxation of the update (factor in [1/2, 2]); "none" (default)."""
+        L.check(L.lib.spmc_set_acceleration(self._h, {"none": L.ACCEL_NONE, "aitken": L.ACCEL_AITKEN}[mode]),
+                self._h)
+
     def set_graphs(self, enable: bool):
         """solve(): run each interval after the first as one captured CUDA graph (default on)."""
         L.check(L.lib.spmc_set_graphs(self._h, 1 if enable else 0), self._h)

@@ -512,4 +512,194 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
   }
 }
 
+// The adjoint of one iteration's sweep on the event pipeline (the forward
+// iteration's own events: same walks, weights and points).  One block per
+// slice.  Per event p at node i: cw = lambda_i w_p / M, u* from the slice's C,
+// alpha = cw s g'(u*), beta = cw; the slice's three tensors
+//   T_alpha = sum alpha Phi(Y),  T_beta = sum beta Phi(Y),  T_psi = sum beta Psi(Y)
+// (Phi = prod phi, Psi = sum over one axis of psi with phi on the others) are
+// outer-product sums over the events: per chunk of 128 events each event writes
+//   a = [alpha ox oy P(x) | beta ox oy P(x) | beta oy lam P(x) | beta ox P(x)],
+//   b = [P(y) | lam P(y)]
+// to shared memory (d = 1: [alpha o P | beta o P | beta lam P]), and each thread
+// accumulates its share of the 3 n^d outputs over the chunk in R, then in FP64
+// across chunks; the slice's sums are added to gT (FP64) at the end, and the
+// derivative in the reaction scale, sum cw (g(u*) - g(u_ex)), to gds.
+template <int D, int NMAX, typename R>
+__global__ void __launch_bounds__(256) adj_events_kernel(const long long* __restrict__ slice_node,
+                                                         const TimeNode* __restrict__ tn,
+                                                         const InstanceParams* __restrict__ ipt,
+                                                         const void* __restrict__ slices_v,
+                                                         const SliceInfo* __restrict__ sinfo,
+                                                         const unsigned int* __restrict__ starts,
+                                                         const void* __restrict__ events_v,
+                                                         const double* __restrict__ lambda, double* __restrict__ gT,
+                                                         double* __restrict__ gds, int n, int S, long long sl_stride,
+                                                         long long M, const unsigned long long* __restrict__ n_events_p,
+                                                         const int* __restrict__ abort) {
+  constexpr int CH = 128;                       // events per chunk
+  constexpr int NA = (D == 2) ? 4 * NMAX : 3 * NMAX, NB = (D == 2) ? 2 * NMAX : 1;
+  constexpr int NOUT = (D == 2) ? 3 * NMAX * NMAX : 3 * NMAX;
+  constexpr int KO = (NOUT + 255) / 256;        // outputs per thread
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (*abort) return;
+  const unsigned long long n_events = *n_events_p;
+  R* sC = reinterpret_cast<R*>(smraw);                        // the slice's C (sl_stride entries)
+  R* sa = sC + ((sl_stride + 3) / 4) * 4;                     // [CH][NA]
+  R* sb = sa + CH * NA;                                       // [CH][NB]
+  __shared__ double dred[8];
+  const long long sidx = blockIdx.x;
+  const unsigned int e0 = starts[sidx * S];
+  const unsigned long long e1 = (sidx + 1 < (long long)gridDim.x) ? starts[(sidx + 1) * S] : n_events;
+  if ((unsigned long long)e0 >= e1) return;
+  const R* src = reinterpret_cast<const R*>(slices_v) + sidx * sl_stride;
+  for (int i = threadIdx.x; i < (int)sl_stride; i += blockDim.x) sC[i] = src[i];
+  const long long ti = slice_node[sidx];
+  const TimeNode node = tn[ti];
+  const InstanceParams ip = ipt[node.inst];
+  const SliceInfo si = sinfo[sidx];
+  const Event<R>* ev = reinterpret_cast<const Event<R>*>(events_v);
+  const double invM = 1.0 / (double)M;
+  double acc[KO];
+#pragma unroll
+  for (int k = 0; k < KO; ++k) acc[k] = 0.0;
+  double ds = 0.0;
+  __syncthreads();
+  for (unsigned long long base = e0; base < e1; base += CH) {
+    if (threadIdx.x < CH) {
+      const unsigned long long i = base + threadIdx.x;
+      R* a = sa + threadIdx.x * NA;
+      R* b = sb + threadIdx.x * NB;
+      if (i < e1) {
+        const Event<R> e = ev[i];
+        const int j = (int)(e.key - (unsigned int)(sidx * S));
+        const double cw = lambda[node.u_off + (long long)node.ell * S + j] * (double)e.w * invM;
+        const R x = e.y[0], ox = R(1) - x * x;
+        R Px[NMAX];
+        {
+          R pm2 = R(1), pm1 = R(2) * x;
+#pragma unroll
+          for (int p = 0; p < NMAX; ++p) {
+            R v;
+            if (p == 0) v = R(1);
+            else if (p == 1) v = R(2) * x;
+            else { v = jac_ra<R>(p) * x * pm1 - jac_rb<R>(p) * pm2; pm2 = pm1; pm1 = v; }
+            Px[p] = p < n ? v : R(0);
+          }
+        }
+        R u;
+        R Py[NMAX], oy = R(1);
+        if (D == 1) {
+          R t = R(0);
+#pragma unroll
+          for (int p = 0; p < NMAX; ++p) t += sC[p] * Px[p];
+          u = ox * t;
+        } else {
+          const R y = e.y[1];
+          oy = R(1) - y * y;
+          R pm2 = R(1), pm1 = R(2) * y;
+#pragma unroll
+          for (int p = 0; p < NMAX; ++p) {
+            R v;
+            if (p == 0) v = R(1);
+            else if (p == 1) v = R(2) * y;
+            else { v = jac_ra<R>(p) * y * pm1 - jac_rb<R>(p) * pm2; pm2 = pm1; pm1 = v; }
+            Py[p] = p < n ? v : R(0);
+          }
+          R t = R(0);
+          for (int p1 = 0; p1 < n; ++p1) {
+            R r2 = R(0);
+#pragma unroll
+            for (int p2 = 0; p2 < NMAX; ++p2) r2 += sC[p1 * NMAX + p2] * Py[p2];
+            t += Px[p1] * r2;
+          }
+          u = ox * oy * t;
+        }
+        double g, dg;
+        reaction_g(ip, (double)u, &g, &dg);
+        double gex = 0.0;
+        if (ip.ex_kind != 0) {
+          double prod = 1.0;
+          for (int d = 0; d < D; ++d) {
+            const double yd = (double)e.y[d];
+            if (ip.ex_kind == 1) prod *= sinpi(yd);
+            else if (ip.ex_kind == 2) prod *= cospi(0.5 * yd);
+            else prod *= (1.0 - yd * yd) * (1.0 + yd);
+          }
+          double dgx;
+          reaction_g(ip, si.Tt * prod, &gex, &dgx);
+        }
+        ds += cw * (g - gex);
+        const R al = (R)(cw * ip.f_scale * dg), be = (R)cw;
+#pragma unroll
+        for (int p = 0; p < NMAX; ++p) {
+          if (D == 2) {
+            a[p] = al * ox * oy * Px[p];
+            a[NMAX + p] = be * ox * oy * Px[p];
+            a[2 * NMAX + p] = be * oy * jac_lam<R>(p) * Px[p];
+            a[3 * NMAX + p] = be * ox * Px[p];
+            b[p] = Py[p];
+            b[NMAX + p] = jac_lam<R>(p) * Py[p];
+          } else {
+            a[p] = al * ox * Px[p];
+            a[NMAX + p] = be * ox * Px[p];
+            a[2 * NMAX + p] = be * jac_lam<R>(p) * Px[p];
+          }
+        }
+      } else {
+        for (int p = 0; p < NA; ++p) a[p] = R(0);
+        for (int p = 0; p < NB; ++p) b[p] = R(0);
+      }
+    }
+    __syncthreads();
+    const int ne = (int)min((unsigned long long)CH, e1 - base);
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+      const int o = threadIdx.x + 256 * k;
+      if (o < NOUT) {
+        R s = R(0);
+        if (D == 2) {
+          const int c = o / (NMAX * NMAX), rem = o - c * NMAX * NMAX, p1 = rem / NMAX, p2 = rem - p1 * NMAX;
+          if (c < 2) {
+            for (int e = 0; e < ne; ++e) s += sa[e * NA + c * NMAX + p1] * sb[e * NB + p2];
+          } else {
+            for (int e = 0; e < ne; ++e)
+              s += sa[e * NA + 2 * NMAX + p1] * sb[e * NB + p2] + sa[e * NA + 3 * NMAX + p1] * sb[e * NB + NMAX + p2];
+          }
+        } else {
+          for (int e = 0; e < ne; ++e) s += sa[e * NA + o];
+        }
+        acc[k] += (double)s;
+      }
+    }
+    __syncthreads();
+  }
+  // the slice's sums, in coefficient order (x_1 fastest): gT[s][c][p1 + n p2]
+#pragma unroll
+  for (int k = 0; k < KO; ++k) {
+    const int o = threadIdx.x + 256 * k;
+    if (o < NOUT && acc[k] != 0.0) {
+      long long dst;
+      if (D == 2) {
+        const int c = o / (NMAX * NMAX), rem = o - c * NMAX * NMAX, p1 = rem / NMAX, p2 = rem - p1 * NMAX;
+        if (p1 >= n || p2 >= n) continue;
+        dst = (long long)c * S + p1 + (long long)n * p2;
+      } else {
+        const int c = o / NMAX, p = o - c * NMAX;
+        if (p >= n) continue;
+        dst = (long long)c * S + p;
+      }
+      atomicAdd(&gT[sidx * 3 * S + dst], acc[k]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
+  if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = ds;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += dred[w];
+    if (t != 0.0) atomicAdd(&gds[node.inst], t);
+  }
+}
+
 }  // namespace spmc

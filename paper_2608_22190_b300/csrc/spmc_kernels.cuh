@@ -668,6 +668,78 @@ __global__ void apply_eps_kernel(const TimeNode* __restrict__ tn, const double* 
   atomicMax(&max_eps_bits[node.inst], (unsigned long long)__double_as_longlong(fabs(e)));
 }
 
+// eps of every pair from the cohort kernel's chunk sums (Neumaier, chunk order).
+__global__ void eps_from_partial_kernel(const double* __restrict__ partial, double* __restrict__ eps,
+                                        long long n_pairs, int n_chunks, double inv_M, int* status) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pairs) return;
+  const double* pp = partial + i * n_chunks;
+  double sum = 0.0, comp = 0.0;
+  for (int c = 0; c < n_chunks; ++c) {
+    const double x = pp[c], t = sum + x;
+    if (fabs(sum) >= fabs(x)) comp += (sum - t) + x; else comp += (x - t) + sum;
+    sum = t;
+  }
+  const double e = (sum + comp) * inv_M;
+  if (!isfinite(e)) atomicOr(status, 1);
+  eps[i] = e;
+}
+
+// Aitken relaxation (the Remark after Algorithm 1), one block per active
+// instance over its pairs [first[b], first[b+1]) x S: omega = -omega_prev
+// <r_prev, r - r_prev> / |r - r_prev|^2 kept in [1/2, 2] (omega = 1 on an
+// interval's first iteration), then u += omega r, r_prev = r.  The dot
+// products are summed in a fixed order (per-thread strided sums, then a
+// fixed tree), so the factor does not depend on scheduling.
+__global__ void aitken_apply_kernel(const InstInterval* __restrict__ ii, const TimeNode* __restrict__ tn,
+                                    const long long* __restrict__ first_tn, const double* __restrict__ eps,
+                                    double* __restrict__ eps_prev, double* __restrict__ omega, double* __restrict__ U,
+                                    unsigned long long* __restrict__ max_eps_bits, int S, int first_iteration,
+                                    const int* __restrict__ abort) {
+  __shared__ double s_num[256], s_den[256];
+  __shared__ double s_w;
+  if (abort && *abort) return;
+  const int b = blockIdx.x;
+  const long long p0 = first_tn[b] * S, p1 = first_tn[b + 1] * S;
+  const int inst = ii[b].inst;
+  double num = 0.0, den = 0.0;
+  if (!first_iteration)
+    for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const double dr = eps[p] - eps_prev[p];
+      num += eps_prev[p] * dr;
+      den += dr * dr;
+    }
+  s_num[threadIdx.x] = num;
+  s_den[threadIdx.x] = den;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { s_num[threadIdx.x] += s_num[threadIdx.x + o]; s_den[threadIdx.x] += s_den[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double w = 1.0;
+    if (!first_iteration) {
+      w = omega[inst];
+      if (s_den[0] > 0.0) w = fmin(fmax(-w * s_num[0] / s_den[0], 0.5), 2.0);
+    }
+    omega[inst] = w;
+    s_w = w;
+  }
+  __syncthreads();
+  const double w = s_w;
+  double mx = 0.0;
+  for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const long long ti = p / S;
+    const int j = (int)(p - ti * S);
+    const TimeNode node = tn[ti];
+    const double e = eps[p];
+    U[node.u_off + (long long)node.ell * S + j] += w * e;
+    eps_prev[p] = e;
+    mx = fmax(mx, fabs(e));
+  }
+  atomicMax(&max_eps_bits[inst], (unsigned long long)__double_as_longlong(mx));
+}
+
 // ----------------------------------------------------------------- Step 4 and first iterate
 // row 0 of interval 0 from u0; every other row equal to row 0.
 __global__ void init_first_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ u0,

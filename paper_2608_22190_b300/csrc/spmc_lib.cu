@@ -45,6 +45,7 @@ struct Round {
   InstInterval* d_ii = nullptr;
   InstInterval* d_ii_of_node = nullptr;
   long long* d_slice_node = nullptr;
+  long long* d_first = nullptr;           // per active instance: its first time node (and the end)
   long long coef_total = 0;
   int iteration = 0;                      // iterations run so far on this interval
 };
@@ -79,6 +80,9 @@ struct spmc_plan_s {
   std::map<void*, size_t> allocs;    // device memory the plan holds
   long long ws_bytes = 0;
   bool use_graphs = true;            // spmc_solve: each interval as one captured CUDA graph
+  int accel = 0;                     // 1: Aitken relaxation of the update
+  double *d_eps_cur = nullptr, *d_eps_prev = nullptr, *d_omega = nullptr;
+  long long eps_cap = 0;
   void* d_tc5 = nullptr;             // d = 5 mixed event sweep: slices in the tensor-core layout
   size_t tc5_bytes = 0;
   cudaStream_t cap_stream = nullptr; // the plan's own stream for capturing (any caller stream may launch)
@@ -242,7 +246,10 @@ spmc_status build(spmc_plan_t plan) {
   // rounds
   int R = 0;
   for (int i = 0; i < B; ++i) R = std::max(R, plan->probs[i].n_int);
-  for (auto& r : plan->rounds) { pfree(plan, r.d_tn); pfree(plan, r.d_ii); pfree(plan, r.d_ii_of_node); pfree(plan, r.d_slice_node); }
+  for (auto& r : plan->rounds) {
+    pfree(plan, r.d_tn); pfree(plan, r.d_ii); pfree(plan, r.d_ii_of_node); pfree(plan, r.d_slice_node);
+    pfree(plan, r.d_first);
+  }
   plan->rounds.assign(R, Round());
   long long slice_cap = 0, partial_cap = 0, coef_cap = 0;
   const int n_chunks = (int)((d.M + plan->chunk - 1) / plan->chunk);
@@ -285,6 +292,9 @@ spmc_status build(spmc_plan_t plan) {
     if ((st = upload(plan, &rd.d_ii, rd.ii)) != SPMC_OK) return st;
     if ((st = upload(plan, &rd.d_ii_of_node, rd.ii_of_node)) != SPMC_OK) return st;
     if ((st = upload(plan, &rd.d_slice_node, rd.slice_node)) != SPMC_OK) return st;
+    std::vector<long long> first(rd.ii.size() + 1, 0);
+    for (size_t a = 0; a < rd.ii.size(); ++a) first[a + 1] = first[a] + rd.ii[a].Mt;   // time nodes l = 1..M_n
+    if ((st = upload(plan, &rd.d_first, first)) != SPMC_OK) return st;
   }
   // workspace
   pfree(plan, plan->d_U); pfree(plan, plan->d_coef); pfree(plan, plan->d_slices); pfree(plan, plan->d_sinfo);
@@ -686,9 +696,24 @@ spmc_status launch_eval5_tc(spmc_plan_t plan, cudaStream_t stream, const Round& 
 // (the plan's first batch is measured here, once) and the scan checks every
 // batch's total against it on the device (see the abort word in
 // spmc_events.cuh).
+// The adjoint evaluation of one batch's events (spmc_grad): gT, gds.
+template <int D, int NMAX, typename R>
+spmc_status launch_adj_eval(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
+  constexpr int NA = (D == 2) ? 4 * NMAX : 3 * NMAX, NB = (D == 2) ? 2 * NMAX : 1;
+  const size_t smem = sizeof(R) * ((((size_t)plan->sl_stride + 3) / 4) * 4 + 128 * (size_t)(NA + NB));
+  SPMC_CUDA(cudaFuncSetAttribute(adj_events_kernel<D, NMAX, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  adj_events_kernel<D, NMAX, R><<<(unsigned)rd.n_slices, 256, smem, stream>>>(
+      rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
+      plan->d_lambda, plan->d_gT, plan->d_gds, plan->d.n_space, plan->S, plan->sl_stride, plan->d.M, plan->d_total,
+      plan->d_abort);
+  SPMC_CUDA(cudaGetLastError());
+  return SPMC_OK;
+}
+
 template <int D, typename R>
 spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration,
-                          long long node_lo, long long node_cnt) {
+                          long long node_lo, long long node_cnt, bool adjoint = false) {
   const spmc_plan_desc& d = plan->d;
   const int S = plan->S;
   const long long n_tn = (long long)rd.tn.size();
@@ -780,7 +805,16 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     if (timer_end(plan, stream, tf, 3) != SPMC_OK) return SPMC_ERR_CUDA;
     if (timer_begin(plan, stream, te) != SPMC_OK) return SPMC_ERR_CUDA;
     const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS;
-    if constexpr (D == 5) {
+    if (adjoint) {
+      if constexpr (D <= 2) {
+        spmc_status as = D == 1 ? launch_adj_eval<1, 32, R>(plan, stream, rd)
+                         : NMAXv == 8 ? launch_adj_eval<2, 8, R>(plan, stream, rd)
+                         : NMAXv == 16 ? launch_adj_eval<2, 16, R>(plan, stream, rd)
+                         : NMAXv == 24 ? launch_adj_eval<2, 24, R>(plan, stream, rd)
+                                       : launch_adj_eval<2, 32, R>(plan, stream, rd);
+        if (as != SPMC_OK) return as;
+      }
+    } else if constexpr (D == 5) {
       spmc_status ts = launch_eval5_tc(plan, stream, rd);
       if (ts != SPMC_OK) return ts;
     } else if (tensor) {
@@ -803,14 +837,15 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
 // The event sweep over the (time node, spatial node) pairs ti S + j in
 // [node_lo, node_lo + node_cnt) of round rd (node_cnt < 0: all of them).
 spmc_status event_sweep(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration,
-                        long long node_lo = 0, long long node_cnt = -1) {
+                        long long node_lo = 0, long long node_cnt = -1, bool adjoint = false) {
   if (node_cnt < 0) node_cnt = (long long)rd.tn.size() * plan->S - node_lo;
   const bool fp64 = plan->d.precision == SPMC_FP64;
-  if (plan->d.dim == 5) return event_sweep_t<5, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
-  if (plan->d.dim == 1) return fp64 ? event_sweep_t<1, double>(plan, stream, rd, interval, iteration, node_lo, node_cnt)
-                                    : event_sweep_t<1, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
-  return fp64 ? event_sweep_t<2, double>(plan, stream, rd, interval, iteration, node_lo, node_cnt)
-              : event_sweep_t<2, float>(plan, stream, rd, interval, iteration, node_lo, node_cnt);
+  const long long a = node_lo, c = node_cnt;
+  if (plan->d.dim == 5) return event_sweep_t<5, float>(plan, stream, rd, interval, iteration, a, c, adjoint);
+  if (plan->d.dim == 1) return fp64 ? event_sweep_t<1, double>(plan, stream, rd, interval, iteration, a, c, adjoint)
+                                    : event_sweep_t<1, float>(plan, stream, rd, interval, iteration, a, c, adjoint);
+  return fp64 ? event_sweep_t<2, double>(plan, stream, rd, interval, iteration, a, c, adjoint)
+              : event_sweep_t<2, float>(plan, stream, rd, interval, iteration, a, c, adjoint);
 }
 
 // Copy the point / capped counters aside at the start of an iteration (unless
@@ -851,7 +886,30 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_maxeps, 0, sizeof(unsigned long long) * plan->d.batch, stream));
   long long nn = (long long)rd.tn.size() * S;
-  if (nn > 0) {
+  if (nn > 0 && plan->accel) {
+    // Aitken relaxation: eps of every pair, then one block per instance
+    if (plan->eps_cap < nn) {
+      pfree(plan, plan->d_eps_cur); pfree(plan, plan->d_eps_prev);
+      plan->d_eps_cur = plan->d_eps_prev = nullptr; plan->eps_cap = 0;
+      SPMC_CUDA(pmalloc(plan, (void**)&plan->d_eps_cur, sizeof(double) * nn));
+      SPMC_CUDA(pmalloc(plan, (void**)&plan->d_eps_prev, sizeof(double) * nn));
+      plan->eps_cap = nn;
+    }
+    if (!plan->d_omega) SPMC_CUDA(pmalloc(plan, (void**)&plan->d_omega, sizeof(double) * plan->d.batch));
+    if (events)
+      eps_out_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(plan->d_acc, plan->d_eps_cur, 0, nn,
+                                                                       1.0 / (double)plan->d.M, plan->d_status,
+                                                                       plan->d_abort);
+    else
+      eps_from_partial_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
+          plan->d_partial, plan->d_eps_cur, nn, (int)((plan->d.M + plan->chunk - 1) / plan->chunk),
+          1.0 / (double)plan->d.M, plan->d_status);
+    aitken_apply_kernel<<<(unsigned)rd.ii.size(), 256, 0, stream>>>(rd.d_ii, rd.d_tn, rd.d_first, plan->d_eps_cur,
+                                                                    plan->d_eps_prev, plan->d_omega, plan->d_U,
+                                                                    plan->d_maxeps, S, iteration == 1 ? 1 : 0,
+                                                                    plan->d_abort);
+    SPMC_CUDA(cudaGetLastError());
+  } else if (nn > 0) {
     if (events)
       update_fixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
           rd.d_tn, plan->d_acc, plan->d_U, nullptr, plan->d_maxeps, plan->d_status, nn, S, 1.0 / (double)plan->d.M,
@@ -1497,6 +1555,7 @@ spmc_status spmc_apply_eps(spmc_plan_t plan, void* cuda_stream, int interval, co
   if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "call spmc_begin_interval first");
   if (interval < 0 || interval >= (int)plan->rounds.size() || !eps_pairs)
     return fail(plan, SPMC_ERR_INVALID, "bad interval or input");
+  if (plan->accel) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_apply_eps: Aitken relaxation is not sharded");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   Round& rd = plan->rounds[interval];
   rd.iteration += 1;
@@ -1596,7 +1655,18 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
       round_copy_kernel<<<nb, 256, 0, s>>>(rd.d_ii, plan->d_U, plan->d_iter + (long long)(k - 1) * blk, S, 0);
       if ((st = prepare_slices(plan, s, rd)) != SPMC_OK) break;
       SPMC_CUDA(cudaMemsetAsync(plan->d_gT, 0, sizeof(double) * 3 * S * std::max(1LL, rd.n_slices), s));
-      st = fp64 ? dispatch_adjoint<double>(plan, s, rd, r, k) : dispatch_adjoint<float>(plan, s, rd, r, k);
+      if (uses_events(plan)) {
+        // the iteration's own events (same walks), adjoint evaluation per slice.  The
+        // forward run of this iteration sized the event buffer for these very
+        // batches, so none can overflow; if one did, the gradient is refused.
+        st = event_sweep(plan, s, rd, r, k, 0, -1, true);
+        if (st != SPMC_OK) break;
+        int failed = 0;
+        if ((st = recover_abort(plan, s, &failed)) != SPMC_OK) break;
+        if (failed) { st = fail(plan, SPMC_ERR_CUDA, "adjoint event sweep: a batch outgrew the event buffer"); break; }
+      } else {
+        st = fp64 ? dispatch_adjoint<double>(plan, s, rd, r, k) : dispatch_adjoint<float>(plan, s, rd, r, k);
+      }
       if (st != SPMC_OK) break;
       adj_time_kernel<<<nb, 256, 0, s>>>(rd.d_ii, rd.d_tn, plan->d_first_tn[r], plan->d_sinfo, plan->d_gT,
                                          plan->d_lam, S, d.n_sub);
@@ -1719,6 +1789,13 @@ spmc_status spmc_set_sweep(spmc_plan_t plan, int mode, long long batch) {
     return fail(plan, SPMC_ERR_INVALID, "spmc_set_sweep: unknown mode");
   plan->sweep_mode = mode;
   plan->ev_batch = batch > 0 ? batch : 0;
+  return SPMC_OK;
+}
+
+spmc_status spmc_set_acceleration(spmc_plan_t plan, int mode) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (mode != SPMC_ACCEL_NONE && mode != SPMC_ACCEL_AITKEN) return fail(plan, SPMC_ERR_INVALID, "unknown acceleration");
+  plan->accel = mode;
   return SPMC_OK;
 }
 

@@ -121,3 +121,29 @@ def test_autograd_function(api):
     assert torch.allclose(s.grad, gs.cpu(), rtol=1e-12, atol=1e-14)
     assert torch.allclose(c.grad, gc.view(-1, c.shape[1], c.shape[1]).transpose(1, 2).cpu(), rtol=1e-12, atol=1e-14)
     plan.close()
+
+
+def test_event_adjoint_matches_cohort_adjoint(api):
+    """The adjoint sweep on the event pipeline (the iteration's own events,
+    outer-product sums per slice) and on the cohort kernel (per-evaluation
+    scatters) compute the same gradient: FP64, to rounding of their different
+    summation orders."""
+    wl = _workload()
+    scales = np.array([i.f_scale for i in wl.instances])
+    coefs = np.array([i.u0_coef for i in wl.instances])
+    out = {}
+    for sweep in ("events", "cohort"):
+        from paper_2608_22190_b300 import _lib as L
+        plan = api.Plan.from_workload(wl, precision=0)
+        plan.set_sweep(sweep)
+        for b, inst in enumerate(wl.instances):
+            plan.set_problem(b, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, float(scales[b]),
+                             inst.ex_kind, inst.ex_beta, np.ascontiguousarray(coefs[b].T).ravel(), L.U0_PHI_COEF,
+                             coefs[b].shape[0])
+        flat = plan.solve()
+        _, z = _loss_and_z(plan, flat)
+        gs, gc = plan.grad(z, n_coef=coefs.shape[1])
+        out[sweep] = (gs.cpu().numpy(), gc.cpu().numpy())
+        plan.close()
+    for a, b in zip(out["events"], out["cohort"]):
+        assert np.abs(a - b).max() <= 1e-10 * max(1.0, np.abs(b).max()), np.abs(a - b).max()

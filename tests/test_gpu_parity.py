@@ -419,3 +419,29 @@ def test_5d_tensor_core_events_match_cohort_and_oracle(O, api, n, Mt, M):
             j = int(rng.integers(0, n ** 5))
             ref = O.node_eps(spec, Mt, 0.0, 0.5, cu, ct, j, l, interval=0, iteration=1)
             assert abs(ee[l, j] - ref) <= 2e-5, (l, j, ee[l, j], ref)
+
+
+@pytest.mark.parametrize("dim,sweep", [(1, "events"), (1, "cohort"), (2, "events")])
+def test_fp64_aitken_stepwise(O, api, dim, sweep):
+    """Aitken relaxation (u += omega eps, the factor from the last two residuals,
+    per instance, in [1/2, 2]): four iterations in FP64 against the oracle's
+    relaxed iteration on the same streams."""
+    from paper_2608_22190_b300 import workloads as W
+    wl = W.w1(M=400, K=4, n_space=6, degree=5) if dim == 1 else W.w2(M=300, K=4, n_space=5, degree=3,
+                                                                        n_intervals=1, h=0.5)
+    wl.n_ref = 12
+    inst = wl.instances[0]
+    Mt = int(inst.degrees[0])
+    plan = api.Plan.from_workload(wl, precision=0)
+    plan.set_sweep(sweep)
+    plan.set_acceleration("aitken")
+    spec = oracle_spec(O, wl, inst)
+    U = np.tile(oracle_u0(O, wl, inst, spec), (Mt + 1, 1)).copy()
+    st = O.AitkenState(spec, Mt)
+    plan.begin_interval(0)
+    for k in range(4):
+        plan.iterate(0, 1)
+        O.iterate_aitken(spec, 0, inst.t_breaks[0], inst.t_breaks[1], Mt, U, st, k + 1, 1)
+        g = plan.get_nodes(0, 0).cpu().numpy()
+        assert np.all(np.abs(g - U) <= parity_tol(U)), (k, np.abs(g - U).max())
+    plan.close()

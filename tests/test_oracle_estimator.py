@@ -269,3 +269,44 @@ def test_manufactured_source_against_finite_differences(O, dim, kind, f_kind, ka
         ref = dt - kappa * lap - fr(u)
         assert abs(O.exact(sp, x, t) - u) < 1e-14
         assert abs(O.source(sp, x, t) - ref) < 2e-5 * (1.0 + abs(ref)), (O.source(sp, x, t), ref)
+
+
+# ----------------------------------------------------------------- Aitken acceleration
+@pytest.mark.parametrize("a", [-0.8, -0.3, 0.0, 0.4])
+def test_aitken_factor_is_exact_for_a_linear_map(O, a):
+    """For the residuals of a linear fixed-point map with one eigenvalue a,
+    r_2 = a r_1 after a plain step, Aitken's factor is 1 / (1 - a), which puts the
+    next iterate exactly on the fixed point.  Catches: the opposite sign, r_k in
+    place of r_{k-1} in the numerator (a / (a - 1)), a missing omega_{k-1}."""
+    rng = np.random.default_rng(5)
+    r1 = rng.standard_normal(37)
+    assert abs(O.aitken_omega(r1, a * r1, 1.0) - 1.0 / (1.0 - a)) < 1e-14
+    assert abs(O.aitken_omega(r1, a * r1, 0.7) - min(max(0.7 / (1.0 - a), 0.5), 2.0)) < 1e-14
+
+
+def test_aitken_factor_is_kept_in_range(O):
+    """Outside [1/2, 2] the factor is clamped: a = 0.9 would give 10, a = -3 would give 1/4."""
+    r1 = np.linspace(-1.0, 2.0, 11)
+    assert O.aitken_omega(r1, 0.9 * r1, 1.0) == 2.0
+    assert O.aitken_omega(r1, -3.0 * r1, 1.0) == 0.5
+    assert O.aitken_omega(r1, r1, 0.8) == 0.8          # no change in the residual: keep the factor
+
+
+def test_aitken_iteration_reaches_the_closed_form(O):
+    """The relaxed iteration has the same fixed point: on the three-interval-sized
+    1-D problem it reaches the closed form as the plain iteration does, and its
+    first iteration (omega = 1) is the plain one bit for bit."""
+    spec = _manufactured_1d(O, 10, 6, 1, 80, 512, walk=0)
+    Mt, h = 6, 0.3
+    pts = O.space_nodes_grid(spec)
+    u0 = np.sin(np.pi * pts[:, 0])
+    Ua = np.tile(u0, (Mt + 1, 1)).copy()
+    Up = Ua.copy()
+    st = O.AitkenState(spec, Mt)
+    O.iterate_aitken(spec, 0, 0.0, h, Mt, Ua, st, 1, 1)
+    O.iterate(spec, 0, 0.0, h, Mt, Up, 1, 1)
+    assert np.array_equal(Ua, Up)
+    O.iterate_aitken(spec, 0, 0.0, h, Mt, Ua, st, 2, 9)
+    ex = O.exact_nodal(spec, [0.0, h], [Mt])[0]
+    assert np.abs(Ua - ex).max() < 1e-6
+    assert 0.5 <= st.omega.value <= 2.0
