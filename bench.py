@@ -37,8 +37,9 @@ def parse():
     ap.add_argument("--intervals", type=int, default=20, help="intervals of the workload (20 = full)")
     ap.add_argument("--M", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU legs")
-    ap.add_argument("--case", default=None, choices=["iterate1"],
-                    help="profiling case: build the plan and run one iteration of the first interval, untimed")
+    ap.add_argument("--case", default=None, choices=["iterate1", "iterate1_5d"],
+                    help="profiling case: build the plan and run one iteration of the first interval, untimed "
+                         "(iterate1_5d: the 5-D workload at --M samples)")
     return ap.parse_args()
 
 
@@ -191,10 +192,10 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
                                 "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if prec == L.FP64
                                 else "148 SMs x 128 FP32 lanes x 2 x sm_max_mhz"}
     # DRAM bytes per event from one ncu capture of each kernel as it is now
-    # (profiles/walk_fill_w2_fullset.md, profiles/eval_tc_w2_fullset.md: M = 1024,
-    # 1.0216e8 events), scaled by the events of one launch; traffic grows with the events
-    per_event_bytes = {"walk_fill": (0.828278 + 2.333514) * 1e9 / 1.0216e8,
-                       "eval_tc": (1.659346 + 0.003315) * 1e9 / 1.0216e8}
+    # (profiles/walk_events_w2_fullset.md, profiles/eval_tc_w2_fullset.md: M = 1024,
+    # 1.0212e8 events), scaled by the events of one launch; traffic grows with the events
+    per_event_bytes = {"walk_fill": (0.513577 + 2.027925) * 1e9 / 1.02118e8,
+                       "eval_tc": (1.660033 + 0.004008) * 1e9 / 1.02118e8}
     launches = max(1, st["eval_launches"])
     for k, v in kern.items():
         v["traffic"] = per_event_bytes[k] * points / launches if (k in per_event_bytes and wl.dim == 2) else None
@@ -348,6 +349,7 @@ def run_ours(args):
         line["time_to_1e-6"] = time_to_tol_legs(args)
         line["batch_w3"] = batch_leg(args)
         line["w4_5d"] = w4_leg(args, peaks)
+        line["w5_adjoint"] = w5_leg(args)
         line["cpu_baseline"] = cpu_baseline(wl)
     plan.close()
     if rank == 0:
@@ -421,7 +423,7 @@ def fp64_leg(args):
                        "step": "one FP64 iteration of interval 1", "l2": "flushed before the timed region"}}
 
 
-def hp_time_to_tol(wl, prec, tol, kmax):
+def hp_time_to_tol(wl, prec, tol, kmax, accel="none"):
     """Time until every node of every interval is within tol of the closed form:
     the hp solve interval by interval (hand-off, then iterations until the
     interval's L-inf error <= tol, at most kmax).  GPU time of the hand-offs and
@@ -433,6 +435,7 @@ def hp_time_to_tol(wl, prec, tol, kmax):
     from paper_2608_22190_b300.api import Plan
     inst = wl.instances[0]
     plan = Plan.from_workload(wl, precision=prec)
+    plan.set_acceleration(accel)
     grid = plan.node_grid()
     ms_total, iters, errs = 0.0, [], []
 
@@ -523,6 +526,7 @@ def time_to_tol_legs(args, tol=1e-6):
         plan.close()
     out["w2_full_mixed"] = hp_time_to_tol(W.w2(M=args.M), L.MIXED, tol, 12)
     out["w2_full_mixed_M2048"] = hp_time_to_tol(W.w2(M=2048), L.MIXED, tol, 16)
+    out["w2_full_mixed_M2048_aitken"] = hp_time_to_tol(W.w2(M=2048), L.MIXED, tol, 16, accel="aitken")
     out["w2_full_fp64"] = hp_time_to_tol(W.w2(M=2048), L.FP64, tol, 16)
     ref = fut.result()
     pool.shutdown()
@@ -530,7 +534,7 @@ def time_to_tol_legs(args, tol=1e-6):
         out[name]["linf_vs_oracle_by_iteration"] = [float(np.abs(g - r).max())
                                                      for g, r in zip(gpu_iterates[name], ref)]
     fp = out["w2_full_fp64"]
-    for name in ("w2_full_mixed", "w2_full_mixed_M2048"):
+    for name in ("w2_full_mixed", "w2_full_mixed_M2048", "w2_full_mixed_M2048_aitken"):
         if out[name]["reached"] and fp["reached"]:
             out[name]["speedup_over_fp64_M2048"] = fp["ms"] / out[name]["ms"]
     return out
@@ -621,6 +625,38 @@ def w4_leg(args, peaks, tol=1e-6):
     return out
 
 
+def w5_leg(args):
+    """The adjoint workload at its full geometry and batch (128 instances of
+    2-D Allen-Cahn, 16 x 16 JG x 12 LGL, T = 5 in 10 intervals, kappa = 0.01,
+    K = 8), mixed, at M = 64 samples per node (the full M = 16384 means about
+    1.9e13 evaluation events per forward solve, since kappa = 0.01 keeps every
+    ball full): the forward solve and the reverse-mode gradient of
+    L = 1/2 |u(T)|^2 w.r.t. the reaction scales and the 64 initial
+    coefficients of every instance, wall time of each (synchronised)."""
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    wl = W.w5(M=64)
+    plan = Plan.from_workload(wl, precision=L.MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    flat = plan.solve()
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    z = plan.final_values(flat)
+    st = plan.stats()
+    t0 = time.perf_counter()
+    gs, gc = plan.grad(z, n_coef=8)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    plan.close()
+    ns = node_samples_per_solve(wl)
+    return {"forward_s": tf, "grad_s": tb, "node_samples_per_s_forward": ns / tf, "events_forward": st["points"],
+            "graph_launches": st["graph_launches"], "M": wl.M, "instances": len(wl.instances),
+            "grad_norm": float(torch.linalg.vector_norm(gs).item())}
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, on a bounded sample of the
     same workload, on the host cores (rank 0 only)."""
@@ -650,7 +686,11 @@ def run_case(args):
     from paper_2608_22190_b300 import _lib as L
     from paper_2608_22190_b300.api import Plan
     torch.cuda.set_device(0)
-    wl = workload(args, 0)
+    if args.case == "iterate1_5d":
+        from paper_2608_22190_b300 import workloads as W
+        wl = W.w4(M=args.M, K=1)
+    else:
+        wl = workload(args, 0)
     plan = Plan.from_workload(wl, precision=L.MIXED if args.precision == "mixed" else L.FP64)
     plan.begin_interval(0)
     plan.iterate(0, 1)
