@@ -34,6 +34,7 @@ class Problem(C.Structure):
         ("f_kind", C.c_int), ("f_coef", C.c_double * 4), ("f_scale", C.c_double),
         ("ex_kind", C.c_int), ("ex_beta", C.c_double), ("n_threads", C.c_int),
         ("walk_mode", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int), ("n_sub", C.c_int),
+        ("bc_kind", C.c_int), ("estimator", C.c_int),
     ]
 
 
@@ -73,6 +74,7 @@ def lib():
             "orc_f": (C.c_double, [P, C.c_double]),
             "orc_exact": (C.c_double, [P, D, C.c_double]),
             "orc_source": (C.c_double, [P, D, C.c_double]),
+            "orc_lift": (None, [P, D, C.c_double, D, D, D]),
             "orc_reconstruct": (None, [P, C.c_int, C.c_double, D, D, D]),
             "orc_eval": (None, [P, C.c_int, D, D, D, C.c_double, D, D, D]),
             "orc_residual": (C.c_double, [P, C.c_int, C.c_double, C.c_double, D, D, D, C.c_double]),
@@ -107,7 +109,9 @@ def _ip(a: np.ndarray):
 
 
 F_POLY3, F_SIN = 0, 1
-EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
+EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS = 0, 1, 2, 3, 4, 5
+BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
+EST_RESIDUAL, EST_DIRECT = 0, 1
 TIME_LGL, TIME_RADAU_LEFT = 0, 1
 
 
@@ -132,6 +136,8 @@ class Spec:
     shell: float = 0.0           # 0: half the outermost node's distance to the boundary
     max_steps: int = 512
     n_sub: int = 4
+    bc_kind: int = 0             # 0 g = 0; 1 lifted (Gordon-Hall); 2 g at absorption (direct estimator)
+    estimator: int = 0           # 0 residual iteration; 1 direct estimator S_i (Eq. Phi_ast)
 
     def struct(self) -> Problem:
         p = Problem()
@@ -142,6 +148,7 @@ class Spec:
             p.f_coef[i] = c
         p.n_threads = self.n_threads
         p.walk_mode, p.shell, p.max_steps, p.n_sub = self.walk_mode, self.shell, self.max_steps, self.n_sub
+        p.bc_kind, p.estimator = self.bc_kind, self.estimator
         return p
 
 
@@ -249,6 +256,15 @@ def source(spec: Spec, x, t):
     x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
     p = spec.struct()
     return lib().orc_source(C.byref(p), _dp(x), float(t))
+
+
+def lift(spec: Spec, x, t):
+    """(G, d_t G, Delta G) of the Gordon-Hall lifting of the boundary data at (x, t)."""
+    x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
+    G, Gt, L = C.c_double(), C.c_double(), C.c_double()
+    p = spec.struct()
+    lib().orc_lift(C.byref(p), _dp(x), float(t), C.byref(G), C.byref(Gt), C.byref(L))
+    return G.value, Gt.value, L.value
 
 
 def walk(spec: Spec, x_start, t_node, nstar_, t0=0.0, h=1.0, Mt=0, cu=None, ct=None,

@@ -397,6 +397,11 @@ typedef struct {
   double shell;     /* inside-ball walk: absorbed once dist(X, boundary) < shell */
   int max_steps;    /* inside-ball walk: cap on the number of quadrature terms */
   int n_sub;        /* inside-ball walk: time sub-points per full step (a power of two) */
+  int bc_kind;      /* boundary data g = trace of the exact solution: 0 g = 0; 1 homogenised by the
+                       Gordon-Hall lifting G of g (the unknown is w = u - G); 2 g applied where the
+                       walk is absorbed (direct estimator only) */
+  int estimator;    /* 0: residual iteration (Eqs. ufg_ep1, varepsilon_1); 1: the direct estimator
+                       S_i of Eq. Phi_ast (Picard iteration, Eq. linearized_func) */
 } orc_problem;
 
 static int64_t ipow(int64_t b, int e) { int64_t r = 1; while (e-- > 0) r *= b; return r; }
@@ -433,7 +438,35 @@ double orc_exact(const orc_problem* pb, const double* x, double t) {
     for (int e = 0; e < d; ++e) v *= (1.0 - x[e] * x[e]) * (1.0 + x[e]);
     return (1.0 + t + t * t) * v;
   }
+  if (pb->ex_kind == 4) {
+    for (int e = 0; e < d; ++e) v *= cos(ORC_PI * (x[e] - 0.3) / 3.0);
+    return exp(-pb->ex_beta * t) * v;
+  }
+  if (pb->ex_kind == 5) {
+    for (int e = 0; e < d; ++e) v *= sin(ORC_PI * x[e]);
+    return exp(-pb->ex_beta * t) * v + 0.5 * t;
+  }
   return 0.0;
+}
+
+/* The exact solutions with non-zero boundary values, with their derivatives:
+ * u, d_t u and the second derivatives d^2 u / d x_e^2 (e < d) at (x, t).
+ *   4: u = e^{-beta t} prod cos(pi (x_e - 0.3) / 3)   (different non-zero values on opposite faces)
+ *   5: u = e^{-beta t} prod sin(pi x_e) + t / 2     (u(., 0) = 0 on the boundary, g = t / 2)  */
+static void exact_parts(const orc_problem* pb, const double* x, double t, double* u, double* ut, double* uxx) {
+  int d = pb->dim;
+  double T = exp(-pb->ex_beta * t), prod = 1.0;
+  if (pb->ex_kind == 4) {
+    for (int e = 0; e < d; ++e) prod *= cos(ORC_PI * (x[e] - 0.3) / 3.0);
+    *u = T * prod;
+    *ut = -pb->ex_beta * T * prod;
+    for (int e = 0; e < d; ++e) uxx[e] = -(ORC_PI * ORC_PI / 9.0) * T * prod;
+    return;
+  }
+  for (int e = 0; e < d; ++e) prod *= sin(ORC_PI * x[e]);
+  *u = T * prod + 0.5 * t;
+  *ut = -pb->ex_beta * T * prod + 0.5;
+  for (int e = 0; e < d; ++e) uxx[e] = -(ORC_PI * ORC_PI) * T * prod;
 }
 
 /* Source added to f so that the exact solution solves
@@ -441,6 +474,12 @@ double orc_exact(const orc_problem* pb, const double* x, double t) {
 double orc_source(const orc_problem* pb, const double* x, double t) {
   if (pb->ex_kind == 0) return 0.0;
   int d = pb->dim;
+  if (pb->ex_kind >= 4) {
+    double u, ut, uxx[ORC_MAXD], lap = 0.0;
+    exact_parts(pb, x, t, &u, &ut, uxx);
+    for (int e = 0; e < d; ++e) lap += uxx[e];
+    return ut - pb->kappa * lap - orc_f(pb, u);
+  }
   double u = orc_exact(pb, x, t);
   double dtu, mlap;
   if (pb->ex_kind == 1) { dtu = -pb->ex_beta * u; mlap = d * ORC_PI * ORC_PI * u; }
@@ -461,6 +500,43 @@ double orc_source(const orc_problem* pb, const double* x, double t) {
     mlap *= T;
   }
   return dtu + pb->kappa * mlap - orc_f(pb, u);
+}
+
+/* Homogenisation of non-zero boundary data g (the remark on non-homogeneous
+ * boundary conditions in Section 2.3): u = w + G with G a lifting of g, and
+ *   d_t w - kappa Delta w = f(w + G) + f_add - (d_t G - kappa Delta G),  w = 0 on the boundary,
+ * w(., 0) = u0 - G(., 0).  G is the Gordon-Hall transfinite interpolant of g,
+ *   G = sum over non-empty axis sets A of (-1)^(|A|+1) P_A g,
+ *   P_A g(x) = sum over s in {-1,1}^A of prod_{e in A} (1 + s_e x_e)/2  g(x with x_e = s_e, e in A),
+ * which uses g on the faces only and equals g on the boundary.  Its blending
+ * factors are linear in their own axes, so d_t G and Delta G need g_t and the
+ * second derivatives of g along the free axes of each face.  The boundary data
+ * here is the trace of the exact solution (kinds 4 and 5; zero for kinds 1-3).
+ * G, d_t G and Delta G at (x, t); zeros unless bc_kind == 1. */
+void orc_lift(const orc_problem* pb, const double* x, double t, double* G, double* Gt, double* lapG) {
+  *G = 0.0; *Gt = 0.0; *lapG = 0.0;
+  if (pb->bc_kind != 1 || pb->ex_kind < 4) return;
+  int d = pb->dim;
+  for (int A = 1; A < (1 << d); ++A) {
+    int na = 0, idx[ORC_MAXD];
+    for (int e = 0; e < d; ++e) if (A & (1 << e)) idx[na++] = e;
+    double sgn = (na % 2 == 1) ? 1.0 : -1.0;
+    for (int sbits = 0; sbits < (1 << na); ++sbits) {
+      double z[ORC_MAXD], wgt = 1.0;
+      for (int e = 0; e < d; ++e) z[e] = x[e];
+      for (int a = 0; a < na; ++a) {
+        double se = (sbits & (1 << a)) ? 1.0 : -1.0;
+        z[idx[a]] = se;
+        wgt *= 0.5 * (1.0 + se * x[idx[a]]);
+      }
+      double u, ut, uxx[ORC_MAXD], lapf = 0.0;
+      exact_parts(pb, z, t, &u, &ut, uxx);
+      for (int e = 0; e < d; ++e) if (!(A & (1 << e))) lapf += uxx[e];
+      *G += sgn * wgt * u;
+      *Gt += sgn * wgt * ut;
+      *lapG += sgn * wgt * lapf;
+    }
+  }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -544,13 +620,21 @@ void orc_eval(const orc_problem* pb, int Mt, const double* cu, const double* ct,
 }
 
 /* Residual of the error equation (Eq. ufg_ep1):
- * r = f(u*) + f_add - d_t u* + kappa Delta u*. */
+ * r = f(u*) + f_add - d_t u* + kappa Delta u*.
+ * With lifted boundary data (bc_kind 1) the equation is the one for w:
+ * r = f(u* + G) + f_add - d_t G + kappa Delta G - d_t u* + kappa Delta u*.
+ * The direct estimator (estimator 1) integrates the right-hand side of the
+ * Picard step (Eq. linearized_func) instead: r without -d_t u* + kappa Delta u*. */
 double orc_residual(const orc_problem* pb, int Mt, double t0, double h, const double* cu,
                     const double* ct, const double* x, double tau) {
   double xi = (2.0 * tau - t0 - (t0 + h)) / h;
   double u, dtu, mlap;
   orc_eval(pb, Mt, cu, ct, x, xi, &u, &dtu, &mlap);
-  return orc_f(pb, u) + orc_source(pb, x, tau) - dtu - pb->kappa * mlap;
+  double G, Gt, lapG;
+  orc_lift(pb, x, tau, &G, &Gt, &lapG);
+  double r = orc_f(pb, u + G) + orc_source(pb, x, tau) - Gt + pb->kappa * lapG;
+  if (pb->estimator == 0) r += -dtu - pb->kappa * mlap;
+  return r;
 }
 
 /* N_* for a time node at s = t_{n,l} - t_{n-1} in an interval of length h. */
@@ -570,9 +654,9 @@ typedef struct {
 
 /* The quadrature points of one walk: for term i, the point pts[i*d..], the
  * time taus[i] and the weight wts[i] (at most cap terms).  Returns L. */
-int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node_lin, uint32_t sample,
-                    const double* x_start, double t_node, int nstar, double* pts, double* taus, double* wts,
-                    int cap, double* x_end) {
+int orc_walk_points_end(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node_lin, uint32_t sample,
+                        const double* x_start, double t_node, int nstar, double* pts, double* taus, double* wts,
+                        int cap, double* x_end, int* end_kind, double* t_end) {
   int d = pb->dim;
   orc_stream st;
   stream_init(&st, pb->seed, sample, node_lin, pb->instance, ic->interval, ic->iteration);
@@ -632,13 +716,22 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
   }
   int64_t k = 0;
   double f = 0.0;
+  int ended = 0;   /* 1: the time ran out (survived), 2: absorbed at the boundary */
   for (int q = 0; q < pb->max_steps; ++q) {
     double dist = 1.0;
+    int near = 0;
     for (int e = 0; e < d; ++e) {
       double de = 1.0 - fabs(X[e]);
-      if (de < dist) dist = de;
+      if (de < dist) { dist = de; near = e; }
     }
-    if (dist < shell) break;
+    if (dist < shell) {
+      /* absorbed: for the direct estimator, the boundary point is the walk's
+       * position moved onto its nearest face, at the path time reached so far */
+      ended = 2;
+      if (t_end) *t_end = t_node - ((double)k * sub + f);
+      if (pb->estimator == 1) X[near] = X[near] < 0.0 ? -1.0 : 1.0;
+      break;
+    }
     int64_t w0 = (int64_t)q * W;
     uint32_t gword = stream_word(&st, w0 + ball_gword_index(d));
     int g = gbits ? (int)(gword >> (32 - gbits)) : 0;
@@ -695,12 +788,33 @@ int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t 
       wts[L] = wq;
     }
     L = q + 1;
-    if (last) break;
+    if (last) {
+      ended = 1;
+      if (pb->estimator == 1) {
+        /* the direct estimator needs the position at t_{n-1}: the last step moves
+         * by sqrt(2 d kappa w) for the time w it took (Lemma Xlocation's increment;
+         * at most the ball's radius, so X stays in Omega), in the step's own
+         * direction words.  Earlier steps move by r = sqrt(2 d kappa w) as well. */
+        direction_at(&st, d, w0, theta);
+        double rl = sqrt(2.0 * d * pb->kappa * w);
+        for (int e = 0; e < d; ++e) X[e] = X[e] + rl * theta[e];
+      }
+      if (t_end) *t_end = ic->t0;
+      break;
+    }
     direction_at(&st, d, w0, theta);
     for (int e = 0; e < d; ++e) X[e] = X[e] + r * theta[e];
   }
   if (x_end) for (int e = 0; e < d; ++e) x_end[e] = X[e];
+  if (end_kind) *end_kind = ended;
   return L;
+}
+
+int orc_walk_points(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node_lin, uint32_t sample,
+                    const double* x_start, double t_node, int nstar, double* pts, double* taus, double* wts,
+                    int cap, double* x_end) {
+  return orc_walk_points_end(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, cap, x_end, NULL,
+                             NULL);
 }
 
 #define ORC_WALK_CAP 8192
@@ -712,13 +826,29 @@ double orc_walk(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node
   double* pts = (double*)malloc(sizeof(double) * ORC_WALK_CAP * d);
   double* taus = (double*)malloc(sizeof(double) * ORC_WALK_CAP);
   double* wts = (double*)malloc(sizeof(double) * ORC_WALK_CAP);
-  int L = orc_walk_points(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, ORC_WALK_CAP, x_end);
+  double xe[ORC_MAXD], te = 0.0;
+  int kind = 0;
+  int L = orc_walk_points_end(pb, ic, node_lin, sample, x_start, t_node, nstar, pts, taus, wts, ORC_WALK_CAP, xe,
+                              &kind, &te);
   double sum = 0.0;
   for (int i = 0; i < L && i < ORC_WALK_CAP; ++i) {
     if (wts[i] == 0.0) continue;
     double r = ic->cu ? orc_residual(pb, ic->Mt, ic->t0, ic->h, ic->cu, ic->ct, pts + i * d, taus[i]) : 1.0;
     sum += wts[i] * r;
   }
+  if (pb->estimator == 1 && ic->cu) {
+    /* Eq. Phi_ast: u*^{n-1}(X, t_{n-1}) for a walk that reached t_{n-1} (the
+     * interval's expansion at xi = -1 is the interpolant of the hand-off row),
+     * g(X, t) where it was absorbed (raw boundary data; zero once homogenised) */
+    if (kind == 1) {
+      double u, dtu, mlap;
+      orc_eval(pb, ic->Mt, ic->cu, ic->ct, xe, -1.0, &u, &dtu, &mlap);
+      sum += u;
+    } else if (kind == 2 && pb->bc_kind == 2) {
+      sum += orc_exact(pb, xe, te);
+    }
+  }
+  if (x_end) for (int e = 0; e < d; ++e) x_end[e] = xe[e];
   free(pts); free(taus); free(wts);
   if (L_out) *L_out = L;
   return sum;
@@ -730,7 +860,8 @@ static void node_coords(int d, int n, const double* xs, int64_t j, double* x) {
 }
 
 /* eps at one node (Eq. varepsilon_1): Neumaier-compensated sum of Q_L over the
- * samples in order, divided by M. */
+ * samples in order, divided by M.  For the direct estimator: the mean of S_i
+ * (Eq. Phi_ast); the iteration subtracts the node's current value. */
 double orc_node_eps(const orc_problem* pb, const orc_interval_ctx* ic, int64_t j, int l) {
   int d = pb->dim, n = pb->n_space;
   double xs[ORC_MAXN], ws[ORC_MAXN], xi[ORC_MAXN + 1], wt[ORC_MAXN + 1], x[ORC_MAXD];
@@ -778,6 +909,7 @@ int orc_iterate(const orc_problem* pb, int interval, double t0, double t1, int M
       int l = 1 + (int)(a / S);
       int64_t j = a % S;
       eps[l * S + j] = orc_node_eps(pb, &ic, j, l);
+      if (pb->estimator == 1) eps[l * S + j] -= U[l * S + j];
     }
     double mx = 0.0;
     for (int l = 1; l <= Mt; ++l)
@@ -842,7 +974,10 @@ int orc_iterate_aitken(const orc_problem* pb, int interval, double t0, double t1
     int nt = pb->n_threads > 0 ? pb->n_threads : 1;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
-    for (int64_t a = 0; a < nn; ++a) eps[a] = orc_node_eps(pb, &ic, a % S, 1 + (int)(a / S));
+    for (int64_t a = 0; a < nn; ++a) {
+      eps[a] = orc_node_eps(pb, &ic, a % S, 1 + (int)(a / S));
+      if (pb->estimator == 1) eps[a] -= U[S + a];
+    }
     double w = (it == 1) ? 1.0 : orc_aitken_omega(nn, eps_prev, eps, *omega);
     double mx = 0.0;
     for (int64_t a = 0; a < nn; ++a) {
@@ -857,7 +992,7 @@ int orc_iterate_aitken(const orc_problem* pb, int interval, double t0, double t1
   return n_iter;
 }
 
-/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:
+/* Value of the interval's expansion at t_n (xi = 1) at every spatial node:
  * u*(x_j, t_n) = sum_q sum_k b_qk U[k][j] L_q(1)  (Algorithm 1, Step 4). */
 void orc_handoff(const orc_problem* pb, int Mt, const double* U, double* row) {
   int64_t S = ipow(pb->n_space, pb->dim);
@@ -881,6 +1016,16 @@ void orc_solve(const orc_problem* pb, int n_int, const double* t, const int* Mt,
   int64_t S = ipow(pb->n_space, pb->dim);
   double* row = (double*)malloc(sizeof(double) * S);
   memcpy(row, u0, sizeof(double) * S);
+  if (pb->bc_kind == 1) {
+    /* w(., 0) = u0 - G(., 0) at the nodes */
+    double xs[ORC_MAXN], ws[ORC_MAXN], x[ORC_MAXD], G, Gt, lapG;
+    orc_jg11_nodes(pb->n_space, xs, ws);
+    for (int64_t j = 0; j < S; ++j) {
+      node_coords(pb->dim, pb->n_space, xs, j, x);
+      orc_lift(pb, x, t[0], &G, &Gt, &lapG);
+      row[j] -= G;
+    }
+  }
   int64_t off = 0;
   for (int m = 0; m < n_int; ++m) {
     double* U = U_all + off;
