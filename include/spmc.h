@@ -48,7 +48,10 @@ typedef enum {
 enum { SPMC_TIME_LGL = 0, SPMC_TIME_RADAU_LEFT = 1 };     /* time nodes per interval */
 enum { SPMC_FP64 = 0, SPMC_MIXED = 1 };                    /* sweep arithmetic */
 enum { SPMC_F_POLY3 = 0, SPMC_F_SIN = 1 };                 /* reaction f(u) */
-enum { SPMC_EX_NONE = 0, SPMC_EX_SIN = 1, SPMC_EX_COSHALF = 2, SPMC_EX_POLY = 3 };
+enum { SPMC_EX_NONE = 0, SPMC_EX_SIN = 1, SPMC_EX_COSHALF = 2, SPMC_EX_POLY = 3,
+       SPMC_EX_COSTHIRD = 4, SPMC_EX_SINPLUS = 5 };                 /* non-zero boundary values */
+enum { SPMC_BC_ZERO = 0, SPMC_BC_LIFT = 1, SPMC_BC_RAW = 2 };       /* boundary data g */
+enum { SPMC_EST_RESIDUAL = 0, SPMC_EST_DIRECT = 1 };               /* estimator */
 enum { SPMC_U0_NODAL = 0, SPMC_U0_PHI_COEF = 1 };
 
 typedef struct spmc_plan_s* spmc_plan_t;
@@ -80,12 +83,22 @@ typedef struct {
                                walk of Lemma Xlocation with the residual at the step centres
                                (Eqs. indexL, interIQ; n_sub is then 1, d <= 2, cohort sweep).
                                The second diverges at high spectral degrees. */
+  int estimator;            /* SPMC_EST_RESIDUAL (0): the residual iteration of Algorithm 1 (u <- u + eps,
+                               eps the mean of Q_L of the residual, Eq. varepsilon_1);
+                               SPMC_EST_DIRECT (1): the direct estimator of Eq. Phi_ast, a Picard
+                               iteration (Eq. linearized_func) u <- mean of S_i, S_i = u*^{n-1}(X, t_{n-1})
+                               for a walk that reaches t_{n-1} (the walk's last step moves by
+                               sqrt(2 d kappa w) for the time w it took), g(X_p, t_p) for one absorbed at
+                               the boundary (raw boundary data), plus the quadrature of f(u*) + f_add.
+                               Its sampling error does not fall with the iterations.  Event sweep only
+                               (d <= 2, walk_mode 0). */
 } spmc_plan_desc;
 enum { SPMC_WALK_BALLS = 0, SPMC_WALK_FIXED = 1 };
 
-/* One instance: partition, degrees, reaction, manufactured source, u0.
- * Eq. mainproblem with homogeneous boundary data; f_add makes the closed form
- * named by ex_kind an exact solution (Section 4 examples). */
+/* One instance: partition, degrees, reaction, manufactured source, boundary
+ * data, u0.  Eq. mainproblem; f_add makes the closed form named by ex_kind an
+ * exact solution (Section 4 examples); the boundary data g is that closed
+ * form's trace (zero for kinds 1-3). */
 typedef struct {
   int n_intervals;          /* 1..max_intervals */
   const double* t_breaks;   /* host, n_intervals + 1 strictly increasing values */
@@ -101,6 +114,14 @@ typedef struct {
                                prod phi_{p_e}(x_e), p_e < n_coef (x_1 fastest) */
   int n_coef;
   const double* u0;         /* host */
+  int bc_kind;              /* SPMC_BC_ZERO: g = 0 (kinds 0-3).  SPMC_BC_LIFT: homogenisation (Section 2.3,
+                               remark on non-homogeneous boundary conditions): the plan solves for
+                               w = u - G, G the Gordon-Hall transfinite lifting of g from its face values,
+                               with the reaction f(w + G) and the source f_add - d_t G + kappa Delta G;
+                               u0 is given for u and w(., 0) = u0 - G(., 0) is formed on the device;
+                               spmc_get_nodes returns w, spmc_get_solution u.  SPMC_BC_RAW: g enters where
+                               the walk is absorbed (SPMC_EST_DIRECT only).  Kinds 4, 5 need LIFT or RAW;
+                               d <= 2 and the event sweep. */
 } spmc_problem;
 
 typedef struct {
@@ -160,6 +181,12 @@ spmc_status spmc_iterate(spmc_plan_t plan, void* cuda_stream, int interval, int 
 /* Copy the current nodal values of (instance, interval) into dst (device
  * pointer, (M_n+1) n_space^d doubles). */
 spmc_status spmc_get_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, double* dst);
+
+/* The solution u at the nodes of (instance, interval) into dst (device
+ * pointer, (M_n+1) n_space^d doubles): the nodal values plus, for lifted
+ * boundary data (SPMC_BC_LIFT), the lifting G(x_j, t_{n,l}) (computed on the
+ * device); otherwise the nodal values themselves. */
+spmc_status spmc_get_solution(spmc_plan_t plan, void* cuda_stream, int instance, int interval, double* dst);
 
 /* Overwrite the nodal values of (instance, interval) with src ((M_n+1)
  * n_space^d doubles, host or device pointer): checkpoint restore, or a chosen

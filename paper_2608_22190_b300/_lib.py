@@ -18,7 +18,9 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5:
 TIME_LGL, TIME_RADAU_LEFT = 0, 1
 FP64, MIXED = 0, 1
 F_POLY3, F_SIN = 0, 1
-EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
+EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS = 0, 1, 2, 3, 4, 5
+BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
+EST_RESIDUAL, EST_DIRECT = 0, 1
 U0_NODAL, U0_PHI_COEF = 0, 1
 SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT, SPMC_SWEEP_EVENTS_ALU = 0, 1, 2
 WALK_BALLS, WALK_FIXED = 0, 1
@@ -31,7 +33,7 @@ class PlanDesc(C.Structure):
         ("max_degree", C.c_int), ("M", C.c_longlong), ("K", C.c_int), ("tol", C.c_double),
         ("n_ref", C.c_int), ("n_sub", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int),
         ("kappa", C.c_double), ("seed", C.c_ulonglong), ("precision", C.c_int), ("batch", C.c_int),
-        ("walk_mode", C.c_int),
+        ("walk_mode", C.c_int), ("estimator", C.c_int),
     ]
 
 
@@ -40,7 +42,7 @@ class Problem(C.Structure):
         ("n_intervals", C.c_int), ("t_breaks", C.POINTER(C.c_double)), ("degrees", C.POINTER(C.c_int)),
         ("f_kind", C.c_int), ("f_coef", C.c_double * 4), ("f_scale", C.c_double),
         ("ex_kind", C.c_int), ("ex_beta", C.c_double), ("u0_kind", C.c_int), ("n_coef", C.c_int),
-        ("u0", C.POINTER(C.c_double)),
+        ("u0", C.POINTER(C.c_double)), ("bc_kind", C.c_int),
     ]
 
 
@@ -62,6 +64,7 @@ _SIGNATURES = {
     "spmc_begin_interval": (C.c_int, [_PLAN, C.c_void_p, C.c_int]),
     "spmc_iterate": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "spmc_get_nodes": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "spmc_get_solution": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "spmc_set_nodes": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "spmc_iterate_static": (C.c_int, [_PLAN, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "spmc_grad": (C.c_int, [_PLAN, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

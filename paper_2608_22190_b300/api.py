@@ -25,13 +25,15 @@ def _stream_ptr(stream) -> Optional[int]:
 
 class Plan:
     def __init__(self, dim, n_space, time_family, max_intervals, max_degree, M, K, tol=0.0, n_ref=80, n_sub=4,
-                 shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1, walk_mode=L.WALK_BALLS):
+                 shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1, walk_mode=L.WALK_BALLS,
+                 estimator=L.EST_RESIDUAL):
         d = L.PlanDesc()
         d.dim, d.n_space, d.time_family = dim, n_space, time_family
         d.max_intervals, d.max_degree, d.M, d.K, d.tol = max_intervals, max_degree, M, K, tol
         d.n_ref, d.n_sub, d.shell, d.max_steps = n_ref, n_sub, shell, max_steps
         d.kappa, d.seed, d.precision, d.batch = kappa, seed, precision, batch
         d.walk_mode = walk_mode
+        d.estimator = estimator
         self.desc = d
         self._h = C.c_void_p()
         L.check(L.lib.spmc_plan(C.byref(d), C.byref(self._h)))
@@ -55,7 +57,7 @@ class Plan:
         return np.stack(cols, axis=1)
 
     def set_problem(self, instance, t_breaks, degrees, f_kind=L.F_POLY3, f_coef=(0, 0, 0, -1.0), f_scale=1.0,
-                    ex_kind=L.EX_NONE, ex_beta=1.0, u0=None, u0_kind=L.U0_NODAL, n_coef=0):
+                    ex_kind=L.EX_NONE, ex_beta=1.0, u0=None, u0_kind=L.U0_NODAL, n_coef=0, bc_kind=L.BC_ZERO):
         t = np.ascontiguousarray(t_breaks, dtype=np.float64)
         dg = np.ascontiguousarray(degrees, dtype=np.int32)
         u = np.ascontiguousarray(u0, dtype=np.float64).ravel()
@@ -68,6 +70,7 @@ class Plan:
             p.f_coef[i] = c
         p.u0_kind, p.n_coef = u0_kind, n_coef
         p.u0 = u.ctypes.data_as(C.POINTER(C.c_double))
+        p.bc_kind = bc_kind
         L.check(L.lib.spmc_set_problem(self._h, instance, C.byref(p)), self._h)
         self.degrees[instance] = [int(v) for v in dg]
 
@@ -90,7 +93,8 @@ class Plan:
                                  L.U0_PHI_COEF, nc)
             else:
                 plan.set_problem(b, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, inst.f_scale,
-                                 inst.ex_kind, inst.ex_beta, W.u0_nodal(inst, grid))
+                                 inst.ex_kind, inst.ex_beta, W.u0_nodal(inst, grid),
+                                 bc_kind=getattr(inst, "bc_kind", L.BC_ZERO))
         return plan
 
     # ------------------------------------------------------------------ layout
@@ -176,6 +180,15 @@ class Plan:
         out = torch.empty((Mt + 1, self.S), dtype=torch.float64, device="cuda")
         L.check(L.lib.spmc_get_nodes(self._h, C.c_void_p(_stream_ptr(stream)), instance, interval,
                                      C.c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def get_solution(self, instance: int, interval: int, stream=None) -> torch.Tensor:
+        """u at the nodes of (instance, interval): the nodal values plus the lifting
+        of the boundary data where it is lifted (computed on the device)."""
+        Mt = self.degrees[instance][interval]
+        out = torch.empty((Mt + 1, self.S), dtype=torch.float64, device="cuda")
+        L.check(L.lib.spmc_get_solution(self._h, C.c_void_p(_stream_ptr(stream)), instance, interval,
+                                        C.c_void_p(out.data_ptr())), self._h)
         return out
 
     def get_nodes_into(self, instance: int, interval: int, dst: torch.Tensor, stream=None):

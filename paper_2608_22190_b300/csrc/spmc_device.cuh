@@ -257,6 +257,35 @@ __device__ __forceinline__ bool fix_from_float(float x, __int128& N) {
   N = (b >> 31) ? -(__int128)v : (__int128)v;
   return true;
 }
+// The same fixed-point value of an FP32 term as five signed 26-bit limbs,
+// N = sum_k L[k] 2^(26 k): the (rounded) 24-bit significand shifted to its
+// place spans two adjacent limbs, the others are zero.  Each |L[k]| < 2^26, so
+// 32 of them sum exactly in an int32 (a warp reduction per limb), and the
+// limb sums reassemble the exact 128-bit total.
+__device__ __forceinline__ bool fix_limbs_float(float x, int (&L)[5]) {
+  const uint32_t b = __float_as_uint(x);
+  const int E = (int)((b >> 23) & 0xff);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) L[k] = 0;
+  if (E >= 127 + 46) return false;
+  uint32_t m = (b & 0x7fffffu) | (E ? 0x800000u : 0u);
+  int s = (E ? E : 1) - 150 + kFixFrac;           // x = m 2^(E - 150): N = m 2^s
+  if (s < 0) { m = s > -25 ? (m + (1u << (-s - 1))) >> (-s) : 0u; s = 0; }
+  const int li = s / 26;                           // s <= 102: li <= 3
+  const unsigned long long t = (unsigned long long)m << (s - 26 * li);   // < 2^50
+  int lo = (int)(t & 0x3ffffffull), hi = (int)(t >> 26);
+  if (b >> 31) { lo = -lo; hi = -hi; }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) L[k] = (k == li) ? lo : ((k == li + 1) ? hi : 0);
+  return true;
+}
+__device__ __forceinline__ __int128 fix_from_limbs(const int (&L)[5]) {
+  __int128 N = 0;
+#pragma unroll
+  for (int k = 4; k >= 0; --k) N = N * ((__int128)1 << 26) + (__int128)L[k];
+  return N;
+}
+
 template <typename R> __device__ __forceinline__ bool fix_from(R x, __int128& N);
 template <> __device__ __forceinline__ bool fix_from<double>(double x, __int128& N) { return fix_from_double(x, N); }
 template <> __device__ __forceinline__ bool fix_from<float>(float x, __int128& N) { return fix_from_float(x, N); }
@@ -302,10 +331,12 @@ __device__ __forceinline__ double fix_value(const unsigned long long* acc) {
 // ------------------------------------------------------------------ problem
 struct InstanceParams {
   int f_kind;      // 0: s (c0 + c1 u + c2 u^2 + c3 u^3), 1: s sin(u)
-  int ex_kind;     // 0 none, 1 sin product, 2 half-cos product, 3 polynomial
+  int ex_kind;     // 0 none, 1 sin product, 2 half-cos product, 3 polynomial,
+                   // 4 shifted third-cos product, 5 sin product + t/2 (non-zero boundary values)
   double fc[4];
   double f_scale;
   double ex_beta;
+  int bc_kind;     // 0 g = 0, 1 lifted (the unknown is w = u - G), 2 g at absorption
 };
 
 template <typename R>
@@ -344,6 +375,76 @@ __device__ __forceinline__ R source(const InstanceParams& ip, R kappa, const R* 
   return dTt * prod + kappa * Tt * mlap - reaction<R>(ip, ue);
 }
 
+// Closed forms with non-zero boundary values (the remark on non-homogeneous
+// boundary conditions in Section 2.3), T = e^{-beta t}:
+//   4: u = T prod c(y_e),  c(y) = cos(pi (y - 0.3) / 3)   (different values on opposite faces)
+//   5: u = T prod sin(pi y_e) + t / 2                      (u(., 0) = 0 on the boundary)
+template <int D, typename R>
+__device__ __forceinline__ R exact_bv(const InstanceParams& ip, const R* y, R Tt, R t) {
+  R prod = R(1);
+  if (ip.ex_kind == 4) {
+#pragma unroll
+    for (int e = 0; e < D; ++e) prod *= Ar<R>::cospi_((y[e] - R(0.3)) / R(3));
+    return Tt * prod;
+  }
+#pragma unroll
+  for (int e = 0; e < D; ++e) prod *= Ar<R>::sinpi_(y[e]);
+  return Tt * prod + R(0.5) * t;
+}
+
+// The Gordon-Hall transfinite lifting G of the boundary trace of kinds 4 and 5
+// and its d_t G, Delta G at (y, t).  For a product trace T prod c(y_e) the
+// lifting is T (prod c - prod (c - c_b)), c_b the linear interpolant of c
+// between the faces; kind 5's trace t/2 lifts to the constant t/2.  Zero
+// unless bc_kind == 1.
+template <int D, typename R>
+__device__ __forceinline__ void lift_bv(const InstanceParams& ip, const R* y, R Tt, R t, R& G, R& Gt, R& lapG) {
+  G = R(0); Gt = R(0); lapG = R(0);
+  if (ip.bc_kind != 1 || ip.ex_kind < 4) return;
+  if (ip.ex_kind == 5) { G = R(0.5) * t; Gt = R(0.5); return; }
+  const R cm = R(0.20791169081775945), cp = R(0.7431448254773942);   // c(-1), c(1)
+  R c[D], dl[D], pc = R(1), pd = R(1);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    c[e] = Ar<R>::cospi_((y[e] - R(0.3)) / R(3));
+    dl[e] = c[e] - (R(0.5) * (R(1) - y[e]) * cm + R(0.5) * (R(1) + y[e]) * cp);
+    pc *= c[e];
+    pd *= dl[e];
+  }
+  G = Tt * (pc - pd);
+  Gt = R(-ip.ex_beta) * G;
+  // c'' = -(pi/3)^2 c and (c - c_b)'' = c''
+  R s = R(0);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    R term = c[e];
+#pragma unroll
+    for (int f = 0; f < D; ++f) if (f != e) term *= dl[f];
+    s += term;
+  }
+  lapG = R(-kPiD * kPiD / 9.0) * Tt * (R(D) * pc - s);
+}
+
+// The forcing of the equation the iteration solves at (y, tau) for the current
+// u* there: f(u*) + f_add, or with lifted boundary data (bc_kind 1)
+// f(u* + G) + f_add - d_t G + kappa Delta G (the equation for w = u - G).
+// Kinds 0-3 evaluate exactly reaction + source.
+template <int D, typename R>
+__device__ __forceinline__ R forcing(const InstanceParams& ip, R kappa, const R* y, R Tt, R dTt, R tau, R u) {
+  if (ip.ex_kind <= 3) return reaction<R>(ip, u) + source<D, R>(ip, kappa, y, Tt, dTt);
+  R G, Gt, lapG;
+  lift_bv<D, R>(ip, y, Tt, tau, G, Gt, lapG);
+  const R ue = exact_bv<D, R>(ip, y, Tt, tau);
+  R fadd;
+  if (ip.ex_kind == 4) {
+    fadd = (R(-ip.ex_beta) + kappa * R(D * kPiD * kPiD / 9.0)) * ue - reaction<R>(ip, ue);
+  } else {
+    const R sp = ue - R(0.5) * tau;   // the sine part
+    fadd = (R(-ip.ex_beta) + kappa * R(D * kPiD * kPiD)) * sp + R(0.5) - reaction<R>(ip, ue);
+  }
+  return reaction<R>(ip, u + G) + fadd - Gt + kappa * lapG;
+}
+
 // Recurrence coefficients of P^{(1,1)}: P_p = ra_p x P_{p-1} - rb_p P_{p-2},
 // ra_p = (2p+1)(p+1)/(p(p+2)), rb_p = (p+1)/(p+2); lam_p = (p+1)(p+2)
 // (tables filled once by the host, read through the constant cache).
@@ -376,15 +477,16 @@ __device__ __forceinline__ void basis(int n, R y, R* phi, R* psi) {
   }
 }
 
-// The residual at y from one slice: C = time-contracted coefficients of u*,
+// u* and G = -d_t u* + kappa Delta u* at y from one slice (slice_parts), and
+// the residual there (residual_at): C = time-contracted coefficients of u*,
 // H = time-contracted coefficients of -d_t u* (both in the phi basis; for d=2
 // stored [p_x][p_y] with p_y contiguous).
 //   u* = sum_p C_p Phi_p(y),
 //   G  = sum_p H_p Phi_p(y) - kappa sum_p C_p Psi_p(y)   (= -d_t u* + kappa Delta u*)
 //   r  = f(u*) + f_add + G
 template <int D, int NMAX, typename R>
-__device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int n, const R* __restrict__ sC,
-                                         const R* __restrict__ sH, const R* y, R Tt, R dTt) {
+__device__ __forceinline__ void slice_parts(R kappa, int n, const R* __restrict__ sC, const R* __restrict__ sH,
+                                            const R* y, R& u_out, R& G_out) {
   R u = R(0), G = R(0);
   if (D == 1) {
     R om = R(1) - y[0] * y[0];
@@ -452,6 +554,14 @@ __device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int 
     }
     G -= kappa * cpsi;
   }
+  u_out = u;
+  G_out = G;
+}
+template <int D, int NMAX, typename R>
+__device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int n, const R* __restrict__ sC,
+                                         const R* __restrict__ sH, const R* y, R Tt, R dTt) {
+  R u, G;
+  slice_parts<D, NMAX, R>(kappa, n, sC, sH, y, u, G);
   return reaction<R>(ip, u) + source<D, R>(ip, kappa, y, Tt, dTt) + G;
 }
 

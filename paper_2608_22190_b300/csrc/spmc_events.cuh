@@ -45,6 +45,7 @@ template <typename R> struct EventOf<5, R> { using type = Event5<R>; };
 
 struct EventArgs {
   const TimeNode* tn;
+  const InstanceParams* ip;
   const double* xnodes;
   unsigned int* counts;          // COUNT: (slice, node) histogram; FILL: placement cursors
   void* events;                  // Event<R>[cap] grouped by (slice, node) (FILL)
@@ -58,6 +59,7 @@ struct EventArgs {
   double kappa, shell;
   uint32_t k0, k1;
   unsigned long long* counters;  // [0] points, [1] capped
+  int direct;                    // the direct estimator (Eq. Phi_ast): initial- and boundary-term events
 };
 
 // Per-warp queue of pending evaluation events of the placing pass: what the
@@ -168,7 +170,9 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
 
   // walk state
   bool live = false, more = true;
-  R X[D], f = R(0), delta = R(0), J = R(0), sub = R(0);
+  bool pend = false;     // direct estimator: the walk reached t_{n-1}; its initial-term event is next
+  bool bc_raw = false;   // direct estimator with raw boundary data: absorbed walks emit the boundary term
+  R X[D], f = R(0), delta = R(0), J = R(0), sub = R(0), t_node = R(0);
   int k = 0, q = 0, Ktot = 0, key_j = 0;
   long long slice_base = 0, cached_ti = -1;
   uint32_t node_ell = 0;
@@ -209,6 +213,8 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
             Ktot = G * node.nstar;
             slice_base = node.slice_base;
             node_ell = (uint32_t)node.ell;
+            t_node = (R)node.t_node;
+            bc_raw = a.direct && a.ip[node.inst].bc_kind == 2;
             ws.tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
                      (uint32_t)(a.iteration & 0x3ff);
             cached_ti = ti;
@@ -226,19 +232,38 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
     }
     // ---- stage 2: the step, as the CPU reference: absorb, ball, weight, sub-point, roulette
     bool emit = false, last = false;
-    R w = R(0), r = R(0);
+    R w = R(0), r = R(0), wstep = R(0);
     unsigned int key = 0;
-    Philox4 b0;
+    Philox4 b0{};
     uint32_t w0 = 0;
-    if (live) {
+    if (live && pend) {
+      // the direct estimator's initial term u*(X, t_{n-1}), weight 1, in the slot after the walk grid
+      emit = true;
+      w = R(1);
+      key = ((uint32_t)slice_base + (uint32_t)Ktot) * (uint32_t)S + (uint32_t)key_j;
+      pend = false;
+      live = false;
+    } else if (live) {
       R dist = R(1);
+      int near = 0;
 #pragma unroll
       for (int e = 0; e < D; ++e) {
         const R de = Ar<R>::sub(R(1), fabs(X[e]));
-        if (de < dist) dist = de;
+        if (de < dist) { dist = de; near = e; }
       }
       if (q >= a.max_steps || dist < shell) {
-        if (q >= a.max_steps) ++capped;
+        if (q >= a.max_steps) {
+          ++capped;
+        } else if (bc_raw) {
+          // absorbed: the boundary term g(X, t) at the nearest face and the path
+          // time reached (carried in the weight field), in the second extra slot
+#pragma unroll
+          for (int e = 0; e < D; ++e)
+            if (e == near) X[e] = X[e] < R(0) ? R(-1) : R(1);
+          w = Ar<R>::sub(t_node, Ar<R>::add(Ar<R>::mul((R)k, sub), f));
+          emit = true;
+          key = ((uint32_t)slice_base + (uint32_t)Ktot + 1u) * (uint32_t)S + (uint32_t)key_j;
+        }
         live = false;
       } else {
         w0 = (uint32_t)q * WS;   // a multiple of 4
@@ -272,6 +297,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
             if (k >= Ktot) last = true;
           }
         }
+        wstep = w;
         // roulette for shrunk balls
         if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D) & 3], Ar<R>::div(w, delta)) ? delta : R(0);
         emit = w > R(0);
@@ -321,11 +347,18 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
         qn = rest;
       }
     }
-    // ---- stage 4: the walk ends, or moves to the sphere of its ball
+    // ---- stage 4: the walk ends, or moves to the sphere of its ball.  For the
+    // direct estimator the last step moves too, by sqrt(2 d kappa w) for the
+    // time w it took (at most the ball's radius), and the walk's initial-term
+    // event follows in the next round.
     if (live) {
-      if (last) {
+      if (last && !a.direct) {
         live = false;
       } else {
+        if (last) {
+          r = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), wstep));
+          pend = true;
+        }
         if constexpr (D == 1) {
           const R th = (b0.v[0] >> 31) ? R(-1) : R(1);
           X[0] = Ar<R>::add(X[0], Ar<R>::mul(r, th));
@@ -458,8 +491,11 @@ __device__ __forceinline__ __int128 warp_run_sum(__int128 v, unsigned int key, u
   return v;
 }
 
-// One block per slice: stage the slice, evaluate its events, sum w r per node
-// (exact fixed-point sums into four limb counters per (time node, node)).
+// One block per slice: stage the slice, evaluate its events, sum their terms
+// per node (exact fixed-point sums into four limb counters per (time node,
+// node)).  A term is w r at a walk-grid slice (the residual, or for the direct
+// estimator the forcing alone), u*(X, t_{n-1}) at the direct estimator's
+// initial-term slot, g(X, t) at its boundary-term slot.
 template <int D, int NMAX, typename R>
 __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __restrict__ slice_node,
                                                           const TimeNode* __restrict__ tn,
@@ -469,7 +505,7 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
                                                           const unsigned int* __restrict__ starts,
                                                           const void* __restrict__ events_v,
                                                           unsigned long long* __restrict__ acc, int n, int S,
-                                                          long long sl_stride, int half, double kappa_d,
+                                                          long long sl_stride, int half, double kappa_d, int direct,
                                                           const unsigned long long* __restrict__ n_events_p,
                                                           int* status, const int* __restrict__ abort) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -500,8 +536,20 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
       R Y[D];
       Y[0] = e.y[0];
       if (D == 2) Y[1] = e.y[1];
-      const R res = residual_at<D, NMAX, R>(ip, kappa, n, sC, sC + half, Y, (R)si.Tt, (R)si.dTt);
-      if (!fix_from<R>(e.w * res, val)) atomicOr(status, 1);
+      R u, G;
+      slice_parts<D, NMAX, R>(kappa, n, sC, sC + half, Y, u, G);
+      R term;
+      if (si.kind == 0) {
+        // w (f + f_add [+ lifting terms]) [+ w (-d_t u* + kappa Delta u*) for the residual iteration]
+        R res = forcing<D, R>(ip, kappa, Y, (R)si.Tt, (R)si.dTt, (R)si.tau, u);
+        if (!direct) res += G;
+        term = e.w * res;
+      } else if (si.kind == 1) {
+        term = u;   // the initial term u*(X, t_{n-1})
+      } else {
+        term = exact_bv<D, R>(ip, Y, (R)exp(-ip.ex_beta * (double)e.w), e.w);   // g(X, t), t in the weight field
+      }
+      if (!fix_from<R>(term, val)) atomicOr(status, 1);
       key = e.key;
     }
     // per-node sums: events are sorted by key, so equal keys are adjacent lanes

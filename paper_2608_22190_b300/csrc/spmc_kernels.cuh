@@ -40,6 +40,8 @@ struct InstInterval {
 struct SliceInfo {
   double tau;       // path time of the sub-point
   double Tt, dTt;   // exact-solution time factor and its derivative at tau
+  int kind;         // 0: a sub-point of the walk grid; the direct estimator's two extra slots
+                    // per time node: 1 the initial term at t_{n-1}, 2 the boundary term
 };
 
 // ----------------------------------------------------------------- Step 1
@@ -124,7 +126,10 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
   const double sdur = __dsub_rn(node.t_node, node.t0);
   const double delta = __ddiv_rn(sdur, (double)node.nstar);
   const double sub = __ddiv_rn(delta, (double)n_sub);
-  const double tau = __dsub_rn(node.t_node, __dmul_rn((double)m + t_off, sub));
+  const int Ktot = n_sub * node.nstar;
+  // the direct estimator's slots after the walk grid: the expansion at t_{n-1}
+  const int kind = m < Ktot ? 0 : 1 + (m - Ktot);
+  const double tau = kind ? node.t0 : __dsub_rn(node.t_node, __dmul_rn((double)m + t_off, sub));
   if (threadIdx.x == 0) {
     double xi = (2.0 * tau - node.t0 - (node.t0 + node.h)) / node.h;
     L[0] = 1.0;
@@ -133,8 +138,9 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
     const InstanceParams P = ip[node.inst];
     SliceInfo si;
     si.tau = tau;
+    si.kind = kind;
     if (P.ex_kind == 3) { si.Tt = 1.0 + tau + tau * tau; si.dTt = 1.0 + 2.0 * tau; }
-    else if (P.ex_kind == 1 || P.ex_kind == 2) { si.Tt = exp(-P.ex_beta * tau); si.dTt = -P.ex_beta * si.Tt; }
+    else if (P.ex_kind >= 1) { si.Tt = exp(-P.ex_beta * tau); si.dTt = -P.ex_beta * si.Tt; }
     else { si.Tt = 0.0; si.dTt = 0.0; }
     sinfo[s] = si;
   }
@@ -629,16 +635,19 @@ __global__ void update_kernel(const TimeNode* __restrict__ tn, const double* __r
 __global__ void update_fixed_kernel(const TimeNode* __restrict__ tn, const unsigned long long* __restrict__ acc,
                                     double* __restrict__ U, double* __restrict__ eps_out,
                                     unsigned long long* __restrict__ max_eps_bits, int* status, long long n_nodes,
-                                    int S, double inv_M, const int* __restrict__ abort) {
+                                    int S, double inv_M, int direct, const int* __restrict__ abort) {
   if (abort && *abort) return;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   const long long ti = i / S;
   const int j = (int)(i - ti * S);
   const TimeNode node = tn[ti];
-  const double e = fix_value(acc + 4 * i) * inv_M;
+  const long long ui = node.u_off + (long long)node.ell * S + j;
+  // residual iteration: eps = mean of Q; direct estimator: eps = mean of S_i - u
+  double e = fix_value(acc + 4 * i) * inv_M;
+  if (direct) e -= U[ui];
   if (!isfinite(e)) atomicOr(status, 1);
-  U[node.u_off + (long long)node.ell * S + j] += e;
+  U[ui] += e;
   if (eps_out) eps_out[i] = e;
   atomicMax(&max_eps_bits[node.inst], (unsigned long long)__double_as_longlong(fabs(e)));
 }
@@ -646,11 +655,17 @@ __global__ void update_fixed_kernel(const TimeNode* __restrict__ tn, const unsig
 // The node-sharded iteration: eps of the pairs i in [lo, hi) from their exact
 // sums (no update), and the update of every pair from a gathered eps array.
 __global__ void eps_out_kernel(const unsigned long long* __restrict__ acc, double* __restrict__ eps, long long lo,
-                               long long hi, double inv_M, int* status, const int* __restrict__ abort) {
+                               long long hi, double inv_M, int* status, const TimeNode* __restrict__ tn,
+                               const double* __restrict__ U, int S, int direct, const int* __restrict__ abort) {
   if (*abort) return;
   const long long i = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= hi) return;
-  const double e = fix_value(acc + 4 * i) * inv_M;
+  double e = fix_value(acc + 4 * i) * inv_M;
+  if (direct) {   // the direct estimator's value minus the node's current value
+    const long long ti = i / S;
+    const TimeNode node = tn[ti];
+    e -= U[node.u_off + (long long)node.ell * S + (i - ti * S)];
+  }
   if (!isfinite(e)) atomicOr(status, 1);
   eps[i] = e;
 }
@@ -742,12 +757,51 @@ __global__ void aitken_apply_kernel(const InstInterval* __restrict__ ii, const T
 
 // ----------------------------------------------------------------- Step 4 and first iterate
 // row 0 of interval 0 from u0; every other row equal to row 0.
+// With lifted boundary data the unknown starts from w(., t_0) = u0 - G(., t_0).
+template <int D>
 __global__ void init_first_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ u0,
-                                  double* __restrict__ U, int S) {
+                                  double* __restrict__ U, int S, const InstanceParams* __restrict__ ipt,
+                                  const double* __restrict__ xnodes, int n) {
   const InstInterval w = ii[blockIdx.x];
+  const InstanceParams ip = ipt[w.inst];
   const int T = w.Mt + 1;
-  for (int i = threadIdx.x; i < T * S; i += blockDim.x)
-    U[w.u_off + i] = u0[(long long)w.inst * S + (i % S)];
+  const double Tt = exp(-ip.ex_beta * w.t0);
+  for (int i = threadIdx.x; i < T * S; i += blockDim.x) {
+    const int j = i % S;
+    double v = u0[(long long)w.inst * S + j];
+    if (ip.bc_kind == 1) {
+      double y[D], G, Gt, lapG;
+      int jr = j;
+#pragma unroll
+      for (int e = 0; e < D; ++e) { y[e] = xnodes[jr % n]; jr /= n; }
+      lift_bv<D, double>(ip, y, Tt, w.t0, G, Gt, lapG);
+      v -= G;
+    }
+    U[w.u_off + i] = v;
+  }
+}
+
+// The solution at the nodes of one instance's interval: the nodal values plus
+// the lifting G(x_j, t_{n,l}) for lifted boundary data.  `times` holds t_{n,l}.
+template <int D>
+__global__ void solution_kernel(const double* __restrict__ U, double* __restrict__ out,
+                                const InstanceParams* __restrict__ ipt, int inst, const double* __restrict__ times,
+                                const double* __restrict__ xnodes, int n, int S, int T) {
+  const InstanceParams ip = ipt[inst];
+  const long long tot = (long long)T * S;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(i / S), j = (int)(i - (long long)l * S);
+    double v = U[i];
+    if (ip.bc_kind == 1) {
+      double y[D], G, Gt, lapG;
+      int jr = j;
+#pragma unroll
+      for (int e = 0; e < D; ++e) { y[e] = xnodes[jr % n]; jr /= n; }
+      lift_bv<D, double>(ip, y, exp(-ip.ex_beta * times[l]), times[l], G, Gt, lapG);
+      v += G;
+    }
+    out[i] = v;
+  }
 }
 
 // u*(x_j, t_n) = sum_k hw_k U[k][j] with hw_k = sum_q b_qk L_q(1); the next

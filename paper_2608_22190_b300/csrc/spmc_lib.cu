@@ -91,6 +91,7 @@ struct spmc_plan_s {
   std::vector<double> xnodes;
   // device
   double* d_x = nullptr;
+  double* d_times = nullptr;     // t_{n,l} of one interval (spmc_get_solution)
   double* d_A = nullptr;
   double* d_B = nullptr;
   double* d_hw = nullptr;
@@ -276,7 +277,8 @@ spmc_status build(spmc_plan_t plan) {
         t.t_node = w.t0 + s;
         t.nstar = nstar_of(d.n_ref, s, w.h);
         t.slice_base = slice_off;
-        long long ns = (long long)d.n_sub * t.nstar;
+        // the direct estimator's two slots after the walk grid: initial term, boundary term
+        long long ns = (long long)d.n_sub * t.nstar + (d.estimator == SPMC_EST_DIRECT ? 2 : 0);
         for (long long m = 0; m < ns; ++m) rd.slice_node.push_back((long long)rd.tn.size());
         slice_off += ns;
         rd.tn.push_back(t);
@@ -342,10 +344,24 @@ spmc_status refresh_params(spmc_plan_t plan, cudaStream_t stream) {
   return SPMC_OK;
 }
 
-spmc_status ensure_ready(spmc_plan_t plan, cudaStream_t stream) {
-  if (!plan->built) return build(plan);
-  if (plan->params_dirty) return refresh_params(plan, stream);
+bool uses_events(spmc_plan_t plan);
+
+// Non-zero boundary data and the direct estimator run on the event sweep only.
+spmc_status check_event_only(spmc_plan_t plan) {
+  bool need = plan->d.estimator == SPMC_EST_DIRECT;
+  for (const HostProblem& P : plan->probs) need = need || P.ip.bc_kind != SPMC_BC_ZERO;
+  if (need && (plan->d.dim > 2 || !uses_events(plan)))
+    return fail(plan, SPMC_ERR_UNSUPPORTED,
+                "boundary data and the direct estimator need the event sweep (d <= 2, inside-ball walk)");
   return SPMC_OK;
+}
+
+spmc_status ensure_ready(spmc_plan_t plan, cudaStream_t stream) {
+  spmc_status st = SPMC_OK;
+  if (!plan->built) st = build(plan);
+  else if (plan->params_dirty) st = refresh_params(plan, stream);
+  if (st != SPMC_OK) return st;
+  return check_event_only(plan);
 }
 
 // Arguments of the cohort sweep kernels for one iteration of round rd.
@@ -621,34 +637,43 @@ void launch_eval(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   const size_t esmem = sizeof(R) * (size_t)plan->sl_stride;
   eval_events_kernel<D, NMAX, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(
       rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
-      plan->d_acc, plan->d.n_space, plan->S, plan->sl_stride, plan->half, plan->d.kappa, plan->d_total,
-      plan->d_status, plan->d_abort);
+      plan->d_acc, plan->d.n_space, plan->S, plan->sl_stride, plan->half, plan->d.kappa, plan->d.estimator,
+      plan->d_total, plan->d_status, plan->d_abort);
 }
 
 // Tensor-core evaluation (d = 2, FP32 sweep).  The dynamic shared memory is
 // padded so that at most 512 / TM_COLS blocks share an SM: their TMEM
-// allocations then always fit and tcgen05.alloc never waits.  The grid covers
-// the event buffer's capacity (the batch's total stays on the device).
-template <int NMAX>
-spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
+// allocations then always fit and tcgen05.alloc never waits.  The grid is one
+// resident wave (BLOCKS_PER_SM x the SM count, fewer for a small buffer); the
+// blocks loop over the batch's event chunks (the total stays on the device).
+template <int NMAX, bool FULL>
+spmc_status launch_eval_tc_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   using Gm = TcGeom<NMAX>;
-  const int max_blocks = 512 / Gm::TM_COLS;
-  const int smem = std::max(Gm::SMEM, 233472 / (max_blocks + 1) + 1024);
+  const int smem = std::max(Gm::SMEM, 233472 / (Gm::BLOCKS_PER_SM + 1) + 1024);
   static bool attr_set[64] = {};
   int dev = 0;
   SPMC_CUDA(cudaGetDevice(&dev));
   if (dev < 64 && !attr_set[dev]) {
-    SPMC_CUDA(cudaFuncSetAttribute(eval_events_tc_kernel<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SPMC_CUDA(cudaFuncSetAttribute(eval_events_tc_kernel<NMAX, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem));
     attr_set[dev] = true;
   }
-  const unsigned long long blocks = (plan->ev_cap + Gm::CHUNK - 1) / Gm::CHUNK;
-  if (blocks > 0x7fffffffULL) return fail(plan, SPMC_ERR_UNSUPPORTED, "event batch too large for one evaluation launch");
-  eval_events_tc_kernel<NMAX><<<(unsigned)blocks, 128, smem, stream>>>(
+  int n_sm = 0;
+  SPMC_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned long long chunks = (plan->ev_cap + Gm::CHUNK - 1) / Gm::CHUNK;
+  const unsigned long long blocks = std::max(1ULL, std::min(chunks, (unsigned long long)Gm::BLOCKS_PER_SM * n_sm));
+  eval_events_tc_kernel<NMAX, FULL><<<(unsigned)blocks, Gm::THREADS, smem, stream>>>(
       rd.d_slice_node, rd.d_tn, plan->d_ip, reinterpret_cast<const float*>(plan->d_slices), plan->d_sinfo,
       plan->d_starts, reinterpret_cast<const Event<float>*>(plan->d_events), plan->d_acc, plan->d.n_space, plan->S,
-      rd.n_slices, plan->sl_stride, plan->half, plan->d.kappa, plan->d_total, plan->d_status, plan->d_abort);
+      rd.n_slices, plan->sl_stride, plan->half, plan->d.kappa, plan->d.estimator, plan->d_total, plan->d_status,
+      plan->d_abort);
   SPMC_CUDA(cudaGetLastError());
   return SPMC_OK;
+}
+template <int NMAX>
+spmc_status launch_eval_tc(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
+  return plan->d.n_space == NMAX ? launch_eval_tc_t<NMAX, true>(plan, stream, rd)
+                                 : launch_eval_tc_t<NMAX, false>(plan, stream, rd);
 }
 
 // Give the event buffer room for `events` events plus a quarter (the batches of
@@ -747,7 +772,8 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   }
   SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, 4 * sizeof(unsigned long long) * n_tn * S, stream));
   EventArgs a;
-  a.tn = rd.d_tn; a.xnodes = plan->d_x; a.counts = plan->d_counts;
+  a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.counts = plan->d_counts;
+  a.direct = d.estimator == SPMC_EST_DIRECT ? 1 : 0;
   a.status = plan->d_status;
   a.abort = plan->d_abort;
   a.events = nullptr; a.cap = 0;
@@ -897,9 +923,9 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
     }
     if (!plan->d_omega) SPMC_CUDA(pmalloc(plan, (void**)&plan->d_omega, sizeof(double) * plan->d.batch));
     if (events)
-      eps_out_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(plan->d_acc, plan->d_eps_cur, 0, nn,
-                                                                       1.0 / (double)plan->d.M, plan->d_status,
-                                                                       plan->d_abort);
+      eps_out_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
+          plan->d_acc, plan->d_eps_cur, 0, nn, 1.0 / (double)plan->d.M, plan->d_status, rd.d_tn, plan->d_U, S,
+          plan->d.estimator, plan->d_abort);
     else
       eps_from_partial_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
           plan->d_partial, plan->d_eps_cur, nn, (int)((plan->d.M + plan->chunk - 1) / plan->chunk),
@@ -913,7 +939,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
     if (events)
       update_fixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
           rd.d_tn, plan->d_acc, plan->d_U, nullptr, plan->d_maxeps, plan->d_status, nn, S, 1.0 / (double)plan->d.M,
-          plan->d_abort);
+          plan->d.estimator, plan->d_abort);
     else
       update_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
           rd.d_tn, plan->d_partial, plan->d_U, nullptr, plan->d_maxeps, plan->d_status, nn, S,
@@ -1055,8 +1081,13 @@ spmc_status begin_interval(spmc_plan_t plan, cudaStream_t stream, int r) {
   Round& rd = plan->rounds[r];
   rd.iteration = 0;
   if (r == 0) {
-    if (!rd.ii.empty())
-      init_first_kernel<<<(unsigned)rd.ii.size(), 256, 0, stream>>>(rd.d_ii, plan->d_u0, plan->d_U, plan->S);
+    if (!rd.ii.empty()) {
+      const unsigned g = (unsigned)rd.ii.size();
+      const int n = plan->d.n_space;
+      if (plan->d.dim == 1) init_first_kernel<1><<<g, 256, 0, stream>>>(rd.d_ii, plan->d_u0, plan->d_U, plan->S, plan->d_ip, plan->d_x, n);
+      else if (plan->d.dim == 2) init_first_kernel<2><<<g, 256, 0, stream>>>(rd.d_ii, plan->d_u0, plan->d_U, plan->S, plan->d_ip, plan->d_x, n);
+      else init_first_kernel<5><<<g, 256, 0, stream>>>(rd.d_ii, plan->d_u0, plan->d_U, plan->S, plan->d_ip, plan->d_x, n);
+    }
   } else {
     Round& prev = plan->rounds[r - 1];
     if (!prev.ii.empty())
@@ -1227,7 +1258,7 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
       (d.n_sub & (d.n_sub - 1)) || !(d.shell >= 0.0) || d.shell >= 0.5 || d.max_steps < 1 || !(d.kappa > 0.0) || d.batch < 1 ||
       (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
       (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL ||
-      (d.walk_mode != 0 && d.walk_mode != 1))
+      (d.walk_mode != 0 && d.walk_mode != 1) || (d.estimator != SPMC_EST_RESIDUAL && d.estimator != SPMC_EST_DIRECT))
     return SPMC_ERR_INVALID;
   if (d.dim != 1 && d.dim != 2 && d.dim != 5) return SPMC_ERR_UNSUPPORTED;
   if (d.dim == 5 && d.n_space > 8) return SPMC_ERR_UNSUPPORTED;
@@ -1238,6 +1269,7 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   }
   if (d.tol > 0.0 && d.batch > 1) return SPMC_ERR_UNSUPPORTED;
   if (d.walk_mode == 1 && d.dim > 2) return SPMC_ERR_UNSUPPORTED;
+  if (d.estimator == SPMC_EST_DIRECT && (d.dim > 2 || d.walk_mode != 0)) return SPMC_ERR_UNSUPPORTED;
   spmc_plan_t plan = new spmc_plan_s();
   plan->d = d;
   if (d.walk_mode == 1) plan->d.n_sub = 1;   // one evaluation time per step: its centre
@@ -1310,7 +1342,14 @@ spmc_status spmc_set_problem(spmc_plan_t plan, int instance, const spmc_problem*
     if (p.degrees[m] < 1 || p.degrees[m] > d.max_degree) return fail(plan, SPMC_ERR_INVALID, "degree out of range");
   }
   if (p.f_kind != SPMC_F_POLY3 && p.f_kind != SPMC_F_SIN) return fail(plan, SPMC_ERR_INVALID, "bad f_kind");
-  if (p.ex_kind < SPMC_EX_NONE || p.ex_kind > SPMC_EX_POLY) return fail(plan, SPMC_ERR_INVALID, "bad ex_kind");
+  if (p.ex_kind < SPMC_EX_NONE || p.ex_kind > SPMC_EX_SINPLUS) return fail(plan, SPMC_ERR_INVALID, "bad ex_kind");
+  if (p.bc_kind < SPMC_BC_ZERO || p.bc_kind > SPMC_BC_RAW) return fail(plan, SPMC_ERR_INVALID, "bad bc_kind");
+  if (p.ex_kind >= SPMC_EX_COSTHIRD && p.bc_kind == SPMC_BC_ZERO)
+    return fail(plan, SPMC_ERR_INVALID, "ex_kind 4 and 5 have non-zero boundary values: bc_kind LIFT or RAW");
+  if (p.bc_kind == SPMC_BC_RAW && d.estimator != SPMC_EST_DIRECT)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "raw boundary data enters through the direct estimator only");
+  if (p.bc_kind != SPMC_BC_ZERO && (d.dim > 2 || d.walk_mode != 0))
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "boundary data: d <= 2 and the inside-ball walk only");
   HostProblem& H = plan->probs[instance];
   bool same_layout = H.set && H.n_int == p.n_intervals &&
                      std::equal(H.deg.begin(), H.deg.end(), p.degrees) &&
@@ -1321,6 +1360,7 @@ spmc_status spmc_set_problem(spmc_plan_t plan, int instance, const spmc_problem*
   H.ip.f_kind = p.f_kind; H.ip.ex_kind = p.ex_kind;
   for (int k = 0; k < 4; ++k) H.ip.fc[k] = p.f_coef[k];
   H.ip.f_scale = p.f_scale; H.ip.ex_beta = p.ex_beta;
+  H.ip.bc_kind = p.bc_kind;
   const int S = plan->S, n = d.n_space, D = d.dim;
   H.u0.assign(S, 0.0);
   H.u0_kind = p.u0_kind;
@@ -1375,7 +1415,9 @@ spmc_status spmc_iterate(spmc_plan_t plan, void* cuda_stream, int interval, int 
   if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "call spmc_begin_interval first");
   if (interval < 0 || interval >= (int)plan->rounds.size() || n_iter < 0) return fail(plan, SPMC_ERR_INVALID, "bad interval");
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  spmc_status st = run_iterations(plan, s, interval, n_iter);
+  spmc_status st = check_event_only(plan);
+  if (st != SPMC_OK) return st;
+  st = run_iterations(plan, s, interval, n_iter);
   if (st != SPMC_OK) return st;
   st = read_status(plan, s);
   if (st != SPMC_OK) return st;
@@ -1437,6 +1479,33 @@ spmc_status spmc_get_nodes(spmc_plan_t plan, void* cuda_stream, int instance, in
   return SPMC_OK;
 }
 
+spmc_status spmc_get_solution(spmc_plan_t plan, void* cuda_stream, int instance, int interval, double* dst) {
+  if (!plan) return SPMC_ERR_INVALID;
+  if (!plan->built) return fail(plan, SPMC_ERR_INVALID, "plan not built");
+  if (instance < 0 || instance >= plan->d.batch || !dst) return fail(plan, SPMC_ERR_INVALID, "bad instance");
+  const HostProblem& P = plan->probs[instance];
+  if (interval < 0 || interval >= P.n_int) return fail(plan, SPMC_ERR_INVALID, "bad interval");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int Mt = P.deg[interval], T = Mt + 1, S = plan->S;
+  // t_{n,l} of the interval's time nodes
+  std::vector<double> xi(T), tt(T);
+  time_nodes(plan->d.time_family, Mt, xi.data());
+  for (int l = 0; l < T; ++l) tt[l] = P.t[interval] + (xi[l] + 1.0) * 0.5 * (P.t[interval + 1] - P.t[interval]);
+  if (!plan->d_times) SPMC_CUDA(pmalloc(plan, (void**)&plan->d_times, sizeof(double) * 64));
+  SPMC_CUDA(cudaMemcpyAsync(plan->d_times, tt.data(), sizeof(double) * T, cudaMemcpyHostToDevice, s));
+  const long long tot = (long long)T * S;
+  const unsigned g = (unsigned)std::min(4096LL, (tot + 255) / 256);
+  const double* U = plan->d_U + plan->int_off[instance][interval];
+  const int n = plan->d.n_space;
+  if (plan->d.dim == 1) solution_kernel<1><<<g, 256, 0, s>>>(U, dst, plan->d_ip, instance, plan->d_times, plan->d_x, n, S, T);
+  else if (plan->d.dim == 2) solution_kernel<2><<<g, 256, 0, s>>>(U, dst, plan->d_ip, instance, plan->d_times, plan->d_x, n, S, T);
+  else solution_kernel<5><<<g, 256, 0, s>>>(U, dst, plan->d_ip, instance, plan->d_times, plan->d_x, n, S, T);
+  SPMC_CUDA(cudaGetLastError());
+  // the host vector of times must outlive the copy
+  SPMC_CUDA(cudaStreamSynchronize(s));
+  return SPMC_OK;
+}
+
 spmc_status spmc_set_nodes(spmc_plan_t plan, void* cuda_stream, int instance, int interval, const double* src) {
   if (!plan) return SPMC_ERR_INVALID;
   if (!plan->built) { spmc_status st = build(plan); if (st != SPMC_OK) return st; }
@@ -1454,6 +1523,9 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
   if (!plan->built || plan->params_dirty)
     return fail(plan, SPMC_ERR_INVALID, "spmc_iterate_static needs a built plan: call spmc_begin_interval first");
   if (plan->d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_iterate_static: dimensions 1 and 2 only");
+  for (const HostProblem& P : plan->probs)
+    if (P.ip.bc_kind != SPMC_BC_ZERO || plan->d.estimator != SPMC_EST_RESIDUAL)
+      return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_iterate_static: zero boundary data and the residual iteration only");
   if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   Round& rd = plan->rounds[interval];
@@ -1539,7 +1611,8 @@ spmc_status spmc_iterate_shard(spmc_plan_t plan, void* cuda_stream, int interval
     if (st == SPMC_OK) st = event_sweep(plan, s, rd, interval, iteration, lo, hi - lo);
     if (st != SPMC_OK) return st;
     eps_out_kernel<<<(unsigned)((hi - lo + 255) / 256), 256, 0, s>>>(plan->d_acc, eps_pairs, lo, hi,
-                                                                   1.0 / (double)plan->d.M, plan->d_status,
+                                                                   1.0 / (double)plan->d.M, plan->d_status, rd.d_tn,
+                                                                   plan->d_U, plan->S, plan->d.estimator,
                                                                    plan->d_abort);
     SPMC_CUDA(cudaGetLastError());
     int failed = 0;
@@ -1587,6 +1660,9 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
   const int R = (int)plan->rounds.size();
   if (d.tol > 0.0) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad needs a fixed iteration count (tol <= 0)");
   if (d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: dimensions 1 and 2 only");
+  for (const HostProblem& P : plan->probs)
+    if (P.ip.bc_kind != SPMC_BC_ZERO || d.estimator != SPMC_EST_RESIDUAL)
+      return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: zero boundary data and the residual iteration only");
   // workspace (first call)
   if (!plan->grad_ready) {
     pfree(plan, plan->d_lambda); pfree(plan, plan->d_Ubak); pfree(plan, plan->d_iter); pfree(plan, plan->d_gT);

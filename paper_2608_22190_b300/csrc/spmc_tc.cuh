@@ -59,6 +59,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity, 
   return false;
 }
 
+// named barrier `id` (1..15) over `n` threads (a multiple of 32)
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// named barrier `id` over `n` threads that also ORs `pred` over them
+__device__ __forceinline__ bool named_sync_or(int id, int n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\n"
+      "setp.ne.u32 p, %1, 0;\n"
+      "bar.red.or.pred q, %2, %3, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
 // Shared-memory matrix descriptor: no swizzle, base offset 0, version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -129,6 +148,13 @@ __host__ __device__ constexpr uint32_t kmajor_offset(int row, int k, int KC) {
 // accumulation in TMEM), which keeps about FP32 accuracy.  Each thread owns one
 // event = one TMEM lane: it writes its row of A, then contracts its TMEM row
 // with P(y) on the FP32 pipe.
+//
+// A block holds NT tile groups of 128 threads; each group has its own A rows,
+// TMEM accumulator (128 columns) and mbarrier, and works through the tiles of
+// the current slice segment independently of the others (named barriers), so
+// that while one group waits for its products the others write rows or finish
+// residuals.  The groups share the slice's B operand, rebuilt at segment
+// boundaries.
 template <int NMAX>
 struct TcGeom {
   static constexpr int K = NMAX;                 // contraction length (a multiple of 8)
@@ -136,16 +162,20 @@ struct TcGeom {
   static constexpr int KC = K / 4;               // 16-byte chunks per row
   static constexpr uint32_t SBO = KC * 128;      // bytes between 8-row groups
   static constexpr uint32_t LBO = 128;           // bytes between K-adjacent core matrices
-  static constexpr int A_BYTES = 128 * K * 4;
+  static constexpr int A_BYTES = 128 * K * 4;    // one tile's rows, hi or lo
   static constexpr int B_BYTES = N * K * 4;
-  static constexpr int TM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
-  static constexpr int SMEM = 4 * A_BYTES + 2 * B_BYTES + 64;   // A: two buffers x (hi, lo)
-  static constexpr int CHUNK = 4096;             // events per block
+  static constexpr int NT = 2;                   // tile groups per block
+  static constexpr int THREADS = 128 * NT;
+  static constexpr int TM_STRIDE = 128;          // TMEM columns per group (N <= 128)
+  static constexpr int TM_COLS = NT * TM_STRIDE;
+  static constexpr int BLOCKS_PER_SM = 512 / TM_COLS;
+  static constexpr int SMEM = 2 * NT * A_BYTES + 2 * B_BYTES + 8 * NT + 16;   // A, B, mbarriers, TMEM slot
+  static constexpr int CHUNK = 16384;            // events per block and step of the block loop
 };
 
-// row `row` of A: P_a(x), a < K (zero for a >= n), split hi / lo, into the
-// K-major tile pair (hi, lo)
-template <int NMAX>
+// row `row` of A: P_a(x), a < K (zero for a >= n unless FULL, n = K), split
+// hi / lo, into the K-major tile pair (hi, lo)
+template <int NMAX, bool FULL>
 __device__ __forceinline__ void write_a_row(unsigned char* hi, unsigned char* lo, int row, float x, int n) {
   constexpr int KC = TcGeom<NMAX>::KC;
   float pm2 = 1.f, pm1 = 2.f * x;
@@ -159,7 +189,7 @@ __device__ __forceinline__ void write_a_row(unsigned char* hi, unsigned char* lo
       if (a == 0) P = 1.f;
       else if (a == 1) P = 2.f * x;
       else { P = jac_ra<float>(a) * x * pm1 - jac_rb<float>(a) * pm2; pm2 = pm1; pm1 = P; }
-      tc::split_tf32(a < n ? P : 0.f, hv[q], lv[q]);
+      tc::split_tf32((FULL || a < n) ? P : 0.f, hv[q], lv[q]);
     }
     const uint32_t off = tc::kmajor_offset(row, 4 * c, KC);
     *reinterpret_cast<float4*>(hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
@@ -167,196 +197,196 @@ __device__ __forceinline__ void write_a_row(unsigned char* hi, unsigned char* lo
   }
 }
 
-// Events in fixed chunks of CHUNK (a chunk may span slices; each block
-// processes the slice segments of its chunk in turn).  Per segment the tiles
-// of 128 events run as a two-stage pipeline: while the tensor core works on
-// tile t, the threads build the A rows of tile t+1 in the other buffer; then
-// they read tile t's products from TMEM and finish its residuals.
-template <int NMAX>
-__global__ void __launch_bounds__(128) eval_events_tc_kernel(const long long* __restrict__ slice_node,
-                                                             const TimeNode* __restrict__ tn,
-                                                             const InstanceParams* __restrict__ ipt,
-                                                             const float* __restrict__ slices,
-                                                             const SliceInfo* __restrict__ sinfo,
-                                                             const unsigned int* __restrict__ starts,
-                                                             const Event<float>* __restrict__ events,
-                                                             unsigned long long* __restrict__ acc, int n, int S,
-                                                             long long n_slices, long long sl_stride, int half,
-                                                             double kappa_d,
-                                                             const unsigned long long* __restrict__ n_events_p,
-                                                             int* status, const int* __restrict__ abort) {
+// Events in chunks of CHUNK; block b takes chunks b, b + G, ... (G = grid
+// size, a multiple of the SM count), so the grid is one resident wave.  A chunk
+// may span slices: its slice segments are processed in turn, the tiles of a
+// segment dealt round-robin to the block's groups.
+template <int NMAX, bool FULL>
+__global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PER_SM) eval_events_tc_kernel(
+    const long long* __restrict__ slice_node, const TimeNode* __restrict__ tn, const InstanceParams* __restrict__ ipt,
+    const float* __restrict__ slices, const SliceInfo* __restrict__ sinfo, const unsigned int* __restrict__ starts,
+    const Event<float>* __restrict__ events, unsigned long long* __restrict__ acc, int n, int S, long long n_slices,
+    long long sl_stride, int half, double kappa_d, int direct, const unsigned long long* __restrict__ n_events_p,
+    int* status, const int* __restrict__ abort) {
   using Gm = TcGeom<NMAX>;
-  constexpr int K = Gm::K, N = Gm::N, KC = Gm::KC;
+  constexpr int K = Gm::K, N = Gm::N, KC = Gm::KC, NT = Gm::NT;
   extern __shared__ __align__(1024) unsigned char smraw[];
-  unsigned char* Abuf = smraw;                                  // [buffer][hi, lo]
-  unsigned char* Bhi = Abuf + 4 * Gm::A_BYTES;
+  unsigned char* Abuf = smraw;                                  // [group][hi, lo]
+  unsigned char* Bhi = Abuf + 2 * NT * Gm::A_BYTES;
   unsigned char* Blo = Bhi + Gm::B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + Gm::B_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + Gm::B_BYTES);   // [group]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + NT);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = tid >> 7, gt = tid & 127;
   if (*abort) return;
-  // the grid covers the event buffer's capacity; blocks past this batch's total return
   const unsigned long long n_events = *n_events_p;
-  const unsigned long long c0 = (unsigned long long)blockIdx.x * Gm::CHUNK;
-  if (c0 >= n_events) return;
-  const unsigned long long c1 = min(c0 + (unsigned long long)Gm::CHUNK, n_events);
+  if ((unsigned long long)blockIdx.x * Gm::CHUNK >= n_events) return;
 
   if (warp == 0) {
     tc::tmem_alloc(tslot, Gm::TM_COLS);
     tc::tmem_relinquish();
   }
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (gt == 0) tc::mbar_init(mbar + grp, 1);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tbase = *tslot;
-  const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tcol = *tslot + (uint32_t)(grp * Gm::TM_STRIDE);
+  const uint32_t lane_base = tcol + ((uint32_t)((warp & 3) * 32) << 16);
   constexpr uint32_t idesc = tc::idesc_tf32(128, N);
-  const uint32_t a0 = tc::smem_u32(Abuf), bHi = tc::smem_u32(Bhi), bLo = tc::smem_u32(Blo);
+  const uint32_t ah = tc::smem_u32(Abuf + 2 * grp * Gm::A_BYTES), al = ah + Gm::A_BYTES;
+  const uint32_t bHi = tc::smem_u32(Bhi), bLo = tc::smem_u32(Blo);
+  unsigned char* Ah = Abuf + 2 * grp * Gm::A_BYTES;
+  unsigned char* Al = Ah + Gm::A_BYTES;
   const float kappa = (float)kappa_d;
   uint32_t phase = 0;
-  bool ok = true;
+  bool ok = true;          // uniform over the group (a vote after every tile)
+  bool timed_out = false;  // this group's last MMA did not complete in time
 
-  unsigned long long pos = c0;
-  while (pos < c1 && ok) {
-    // the slice holding event pos: the last s with starts[s S] <= pos
-    long long lo_s = 0, hi_s = n_slices - 1;
-    while (lo_s < hi_s) {
-      const long long mid = (lo_s + hi_s + 1) >> 1;
-      if ((unsigned long long)starts[mid * S] <= pos) lo_s = mid; else hi_s = mid - 1;
-    }
-    const long long sidx = lo_s;
-    const unsigned long long s_end = (sidx + 1 < n_slices) ? (unsigned long long)starts[(sidx + 1) * S] : n_events;
-    const unsigned long long g1 = min(c1, s_end);
-
-    // B = [C | H | Lam C | C Lam] of this slice as N rows of K, split hi / lo
-    const float* src = slices + sidx * sl_stride;
-    for (int idx = tid; idx < N * K; idx += 128) {
-      const int nn = idx / K, a = idx - nn * K;
-      const int blk = nn / NMAX, b = nn - blk * NMAX;
-      float v = 0.f;
-      if (a < n && b < n) {
-        const float c = src[a * NMAX + b];
-        if (blk == 0) v = c;
-        else if (blk == 1) v = src[half + a * NMAX + b];
-        else if (blk == 2) v = jac_lam<float>(a) * c;
-        else v = c * jac_lam<float>(b);
+  for (unsigned long long c0 = (unsigned long long)blockIdx.x * Gm::CHUNK; c0 < n_events;
+       c0 += (unsigned long long)gridDim.x * Gm::CHUNK) {
+    const unsigned long long c1 = min(c0 + (unsigned long long)Gm::CHUNK, n_events);
+    unsigned long long pos = c0;
+    while (pos < c1) {
+      // the slice holding event pos: the last s with starts[s S] <= pos
+      long long lo_s = 0, hi_s = n_slices - 1;
+      while (lo_s < hi_s) {
+        const long long mid = (lo_s + hi_s + 1) >> 1;
+        if ((unsigned long long)starts[mid * S] <= pos) lo_s = mid; else hi_s = mid - 1;
       }
-      float h, l;
-      tc::split_tf32(v, h, l);
-      const uint32_t off = tc::kmajor_offset(nn, a, KC);
-      *reinterpret_cast<float*>(Bhi + off) = h;
-      *reinterpret_cast<float*>(Blo + off) = l;
-    }
-    const long long ti = slice_node[sidx];
-    const TimeNode node = tn[ti];
-    const InstanceParams ip = ipt[node.inst];
-    const SliceInfo si = sinfo[sidx];
-    const float Tt = (float)si.Tt, dTt = (float)si.dTt;
-    const unsigned int key0 = (unsigned int)(sidx * S);
+      const long long sidx = lo_s;
+      const unsigned long long s_end = (sidx + 1 < n_slices) ? (unsigned long long)starts[(sidx + 1) * S] : n_events;
+      const unsigned long long g1 = min(c1, s_end);
 
-    // tile 0 of the segment
-    const int n_tiles = (int)((g1 - pos + 127) / 128);
-    float4 cur = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
-    bool cur_has = pos + tid < g1;
-    if (cur_has) cur = *reinterpret_cast<const float4*>(events + pos + tid);
-    write_a_row<NMAX>(Abuf, Abuf + Gm::A_BYTES, tid, cur.x, n);
-    tc::fence_async_smem();
-    __syncthreads();
-    auto issue = [&](int buf) {
-      tc::fence_after();
-      const uint32_t ah = a0 + (uint32_t)(2 * buf) * Gm::A_BYTES, al = ah + Gm::A_BYTES;
-#pragma unroll
-      for (int s = 0; s < K / 8; ++s) {
-        const uint32_t ko = (uint32_t)s * 256;   // 8 TF32 = two core matrices along K
-        tc::mma_tf32(tbase, tc::sdesc(al + ko, Gm::LBO, Gm::SBO), tc::sdesc(bHi + ko, Gm::LBO, Gm::SBO), idesc,
-                     s > 0 ? 1u : 0u);
-        tc::mma_tf32(tbase, tc::sdesc(ah + ko, Gm::LBO, Gm::SBO), tc::sdesc(bLo + ko, Gm::LBO, Gm::SBO), idesc, 1u);
-        tc::mma_tf32(tbase, tc::sdesc(ah + ko, Gm::LBO, Gm::SBO), tc::sdesc(bHi + ko, Gm::LBO, Gm::SBO), idesc, 1u);
-      }
-      tc::mma_commit(mbar);
-    };
-    if (tid == 0) issue(0);
-
-    for (int t = 0; t < n_tiles; ++t) {
-      // stage 1: A rows of tile t+1 (other buffer) while the MMA of tile t runs
-      float4 nxt = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
-      bool nxt_has = false;
-      if (t + 1 < n_tiles) {
-        const unsigned long long i = pos + (unsigned long long)(t + 1) * 128 + tid;
-        nxt_has = i < g1;
-        if (nxt_has) nxt = *reinterpret_cast<const float4*>(events + i);
-        const int b = (t + 1) & 1;
-        write_a_row<NMAX>(Abuf + 2 * b * Gm::A_BYTES, Abuf + (2 * b + 1) * Gm::A_BYTES, tid, nxt.x, n);
-      }
-      // P_b(y) of tile t
-      const float y0 = cur.x, y1 = cur.y;
-      float Py[NMAX];
-      {
-        float pm2 = 1.f, pm1 = 2.f * y1;
-#pragma unroll
-        for (int b = 0; b < NMAX; ++b) {
-          float P;
-          if (b == 0) P = 1.f;
-          else if (b == 1) P = 2.f * y1;
-          else { P = jac_ra<float>(b) * y1 * pm1 - jac_rb<float>(b) * pm2; pm2 = pm1; pm1 = P; }
-          Py[b] = b < n ? P : 0.f;
+      // every group is done with the previous segment's B; a failed group stops the block
+      if (__syncthreads_or(!ok)) { ok = false; break; }
+      // B = [C | H | Lam C | C Lam] of this slice as N rows of K, split hi / lo
+      const float* src = slices + sidx * sl_stride;
+      for (int idx = tid; idx < N * K; idx += Gm::THREADS) {
+        const int nn = idx / K, a = idx - nn * K;
+        const int blk = nn / NMAX, b = nn - blk * NMAX;
+        float v = 0.f;
+        if (FULL || (a < n && b < n)) {
+          const float c = src[a * NMAX + b];
+          if (blk == 0) v = c;
+          else if (blk == 1) v = src[half + a * NMAX + b];
+          else if (blk == 2) v = jac_lam<float>(a) * c;
+          else v = c * jac_lam<float>(b);
         }
+        float h, l;
+        tc::split_tf32(v, h, l);
+        const uint32_t off = tc::kmajor_offset(nn, a, KC);
+        *reinterpret_cast<float*>(Bhi + off) = h;
+        *reinterpret_cast<float*>(Blo + off) = l;
       }
-      // stage 2: products of tile t
-      if (!tc::mbar_wait_bounded(mbar, phase)) ok = false;
-      phase ^= 1u;
-      tc::fence_after();
-      float sv[4];
-#pragma unroll
-      for (int blk = 0; blk < 4; ++blk) {
-        float v[NMAX];
-#pragma unroll
-        for (int c8 = 0; c8 < NMAX / 8; ++c8) tc::tmem_ld8(lane_base + (uint32_t)(blk * NMAX + c8 * 8), v + 8 * c8);
-        tc::tmem_ld_wait();
-        float s = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int q = 0; q < NMAX; q += 2) {
-          s = fmaf(v[q], Py[q], s);
-          s2 = fmaf(v[q + 1], Py[q + 1], s2);
-        }
-        sv[blk] = s + s2;
-      }
-      __int128 val = 0;
-      const unsigned int key = cur_has ? __float_as_uint(cur.w) : 0xffffffffu;
-      if (cur_has) {
-        const float ox = 1.f - y0 * y0, oy = 1.f - y1 * y1;
-        const float u = ox * oy * sv[0];
-        const float G = ox * oy * sv[1] - kappa * (oy * sv[2] + ox * sv[3]);
-        const float yy[2] = {y0, y1};
-        const float res = reaction<float>(ip, u) + source<2, float>(ip, kappa, yy, Tt, dTt) + G;
-        if (!fix_from_float(cur.z * res, val)) atomicOr(status, 1);
-      }
-      // per-node sums (exact): events are sorted by key, so equal keys are adjacent lanes
-      val = warp_run_sum(val, key, (unsigned int)lane);
-      const unsigned int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-      if (cur_has && (lane == 0 || kprev != key)) fix_atomic_add(acc + 4 * (ti * S + (long long)(key - key0)), val);
       tc::fence_async_smem();
-      tc::fence_before();
-      const bool all_ok = !__syncthreads_or(!ok);
-      if (!all_ok) { ok = false; break; }
-      if (t + 1 < n_tiles && tid == 0) issue((t + 1) & 1);
-      cur = nxt;
-      cur_has = nxt_has;
+      __syncthreads();
+      const long long ti = slice_node[sidx];
+      const TimeNode node = tn[ti];
+      const InstanceParams ip = ipt[node.inst];
+      const SliceInfo si = sinfo[sidx];
+      const float Tt = (float)si.Tt, dTt = (float)si.dTt, tau = (float)si.tau;
+      const long long node0 = ti * S - (long long)(sidx * S);   // node index = node0 + key
+
+      const int n_tiles = (int)((g1 - pos + 127) / 128);
+      for (int t = grp; t < n_tiles; t += NT) {
+        const unsigned long long i = pos + (unsigned long long)t * 128 + gt;
+        const bool has = i < g1;
+        float4 ev = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+        if (has) ev = *reinterpret_cast<const float4*>(events + i);
+        write_a_row<NMAX, FULL>(Ah, Al, gt, ev.x, n);
+        tc::fence_async_smem();
+        tc::named_sync(1 + grp, 128);
+        if (gt == 0) {
+          tc::fence_after();
+#pragma unroll
+          for (int s = 0; s < K / 8; ++s) {
+            const uint32_t ko = (uint32_t)s * 256;   // 8 TF32 = two core matrices along K
+            tc::mma_tf32(tcol, tc::sdesc(al + ko, Gm::LBO, Gm::SBO), tc::sdesc(bHi + ko, Gm::LBO, Gm::SBO), idesc,
+                         s > 0 ? 1u : 0u);
+            tc::mma_tf32(tcol, tc::sdesc(ah + ko, Gm::LBO, Gm::SBO), tc::sdesc(bLo + ko, Gm::LBO, Gm::SBO), idesc,
+                         1u);
+            tc::mma_tf32(tcol, tc::sdesc(ah + ko, Gm::LBO, Gm::SBO), tc::sdesc(bHi + ko, Gm::LBO, Gm::SBO), idesc,
+                         1u);
+          }
+          tc::mma_commit(mbar + grp);
+        }
+        // P_b(y) while the products run
+        const float y0 = ev.x, y1 = ev.y;
+        float Py[NMAX];
+        {
+          float pm2 = 1.f, pm1 = 2.f * y1;
+#pragma unroll
+          for (int b = 0; b < NMAX; ++b) {
+            float P;
+            if (b == 0) P = 1.f;
+            else if (b == 1) P = 2.f * y1;
+            else { P = jac_ra<float>(b) * y1 * pm1 - jac_rb<float>(b) * pm2; pm2 = pm1; pm1 = P; }
+            Py[b] = (FULL || b < n) ? P : 0.f;
+          }
+        }
+        const bool done = tc::mbar_wait_bounded(mbar + grp, phase);
+        phase ^= 1u;
+        tc::fence_after();
+        float sv[4];
+#pragma unroll
+        for (int blk = 0; blk < 4; ++blk) {
+          float v[NMAX];
+#pragma unroll
+          for (int c8 = 0; c8 < NMAX / 8; ++c8) tc::tmem_ld8(lane_base + (uint32_t)(blk * NMAX + c8 * 8), v + 8 * c8);
+          tc::tmem_ld_wait();
+          float s = 0.f, s2 = 0.f;
+#pragma unroll
+          for (int q = 0; q < NMAX; q += 2) {
+            s = fmaf(v[q], Py[q], s);
+            s2 = fmaf(v[q + 1], Py[q + 1], s2);
+          }
+          sv[blk] = s + s2;
+        }
+        int L[5] = {0, 0, 0, 0, 0};
+        const unsigned int key = has ? __float_as_uint(ev.w) : 0xffffffffu;
+        if (has) {
+          const float ox = 1.f - y0 * y0, oy = 1.f - y1 * y1;
+          const float u = ox * oy * sv[0];
+          const float G = ox * oy * sv[1] - kappa * (oy * sv[2] + ox * sv[3]);
+          const float yy[2] = {y0, y1};
+          float term;
+          if (si.kind == 0) {
+            float res = forcing<2, float>(ip, kappa, yy, Tt, dTt, tau, u);
+            if (!direct) res += G;
+            term = ev.z * res;
+          } else if (si.kind == 1) {
+            term = u;   // the direct estimator's initial term u*(X, t_{n-1})
+          } else {
+            term = exact_bv<2, float>(ip, yy, (float)exp(-ip.ex_beta * (double)ev.z), ev.z);   // g(X, t)
+          }
+          if (!fix_limbs_float(term, L)) atomicOr(status, 1);
+        }
+        // per-node sums (exact): events are sorted by key, so each key's lanes
+        // form one run; each run's limbs are summed by a warp reduction
+        const unsigned int peers = __match_any_sync(0xffffffffu, key);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) L[k] = __reduce_add_sync(peers, L[k]);
+        if (done && has && lane == __ffs(peers) - 1)
+          fix_atomic_add(acc + 4 * (node0 + (long long)key), fix_from_limbs(L));
+        tc::fence_before();
+        // TMEM read and A free before the group's next tile; the group agrees on a time-out
+        if (tc::named_sync_or(1 + grp, 128, !done)) { ok = false; timed_out = true; break; }
+      }
+      pos = g1;
     }
-    pos = g1;
+    if (__syncthreads_or(!ok)) { ok = false; break; }
   }
-  if (!ok) {
-    // an MMA did not complete in time: report, give it one more bounded wait, stop
-    if (tid == 0) atomicOr(status, 8);
-    tc::mbar_wait_bounded(mbar, phase ^ 1u);
+  if (timed_out) {
+    // an MMA of this group did not complete in time: report, give it one more bounded wait
+    if (gt == 0) atomicOr(status, 8);
+    tc::mbar_wait_bounded(mbar + grp, phase ^ 1u);
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tbase, Gm::TM_COLS);
+    tc::tmem_dealloc(*tslot, Gm::TM_COLS);
   }
 }
 

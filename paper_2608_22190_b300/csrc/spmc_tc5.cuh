@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) slice5_tc_kernel(const TimeNode* __restri
     const InstanceParams P = ip[node.inst];
     SliceInfo si;
     si.tau = tau;
+    si.kind = 0;
     if (P.ex_kind == 3) { si.Tt = 1.0 + tau + tau * tau; si.dTt = 1.0 + 2.0 * tau; }
     else if (P.ex_kind == 1 || P.ex_kind == 2) { si.Tt = exp(-P.ex_beta * tau); si.dTt = -P.ex_beta * si.Tt; }
     else { si.Tt = 0.0; si.dTt = 0.0; }

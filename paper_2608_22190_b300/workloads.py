@@ -17,6 +17,11 @@ Workloads (sizes as the benchmarks state them; Section 4 examples they stand in 
       M = 32768, K = 8; 256 instances, s ~ U[0.5, 2], N ~ U{8..16}  (Ex. 3 shape)
   w4  5-D, u = e^{-t} prod cos(pi x_e / 2), f = -u^3 + source, T = 0.5,
       8 JG nodes per axis x 8 LGL, M = 16384, K = 6              (Ex. 4 shape)
+  w6  2-D non-homogeneous boundary data, u = e^{-0.1 t} prod cos(pi (x_e - 0.3) / 3)
+      (different non-zero values on opposite faces), f = sin u + source, lifted,
+      T = 20 in 20 intervals of h = 1, 24 x 24 JG x 16 LGL, M = 65536, K = 8
+  w7  1-D long time for the direct estimator and the classical comparison,
+      u = e^{-t/4} sin(pi x) + t/2 (boundary data t/2), f = 0 + source, kappa = 1/(4 pi^2)
   w5  adjoint: 2-D u_t = 0.01 Delta u + a (u - u^3), T = 5 in 10 intervals,
       16 x 16 JG x 12 LGL, M = 16384, u0 = sum_{i,j<8} c_ij phi_i phi_j with
       c_ij = z_ij / (1+i+j)^2, z ~ N(0,1), scaled down to max |u0| = 1 where the
@@ -34,7 +39,8 @@ import numpy as np
 # enums shared by name with the C-ABI header (values fixed there)
 TIME_LGL, TIME_RADAU_LEFT = 0, 1
 F_POLY3, F_SIN = 0, 1
-EX_NONE, EX_SIN, EX_COSHALF, EX_POLY = 0, 1, 2, 3
+EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS = 0, 1, 2, 3, 4, 5
+BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
 
 
 @dataclass
@@ -48,6 +54,7 @@ class Instance:
     ex_beta: float = 1.0
     u0_kind: str = "exact"          # "exact" (closed form at t=0), "singular", "phi_coef"
     u0_coef: Optional[np.ndarray] = None   # phi_i phi_j coefficients (u0_kind == "phi_coef")
+    bc_kind: int = BC_ZERO          # boundary data: zero, lifted, or raw (direct estimator)
 
 
 @dataclass
@@ -150,6 +157,21 @@ def uniform_points(n: int, dim: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, dim))
 
 
+def w6(M: int = 65536, K: int = 8, seed: int = 0, n_space: int = 24, degree: int = 15,
+       n_intervals: int = 20, h: float = 1.0) -> Workload:
+    inst = Instance(t_breaks=uniform_mesh(h * n_intervals, n_intervals), degrees=np.full(n_intervals, degree),
+                    f_kind=F_SIN, f_coef=(0, 0, 0, 0), ex_kind=EX_COSTHIRD, ex_beta=0.1, bc_kind=BC_LIFT)
+    return Workload("w6-2d-boundary-data", 2, n_space, TIME_LGL, M, K, seed=seed, n_ref=160, instances=[inst])
+
+
+def w7(M: int = 16384, K: int = 4, seed: int = 0, n_space: int = 14, degree: int = 8, T: float = 20.0,
+       n_intervals: int = 20, bc_kind: int = BC_RAW) -> Workload:
+    inst = Instance(t_breaks=uniform_mesh(T, n_intervals), degrees=np.full(n_intervals, degree),
+                    f_coef=(0, 0, 0, 0), ex_kind=EX_SINPLUS, ex_beta=0.25, bc_kind=bc_kind)
+    return Workload("w7-1d-direct-long-time", 1, n_space, TIME_LGL, M, K, kappa=0.25 / np.pi ** 2, seed=seed,
+                    n_ref=40, instances=[inst])
+
+
 def u0_nodal(inst: Instance, grid: np.ndarray) -> np.ndarray:
     """Initial values at the spatial nodes (grid: (S, d) coordinates): the
     closed form at t = 0 of the manufactured solution, or the singular profile
@@ -162,6 +184,10 @@ def u0_nodal(inst: Instance, grid: np.ndarray) -> np.ndarray:
         return np.prod(np.cos(0.5 * np.pi * grid), axis=1)
     if inst.ex_kind == EX_POLY:
         return np.prod((1.0 - grid ** 2) * (1.0 + grid), axis=1)
+    if inst.ex_kind == EX_COSTHIRD:
+        return np.prod(np.cos(np.pi * (grid - 0.3) / 3.0), axis=1)
+    if inst.ex_kind == EX_SINPLUS:
+        return np.prod(np.sin(np.pi * grid), axis=1)
     raise ValueError("instance has no closed-form initial condition")
 
 
@@ -186,4 +212,9 @@ def exact_block(wl: Workload, inst: Instance, grid: np.ndarray, interval: int) -
         return np.exp(-inst.ex_beta * t)[:, None] * np.prod(np.cos(0.5 * np.pi * grid), axis=1)[None, :]
     if inst.ex_kind == EX_POLY:
         return (1.0 + t + t * t)[:, None] * np.prod((1.0 - grid ** 2) * (1.0 + grid), axis=1)[None, :]
+    if inst.ex_kind == EX_COSTHIRD:
+        return np.exp(-inst.ex_beta * t)[:, None] * np.prod(np.cos(np.pi * (grid - 0.3) / 3.0), axis=1)[None, :]
+    if inst.ex_kind == EX_SINPLUS:
+        return (np.exp(-inst.ex_beta * t)[:, None] * np.prod(np.sin(np.pi * grid), axis=1)[None, :]
+                + 0.5 * t[:, None])
     raise ValueError("instance has no closed form")
