@@ -350,6 +350,7 @@ def run_ours(args):
         line["batch_w3"] = batch_leg(args)
         line["w4_5d"] = w4_leg(args, peaks)
         line["w5_adjoint"] = w5_leg(args)
+        line["boundary"] = boundary_leg(args)
         line["cpu_baseline"] = cpu_baseline(wl)
     plan.close()
     if rank == 0:
@@ -423,18 +424,19 @@ def fp64_leg(args):
                        "step": "one FP64 iteration of interval 1", "l2": "flushed before the timed region"}}
 
 
-def hp_time_to_tol(wl, prec, tol, kmax, accel="none"):
+def hp_time_to_tol(wl, prec, tol, kmax, accel="none", estimator=0):
     """Time until every node of every interval is within tol of the closed form:
     the hp solve interval by interval (hand-off, then iterations until the
     interval's L-inf error <= tol, at most kmax).  GPU time of the hand-offs and
-    iterations (CUDA events around each call); the error is read between calls,
-    outside the events."""
+    iterations (CUDA events around each call); the error of the solution u (the
+    nodal values, plus the lifting for lifted boundary data) is read between
+    calls, outside the events."""
     import numpy as np
     import torch
     from paper_2608_22190_b300 import workloads as W
     from paper_2608_22190_b300.api import Plan
     inst = wl.instances[0]
-    plan = Plan.from_workload(wl, precision=prec)
+    plan = Plan.from_workload(wl, precision=prec, estimator=estimator)
     plan.set_acceleration(accel)
     grid = plan.node_grid()
     ms_total, iters, errs = 0.0, [], []
@@ -454,7 +456,7 @@ def hp_time_to_tol(wl, prec, tol, kmax, accel="none"):
         while k < kmax and err > tol:
             ms_total += timed(lambda: plan.iterate(r, 1))
             k += 1
-            err = float(np.abs(plan.get_nodes(0, r).cpu().numpy() - ex).max())
+            err = float(np.abs(plan.get_solution(0, r).cpu().numpy() - ex).max())
         iters.append(k)
         errs.append(err)
     plan.close()
@@ -622,6 +624,60 @@ def w4_leg(args, peaks, tol=1e-6):
                                                            "bf16_tflops_sustained" in peaks else
                                                            "fallback 1400 TFLOP/s sustained BF16 (of fallback)")
                                            + " x nominal TF32/BF16 1.1/2.25"}}
+    return out
+
+
+def boundary_leg(args, tol=1e-6):
+    """Non-homogeneous boundary data and the direct estimator (Eq. Phi_ast).
+      w6_lifted_M2048: the 2-D boundary-data workload (lifted, f = sin u), mixed,
+        all 20 intervals, time to L-inf 1e-6 of u = w + G;
+      w6_lifted_interval: one interval (hand-off + K = 8 iterations) at the full
+        M = 65536, node-samples/s;
+      w7_*: the 1-D long-time problem (T = 20, f = sin u, boundary data t/2),
+        FP64, M = 16384: the hp partition of 20 intervals with the residual
+        iteration (lifted data) and with the direct estimator (raw data), and the
+        classical single-interval solve over [0, 20] with each (degree 16): the
+        L-inf error of u at every node after K iterations per interval."""
+    import numpy as np
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    out = {}
+    out["w6_lifted_M2048"] = hp_time_to_tol(W.w6(M=2048), L.MIXED, tol, 16)
+    wl = W.w6(M=65536, K=8, n_intervals=1)
+    plan = Plan.from_workload(wl, precision=L.MIXED)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.begin_interval(0)
+    plan.iterate(0, 1)    # sizes the event buffer
+    plan.begin_interval(0)
+    a.record()
+    plan.begin_interval(0)
+    plan.iterate(0, 8)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    plan.close()
+    out["w6_lifted_interval"] = {"value": node_samples_per_interval(wl, 0) / (ms / 1e3), "unit": "node-samples/s",
+                                 "ms": ms, "M": wl.M, "K": 8}
+
+    def solve_err(wl, estimator):
+        plan = Plan.from_workload(wl, precision=L.FP64, estimator=estimator)
+        grid = plan.node_grid()
+        t0 = time.time()
+        plan.solve()
+        torch.cuda.synchronize()
+        wall = time.time() - t0
+        errs = [float(np.abs(plan.get_solution(0, m).cpu().numpy()
+                             - W.exact_block(wl, wl.instances[0], grid, m)).max())
+                for m in range(len(wl.instances[0].degrees))]
+        plan.close()
+        return {"linf": max(errs), "linf_last_interval": errs[-1], "wall_s": wall, "M": wl.M, "K": wl.K,
+                "intervals": len(errs)}
+    out["w7_hp_residual_lifted"] = solve_err(W.w7(bc_kind=W.BC_LIFT), 0)
+    out["w7_hp_direct_raw"] = solve_err(W.w7(bc_kind=W.BC_RAW), 1)
+    out["w7_classical_residual_lifted"] = solve_err(W.w7(bc_kind=W.BC_LIFT, n_intervals=1, degree=16, K=16), 0)
+    out["w7_classical_direct_raw"] = solve_err(W.w7(bc_kind=W.BC_RAW, n_intervals=1, degree=16, K=16), 1)
     return out
 
 

@@ -203,7 +203,7 @@ void slice_geometry(spmc_plan_t plan) {
 // every instance is set.
 spmc_status build(spmc_plan_t plan) {
   const spmc_plan_desc& d = plan->d;
-  const int S = plan->S, n = d.n_space, B = d.batch;
+  const int S = plan->S, B = d.batch;
   for (int i = 0; i < B; ++i)
     if (!plan->probs[i].set) return fail(plan, SPMC_ERR_INVALID, "instance " + std::to_string(i) + " not set");
   // nodal layout: instance-major, interval blocks of (M_n+1) x S

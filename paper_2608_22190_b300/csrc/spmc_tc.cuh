@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
     int* status, const int* __restrict__ abort) {
   using Gm = TcGeom<NMAX>;
   constexpr int K = Gm::K, N = Gm::N, KC = Gm::KC, NT = Gm::NT;
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  unsigned char* Abuf = smraw;                                  // [group][hi, lo]
+  extern __shared__ __align__(1024) unsigned char sm_tc[];
+  unsigned char* Abuf = sm_tc;                                 // [group][hi, lo]
   unsigned char* Bhi = Abuf + 2 * NT * Gm::A_BYTES;
   unsigned char* Blo = Bhi + Gm::B_BYTES;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + Gm::B_BYTES);   // [group]
@@ -289,11 +289,19 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
       const long long node0 = ti * S - (long long)(sidx * S);   // node index = node0 + key
 
       const int n_tiles = (int)((g1 - pos + 127) / 128);
-      for (int t = grp; t < n_tiles; t += NT) {
+      // the group's next event is loaded one tile ahead
+      auto load_event = [&](int t, float4& e) {
         const unsigned long long i = pos + (unsigned long long)t * 128 + gt;
-        const bool has = i < g1;
-        float4 ev = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
-        if (has) ev = *reinterpret_cast<const float4*>(events + i);
+        e = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+        if (t < n_tiles && i < g1) e = *reinterpret_cast<const float4*>(events + i);
+        return t < n_tiles && i < g1;
+      };
+      float4 ev_next;
+      bool has_next = load_event(grp, ev_next);
+      for (int t = grp; t < n_tiles; t += NT) {
+        const float4 ev = ev_next;
+        const bool has = has_next;
+        has_next = load_event(t + NT, ev_next);
         write_a_row<NMAX, FULL>(Ah, Al, gt, ev.x, n);
         tc::fence_async_smem();
         tc::named_sync(1 + grp, 128);
@@ -363,12 +371,18 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
           if (!fix_limbs_float(term, L)) atomicOr(status, 1);
         }
         // per-node sums (exact): events are sorted by key, so each key's lanes
-        // form one run; each run's limbs are summed by a warp reduction
-        const unsigned int peers = __match_any_sync(0xffffffffu, key);
+        // form one run [start, end) of the warp, found from the run heads; each
+        // run's limbs are summed by a warp reduction over its lanes
+        const unsigned int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+        const unsigned int heads = __ballot_sync(0xffffffffu, lane == 0 || kprev != key);
+        const unsigned int upto = 0xffffffffu >> (31 - lane);          // lanes 0..lane
+        const int start = 31 - __clz(heads & upto);
+        const unsigned int after = heads & ~upto;
+        const unsigned int below_end = after ? (1u << (__ffs(after) - 1)) - 1u : 0xffffffffu;
+        const unsigned int peers = below_end & ~((1u << start) - 1u);
 #pragma unroll
         for (int k = 0; k < 5; ++k) L[k] = __reduce_add_sync(peers, L[k]);
-        if (done && has && lane == __ffs(peers) - 1)
-          fix_atomic_add(acc + 4 * (node0 + (long long)key), fix_from_limbs(L));
+        if (done && has && lane == start) fix_atomic_add(acc + 4 * (node0 + (long long)key), fix_from_limbs(L));
         tc::fence_before();
         // TMEM read and A free before the group's next tile; the group agrees on a time-out
         if (tc::named_sync_or(1 + grp, 128, !done)) { ok = false; timed_out = true; break; }

@@ -21,7 +21,8 @@ Workloads (sizes as the benchmarks state them; Section 4 examples they stand in 
       (different non-zero values on opposite faces), f = sin u + source, lifted,
       T = 20 in 20 intervals of h = 1, 24 x 24 JG x 16 LGL, M = 65536, K = 8
   w7  1-D long time for the direct estimator and the classical comparison,
-      u = e^{-t/4} sin(pi x) + t/2 (boundary data t/2), f = 0 + source, kappa = 1/(4 pi^2)
+      u = e^{-t/4} sin(pi x) + t/2 (boundary data t/2), f = sin u + source, kappa = 1/(4 pi^2),
+      T = 20 in 20 intervals of degree 8 (or one interval: the classical single solve)
   w5  adjoint: 2-D u_t = 0.01 Delta u + a (u - u^3), T = 5 in 10 intervals,
       16 x 16 JG x 12 LGL, M = 16384, u0 = sum_{i,j<8} c_ij phi_i phi_j with
       c_ij = z_ij / (1+i+j)^2, z ~ N(0,1), scaled down to max |u0| = 1 where the
@@ -167,7 +168,7 @@ def w6(M: int = 65536, K: int = 8, seed: int = 0, n_space: int = 24, degree: int
 def w7(M: int = 16384, K: int = 4, seed: int = 0, n_space: int = 14, degree: int = 8, T: float = 20.0,
        n_intervals: int = 20, bc_kind: int = BC_RAW) -> Workload:
     inst = Instance(t_breaks=uniform_mesh(T, n_intervals), degrees=np.full(n_intervals, degree),
-                    f_coef=(0, 0, 0, 0), ex_kind=EX_SINPLUS, ex_beta=0.25, bc_kind=bc_kind)
+                    f_kind=F_SIN, f_coef=(0, 0, 0, 0), ex_kind=EX_SINPLUS, ex_beta=0.25, bc_kind=bc_kind)
     return Workload("w7-1d-direct-long-time", 1, n_space, TIME_LGL, M, K, kappa=0.25 / np.pi ** 2, seed=seed,
                     n_ref=40, instances=[inst])
 
