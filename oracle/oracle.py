@@ -34,7 +34,7 @@ class Problem(C.Structure):
         ("f_kind", C.c_int), ("f_coef", C.c_double * 4), ("f_scale", C.c_double),
         ("ex_kind", C.c_int), ("ex_beta", C.c_double), ("n_threads", C.c_int),
         ("walk_mode", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int), ("n_sub", C.c_int),
-        ("bc_kind", C.c_int), ("estimator", C.c_int),
+        ("bc_kind", C.c_int), ("estimator", C.c_int), ("alpha", C.c_double),
     ]
 
 
@@ -75,6 +75,14 @@ def lib():
             "orc_exact": (C.c_double, [P, D, C.c_double]),
             "orc_source": (C.c_double, [P, D, C.c_double]),
             "orc_lift": (None, [P, D, C.c_double, D, D, D]),
+            "orc_jacobi_aa": (None, [C.c_int, C.c_double, C.c_double, D]),
+            "orc_gj_nodes": (None, [C.c_int, C.c_double, D, D]),
+            "orc_frac_lambda": (C.c_double, [C.c_double, C.c_int]),
+            "orc_space_nodes": (None, [P, D, D]),
+            "orc_space_analysis_pb": (None, [P, D]),
+            "orc_ibeta": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+            "orc_ibeta_inv": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+            "orc_stable_jump": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "orc_reconstruct": (None, [P, C.c_int, C.c_double, D, D, D]),
             "orc_eval": (None, [P, C.c_int, D, D, D, C.c_double, D, D, D]),
             "orc_residual": (C.c_double, [P, C.c_int, C.c_double, C.c_double, D, D, D, C.c_double]),
@@ -112,6 +120,8 @@ F_POLY3, F_SIN = 0, 1
 EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS = 0, 1, 2, 3, 4, 5
 BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
 EST_RESIDUAL, EST_DIRECT = 0, 1
+EX_FRAC_SIN, EX_FRAC_POLY = 6, 7
+WALK_BALLS, WALK_FIXED, WALK_STABLE = 0, 1, 2
 TIME_LGL, TIME_RADAU_LEFT = 0, 1
 
 
@@ -138,6 +148,7 @@ class Spec:
     n_sub: int = 4
     bc_kind: int = 0             # 0 g = 0; 1 lifted (Gordon-Hall); 2 g at absorption (direct estimator)
     estimator: int = 0           # 0 residual iteration; 1 direct estimator S_i (Eq. Phi_ast)
+    alpha: float = 0.0           # 0: -kappa Delta; (0, 2): kappa (-Delta)^{alpha/2} (d = 1, walk_mode 2)
 
     def struct(self) -> Problem:
         p = Problem()
@@ -148,7 +159,7 @@ class Spec:
             p.f_coef[i] = c
         p.n_threads = self.n_threads
         p.walk_mode, p.shell, p.max_steps, p.n_sub = self.walk_mode, self.shell, self.max_steps, self.n_sub
-        p.bc_kind, p.estimator = self.bc_kind, self.estimator
+        p.bc_kind, p.estimator, p.alpha = self.bc_kind, self.estimator, self.alpha
         return p
 
 
@@ -181,6 +192,41 @@ def radau_left_nodes(M):
 
 def time_nodes(family, M):
     return lgl_nodes(M) if family == TIME_LGL else radau_left_nodes(M)
+
+
+def jacobi_aa(m, a, x):
+    out = np.zeros(m + 1)
+    lib().orc_jacobi_aa(m, float(a), float(x), _dp(out))
+    return out
+
+
+def gj_nodes(n, a):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().orc_gj_nodes(n, float(a), _dp(x), _dp(w))
+    return x, w
+
+
+def frac_lambda(alpha, p):
+    return lib().orc_frac_lambda(float(alpha), int(p))
+
+
+def space_analysis_spec(spec):
+    A = np.zeros((spec.n_space, spec.n_space))
+    p = spec.struct()
+    lib().orc_space_analysis_pb(C.byref(p), _dp(A))
+    return A
+
+
+def ibeta(x, p, q):
+    return lib().orc_ibeta(float(x), float(p), float(q))
+
+
+def ibeta_inv(w, p, q):
+    return lib().orc_ibeta_inv(float(w), float(p), float(q))
+
+
+def stable_jump(r, alpha, omega):
+    return lib().orc_stable_jump(float(r), float(alpha), float(omega))
 
 
 def space_analysis(n):
@@ -377,7 +423,9 @@ def solve_tangent(spec: Spec, t_breaks, degrees, K, u0, du0, ds):
 
 def space_nodes_grid(spec: Spec):
     """Coordinates of all spatial nodes, shape (S, d), x_1 fastest."""
-    x, _ = jg11_nodes(spec.n_space)
+    x, w = np.zeros(spec.n_space), np.zeros(spec.n_space)
+    p = spec.struct()
+    lib().orc_space_nodes(C.byref(p), _dp(x), _dp(w))
     grids = np.meshgrid(*([x] * spec.dim), indexing="ij")
     # linear index j = j1 + n*(j2 + n*(...)): x_1 fastest
     pts = np.stack([g.transpose(*reversed(range(spec.dim))).reshape(-1) for g in grids], axis=1)

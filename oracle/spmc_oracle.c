@@ -253,9 +253,65 @@ void orc_phi(int m, double x, double* phi) {
   for (int p = 0; p <= m; ++p) phi[p] = (1.0 - x * x) * P[p];
 }
 
+/* Jacobi P_0^{(a,a)}..P_m^{(a,a)} at x (the general three-term recurrence with
+ * both parameters a):
+ * 2n(n+2a)(2n+2a-2) P_n = (2n+2a-1)(2n+2a)(2n+2a-2) x P_{n-1} - 2(n+a-1)^2(2n+2a) P_{n-2},
+ * P_0 = 1, P_1 = (a+1) x. */
+void orc_jacobi_aa(int m, double a, double x, double* P) {
+  P[0] = 1.0;
+  if (m >= 1) P[1] = (a + 1.0) * x;
+  for (int n = 2; n <= m; ++n) {
+    double c = 2.0 * n + 2.0 * a;
+    P[n] = ((c - 1.0) * c * (c - 2.0) * x * P[n - 1] - 2.0 * (n + a - 1.0) * (n + a - 1.0) * c * P[n - 2]) /
+           (2.0 * n * (n + 2.0 * a) * (c - 2.0));
+  }
+}
+
+/* The fractional case (Section 4, Ex. 2; the remark on generalised Jacobi
+ * functions): basis phi_p = (1-x^2)_+^a P_p^{(a,a)}, a = alpha/2, with
+ * (-Delta)^{alpha/2} phi_p = lam_p P_p^{(a,a)} on (-1,1), lam_p = Gamma(alpha+p+1)/p!
+ * (the hypersingular integral with the standard constant
+ * C_{1,alpha} = alpha 2^{alpha-1} Gamma((1+alpha)/2) / (sqrt(pi) Gamma(1-alpha/2))).
+ * For alpha = 2 these are the Babuska-Shen basis and (p+1)(p+2). */
+double orc_frac_lambda(double alpha, int p) { return exp(lgamma(alpha + p + 1.0) - lgamma(p + 1.0)); }
+
+/* int_{-1}^{1} (1-x^2)^a P_p^{(a,a)}(x)^2 dx */
+static double jacobi_aa_norm(double a, int p) {
+  return exp((2.0 * a + 1.0) * log(2.0) + 2.0 * lgamma(p + a + 1.0) - lgamma(p + 1.0) - lgamma(p + 2.0 * a + 1.0)) /
+         (2.0 * p + 2.0 * a + 1.0);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Gauss-type nodes and weights.                                              */
 /* ------------------------------------------------------------------------- */
+/* Jacobi-Gauss (a,a): the n zeros of P_n^{(a,a)}, weights for (1-x^2)^a:
+ * w_j = 2^{2a+1} Gamma(n+a+1)^2 / (Gamma(n+1) Gamma(n+2a+1) (1-x_j^2) P_n'(x_j)^2),
+ * with (1-x^2) P_n' = (n+a) P_{n-1} - n x P_n.  Newton with deflation. */
+void orc_gj_nodes(int n, double a, double* x, double* w) {
+  double P[ORC_MAXN + 2];
+  for (int j = 0; j < n; ++j) {
+    double z = -cos(ORC_PI * (j + 0.75) / (n + 0.5));
+    for (int it = 0; it < 200; ++it) {
+      orc_jacobi_aa(n, a, z, P);
+      double dP = ((n + a) * P[n - 1] - n * z * P[n]) / (1.0 - z * z);
+      double defl = 0.0;
+      for (int k = 0; k < j; ++k) defl += 1.0 / (z - x[k]);
+      double step = P[n] / (dP - P[n] * defl);
+      z -= step;
+      if (fabs(step) < 1e-16 * (1.0 + fabs(z))) break;
+    }
+    x[j] = z;
+  }
+  for (int u = 0; u < n; ++u)
+    for (int v = u + 1; v < n; ++v)
+      if (x[v] < x[u]) { double t = x[u]; x[u] = x[v]; x[v] = t; }
+  double cst = exp((2.0 * a + 1.0) * log(2.0) + 2.0 * lgamma(n + a + 1.0) - lgamma(n + 1.0) - lgamma(n + 2.0 * a + 1.0));
+  for (int j = 0; j < n; ++j) {
+    orc_jacobi_aa(n, a, x[j], P);
+    double dP = ((n + a) * P[n - 1] - n * x[j] * P[n]) / (1.0 - x[j] * x[j]);
+    w[j] = cst / ((1.0 - x[j] * x[j]) * dP * dP);
+  }
+}
 /* Jacobi-Gauss (1,1): the n zeros of P_n^{(1,1)} and the weights for the
  * weight function (1-x^2):  w_j = 8(n+1)/((n+2)(1-x_j^2) P_n'(x_j)^2), with
  * (1-x^2) P_n' = (n+1) P_{n-1} - n x P_n.  Newton with deflation of the roots
@@ -402,7 +458,31 @@ typedef struct {
                        walk is absorbed (direct estimator only) */
   int estimator;    /* 0: residual iteration (Eqs. ufg_ep1, varepsilon_1); 1: the direct estimator
                        S_i of Eq. Phi_ast (Picard iteration, Eq. linearized_func) */
+  double alpha;     /* 0: L = -kappa Delta; in (0, 2): L = kappa (-Delta)^{alpha/2} (d = 1, walk_mode 2,
+                       generalised Jacobi functions with a = alpha/2) */
 } orc_problem;
+
+static int is_frac(const orc_problem* pb) { return pb->alpha > 0.0 && pb->alpha < 2.0; }
+
+/* Spatial nodes of the problem: Jacobi-Gauss (1,1), or (a,a) in the fractional case. */
+void orc_space_nodes(const orc_problem* pb, double* x, double* w) {
+  if (is_frac(pb)) orc_gj_nodes(pb->n_space, 0.5 * pb->alpha, x, w);
+  else orc_jg11_nodes(pb->n_space, x, w);
+}
+
+/* The space analysis matrix of the problem: (1,1) as above, or in the
+ * fractional case A[p*n + j] = w_j P_p^{(a,a)}(x_j) / ((1-x_j^2)^a gamma_p^{(a)})
+ * (Gauss-Jacobi (a,a) quadrature of u (1-x^2)^{-a} P_p against the weight). */
+void orc_space_analysis_pb(const orc_problem* pb, double* A) {
+  int n = pb->n_space;
+  if (!is_frac(pb)) { orc_space_analysis(n, A); return; }
+  double a = 0.5 * pb->alpha, x[ORC_MAXN], w[ORC_MAXN], P[ORC_MAXN + 2];
+  orc_gj_nodes(n, a, x, w);
+  for (int j = 0; j < n; ++j) {
+    orc_jacobi_aa(n - 1, a, x[j], P);
+    for (int p = 0; p < n; ++p) A[p * n + j] = w[j] * P[p] / (pow(1.0 - x[j] * x[j], a) * jacobi_aa_norm(a, p));
+  }
+}
 
 static int64_t ipow(int64_t b, int e) { int64_t r = 1; while (e-- > 0) r *= b; return r; }
 
@@ -446,7 +526,47 @@ double orc_exact(const orc_problem* pb, const double* x, double t) {
     for (int e = 0; e < d; ++e) v *= sin(ORC_PI * x[e]);
     return exp(-pb->ex_beta * t) * v + 0.5 * t;
   }
+  if (pb->ex_kind == 6 || pb->ex_kind == 7) {
+    /* fractional examples (1-D, zero outside Omega), a = alpha/2:
+     * 6: (1-x^2)_+^a sin(x) e^{cos t} / (1+t^2)   (Section 4, Ex. 2)
+     * 7: (1+t) (1-x^2)_+^a (1 + P_1^{(a,a)}(x)/2)  (in the approximation space) */
+    double a = 0.5 * pb->alpha;
+    if (!(fabs(x[0]) < 1.0)) return 0.0;
+    double wgt = pow(1.0 - x[0] * x[0], a);
+    if (pb->ex_kind == 6) return wgt * sin(x[0]) * exp(cos(t)) / (1.0 + t * t);
+    return (1.0 + t) * wgt * (1.0 + 0.5 * (a + 1.0) * x[0]);
+  }
   return 0.0;
+}
+
+/* Coefficients s_n of sin(x) = sum_n s_n P_n^{(a,a)}(x), n < 40, by Gauss-Jacobi
+ * (a,a) quadrature with 40 nodes (exact for the polynomial part up to degree
+ * 79; the remainder of the sine's Taylor series is below 1e-40). */
+static void frac_sin_coef(double a, double* s) {
+  double x[40], w[40], P[41];
+  orc_gj_nodes(40, a, x, w);
+  for (int k = 0; k < 40; ++k) s[k] = 0.0;
+  for (int j = 0; j < 40; ++j) {
+    orc_jacobi_aa(39, a, x[j], P);
+    for (int k = 0; k < 40; ++k) s[k] += w[j] * sin(x[j]) * P[k];
+  }
+  for (int k = 0; k < 40; ++k) s[k] /= jacobi_aa_norm(a, k);
+}
+
+/* (-Delta)^{alpha/2} of the fractional exact solutions at (x, t), |x| < 1:
+ * kind 6: T(t) sum_n s_n lam_n P_n(x); kind 7: (1+t)(lam_0 + lam_1 P_1(x)/2). */
+static double frac_op_exact(const orc_problem* pb, double x, double t) {
+  static _Thread_local double cache_alpha = -1.0, s[40];
+  double a = 0.5 * pb->alpha, P[41];
+  if (pb->ex_kind == 7) {
+    orc_jacobi_aa(1, a, x, P);
+    return (1.0 + t) * (orc_frac_lambda(pb->alpha, 0) + 0.5 * orc_frac_lambda(pb->alpha, 1) * P[1]);
+  }
+  if (cache_alpha != pb->alpha) { frac_sin_coef(a, s); cache_alpha = pb->alpha; }
+  orc_jacobi_aa(39, a, x, P);
+  double acc = 0.0;
+  for (int n = 0; n < 40; ++n) acc += s[n] * orc_frac_lambda(pb->alpha, n) * P[n];
+  return acc * exp(cos(t)) / (1.0 + t * t);
 }
 
 /* The exact solutions with non-zero boundary values, with their derivatives:
@@ -474,6 +594,13 @@ static void exact_parts(const orc_problem* pb, const double* x, double t, double
 double orc_source(const orc_problem* pb, const double* x, double t) {
   if (pb->ex_kind == 0) return 0.0;
   int d = pb->dim;
+  if (pb->ex_kind == 6 || pb->ex_kind == 7) {
+    /* d_t u + kappa (-Delta)^{alpha/2} u - f(u) */
+    double u = orc_exact(pb, x, t), ut;
+    if (pb->ex_kind == 6) ut = u * (-sin(t) - 2.0 * t / (1.0 + t * t));
+    else ut = u / (1.0 + t);
+    return ut + pb->kappa * frac_op_exact(pb, x[0], t) - orc_f(pb, u);
+  }
   if (pb->ex_kind >= 4) {
     double u, ut, uxx[ORC_MAXD], lap = 0.0;
     exact_parts(pb, x, t, &u, &ut, uxx);
@@ -550,7 +677,7 @@ void orc_reconstruct(const orc_problem* pb, int Mt, double h, const double* U, d
   int64_t S = ipow(n, d);
   double* A = (double*)malloc(sizeof(double) * n * n);
   double* B = (double*)malloc(sizeof(double) * (Mt + 1) * (Mt + 1));
-  orc_space_analysis(n, A);
+  orc_space_analysis_pb(pb, A);
   orc_time_analysis(pb->time_family, Mt, B);
   int64_t tot = S * (Mt + 1);
   double* cur = (double*)malloc(sizeof(double) * tot);
@@ -587,15 +714,25 @@ void orc_reconstruct(const orc_problem* pb, int Mt, double h, const double* U, d
 }
 
 /* Values of u*, d_t u* and -Delta u* at (x, xi) by the direct sum over all
- * coefficients (Eq. u_N, with -d^2 phi_p = (p+1)(p+2) P_p^{(1,1)} per axis). */
+ * coefficients (Eq. u_N, with -d^2 phi_p = (p+1)(p+2) P_p^{(1,1)} per axis; in
+ * the fractional case (-Delta)^{alpha/2} u* with lam_p = Gamma(alpha+p+1)/p!). */
 void orc_eval(const orc_problem* pb, int Mt, const double* cu, const double* ct, const double* x,
               double xi, double* u_out, double* dtu_out, double* mlap_out) {
   int d = pb->dim, n = pb->n_space;
   int64_t S = ipow(n, d);
-  double phi[ORC_MAXD][ORC_MAXN + 2], P[ORC_MAXD][ORC_MAXN + 2], L[ORC_MAXN + 2];
+  double phi[ORC_MAXD][ORC_MAXN + 2], P[ORC_MAXD][ORC_MAXN + 2], L[ORC_MAXN + 2], lam[ORC_MAXN + 2];
+  for (int p = 0; p < n; ++p) lam[p] = is_frac(pb) ? orc_frac_lambda(pb->alpha, p) : (p + 1.0) * (p + 2.0);
   for (int e = 0; e < d; ++e) {
-    orc_jacobi11(n - 1, x[e], P[e]);
-    orc_phi(n - 1, x[e], phi[e]);
+    if (is_frac(pb)) {
+      /* phi_p = (1-x^2)^a P_p^{(a,a)}; (-Delta)^{alpha/2} phi_p = lam_p P_p^{(a,a)} */
+      double a = 0.5 * pb->alpha;
+      orc_jacobi_aa(n - 1, a, x[e], P[e]);
+      double wgt = fabs(x[e]) < 1.0 ? pow(1.0 - x[e] * x[e], a) : 0.0;
+      for (int p = 0; p < n; ++p) phi[e][p] = wgt * P[e][p];
+    } else {
+      orc_jacobi11(n - 1, x[e], P[e]);
+      orc_phi(n - 1, x[e], phi[e]);
+    }
   }
   orc_legendre(Mt, xi, L);
   double u = 0.0, dtu = 0.0, mlap = 0.0;
@@ -608,7 +745,7 @@ void orc_eval(const orc_problem* pb, int Mt, const double* cu, const double* ct,
       for (int e = 0; e < d; ++e) prod *= phi[e][p[e]];
       double lap = 0.0;
       for (int e = 0; e < d; ++e) {
-        double term = L[q] * (p[e] + 1.0) * (p[e] + 2.0) * P[e][p[e]];
+        double term = L[q] * lam[p[e]] * P[e][p[e]];
         for (int e2 = 0; e2 < d; ++e2) if (e2 != e) term *= phi[e2][p[e2]];
         lap += term;
       }
@@ -654,6 +791,45 @@ typedef struct {
 
 /* The quadrature points of one walk: for term i, the point pts[i*d..], the
  * time taus[i] and the weight wts[i] (at most cap terms).  Returns L. */
+/* Regularised incomplete beta function I_x(p, q) from its hypergeometric form
+ * I_x(p,q) = x^p (1-x)^q / (p B(p,q)) F(p+q, 1; p+1; x), summed for x <= 1/2,
+ * with I_x(p,q) = 1 - I_{1-x}(q,p) above. */
+double orc_ibeta(double x, double p, double q) {
+  if (!(x > 0.0)) return 0.0;
+  if (!(x < 1.0)) return 1.0;
+  if (x > 0.5) return 1.0 - orc_ibeta(1.0 - x, q, p);
+  double pre = exp(p * log(x) + q * log1p(-x) - (lgamma(p) + lgamma(q) - lgamma(p + q))) / p;
+  double term = 1.0, sum = 1.0;
+  for (int k = 0; k < 4000; ++k) {
+    term *= (p + q + k) / (p + 1.0 + k) * x;
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  return pre * sum;
+}
+
+/* Its inverse in x by bisection (I_x is increasing in x). */
+double orc_ibeta_inv(double w, double p, double q) {
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (orc_ibeta(mid, p, q) < w) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* Jump length of the alpha-stable process out of a ball of radius r around
+ * its centre (d = 1), from the uniform omega: the exit point lies at distance
+ * r / sqrt(U), U ~ Beta(alpha/2, 1 - alpha/2) (the Blumenthal-Getoor-Ray exit
+ * law).  Section 4, Ex. 2 writes U = 1 - X, X = I^{-1}_omega(1 - alpha/2, alpha/2);
+ * the same number is U = I^{-1}_{1-omega}(alpha/2, 1 - alpha/2), computed so to
+ * avoid the cancellation in 1 - X for omega near 1. */
+double orc_stable_jump(double r, double alpha, double omega) {
+  double a = 0.5 * alpha;
+  double U = orc_ibeta_inv(1.0 - omega, a, 1.0 - a);
+  return r / sqrt(U);
+}
+
 int orc_walk_points_end(const orc_problem* pb, const orc_interval_ctx* ic, uint32_t node_lin, uint32_t sample,
                         const double* x_start, double t_node, int nstar, double* pts, double* taus, double* wts,
                         int cap, double* x_end, int* end_kind, double* t_end) {
@@ -666,6 +842,34 @@ int orc_walk_points_end(const orc_problem* pb, const orc_interval_ctx* ic, uint3
   double X[ORC_MAXD], Xn[ORC_MAXD], theta[ORC_MAXD];
   for (int e = 0; e < d; ++e) X[e] = x_start[e];
   int L = 0;
+  if (pb->walk_mode == 2) {
+    /* The alpha-stable walk (Section 4, Ex. 2, d = 1): steps of time Delta, each
+     * the exit from the ball of radius r = (kappa Delta Gamma(1+alpha))^{1/alpha}
+     * around X_q (its mean exit time C r^alpha / kappa is Delta, C = 1/Gamma(1+alpha));
+     * the jump J_q = r / sqrt(1 - I^{-1}_omega(1-alpha/2, alpha/2)) in direction
+     * theta_q = +-1.  Words 2q (direction, top bit) and 2q+1 (omega).  As in the
+     * fixed-radius walk, the walk ends at the first point outside Omega and the
+     * term q (the residual at X_q, time t_node - q Delta, weight Delta) counts
+     * when X_{q+1} is inside. */
+    double r = pow(pb->kappa * delta * exp(lgamma(1.0 + pb->alpha)), 1.0 / pb->alpha);
+    for (int q = 0; q < nstar && q < pb->max_steps; ++q) {
+      uint32_t wd = stream_word(&st, 2 * (int64_t)q), wo = stream_word(&st, 2 * (int64_t)q + 1);
+      double th = (wd >> 31) ? -1.0 : 1.0;
+      double J = orc_stable_jump(r, pb->alpha, orc_u01_word(wo));
+      double Xn = X[0] + J * th;
+      if (!(Xn > -1.0 && Xn < 1.0)) break;
+      if (L < cap) {
+        pts[L] = X[0];
+        taus[L] = t_node - q * delta;
+        wts[L] = delta;
+      }
+      L = q + 1;
+      X[0] = Xn;
+    }
+    if (x_end) x_end[0] = X[0];
+    if (end_kind) *end_kind = 0;
+    return L;
+  }
   if (pb->walk_mode == 1) {
     /* Fixed radius J; the walk ends at the first step centre outside Omega
      * (Eq. indexL); the term q counts when X_{q+1} is still inside. */
@@ -710,7 +914,7 @@ int orc_walk_points_end(const orc_problem* pb, const orc_interval_ctx* ic, uint3
   if (!(shell > 0.0)) {
     /* half the distance of the outermost JG(1,1) node to the boundary, at most 2e-3 */
     double xs[ORC_MAXN], ws[ORC_MAXN];
-    orc_jg11_nodes(pb->n_space, xs, ws);
+    orc_space_nodes(pb, xs, ws);
     shell = 0.5 * (1.0 - fabs(xs[0]));
     if (shell > 2e-3) shell = 2e-3;
   }
@@ -865,7 +1069,7 @@ static void node_coords(int d, int n, const double* xs, int64_t j, double* x) {
 double orc_node_eps(const orc_problem* pb, const orc_interval_ctx* ic, int64_t j, int l) {
   int d = pb->dim, n = pb->n_space;
   double xs[ORC_MAXN], ws[ORC_MAXN], xi[ORC_MAXN + 1], wt[ORC_MAXN + 1], x[ORC_MAXD];
-  orc_jg11_nodes(n, xs, ws);
+  orc_space_nodes(pb, xs, ws);
   orc_time_nodes(pb->time_family, ic->Mt, xi, wt);
   node_coords(d, n, xs, j, x);
   double s = (xi[l] + 1.0) * 0.5 * ic->h;
@@ -1019,7 +1223,7 @@ void orc_solve(const orc_problem* pb, int n_int, const double* t, const int* Mt,
   if (pb->bc_kind == 1) {
     /* w(., 0) = u0 - G(., 0) at the nodes */
     double xs[ORC_MAXN], ws[ORC_MAXN], x[ORC_MAXD], G, Gt, lapG;
-    orc_jg11_nodes(pb->n_space, xs, ws);
+    orc_space_nodes(pb, xs, ws);
     for (int64_t j = 0; j < S; ++j) {
       node_coords(pb->dim, pb->n_space, xs, j, x);
       orc_lift(pb, x, t[0], &G, &Gt, &lapG);
@@ -1078,7 +1282,7 @@ void orc_solve_tangent(const orc_problem* pb, int n_int, const double* t, const 
   memcpy(row, u0, sizeof(double) * S);
   memcpy(drow, du0, sizeof(double) * S);
   double xs[ORC_MAXN], ws[ORC_MAXN];
-  orc_jg11_nodes(n, xs, ws);
+  orc_space_nodes(pb, xs, ws);
   int64_t off = 0;
   for (int m = 0; m < n_int; ++m) {
     int M_t = Mt[m];
