@@ -49,7 +49,8 @@ enum { SPMC_TIME_LGL = 0, SPMC_TIME_RADAU_LEFT = 1 };     /* time nodes per inte
 enum { SPMC_FP64 = 0, SPMC_MIXED = 1 };                    /* sweep arithmetic */
 enum { SPMC_F_POLY3 = 0, SPMC_F_SIN = 1 };                 /* reaction f(u) */
 enum { SPMC_EX_NONE = 0, SPMC_EX_SIN = 1, SPMC_EX_COSHALF = 2, SPMC_EX_POLY = 3,
-       SPMC_EX_COSTHIRD = 4, SPMC_EX_SINPLUS = 5 };                 /* non-zero boundary values */
+       SPMC_EX_COSTHIRD = 4, SPMC_EX_SINPLUS = 5,                   /* non-zero boundary values */
+       SPMC_EX_FRAC_SIN = 6, SPMC_EX_FRAC_POLY = 7 };               /* the fractional case */
 enum { SPMC_BC_ZERO = 0, SPMC_BC_LIFT = 1, SPMC_BC_RAW = 2 };       /* boundary data g */
 enum { SPMC_EST_RESIDUAL = 0, SPMC_EST_DIRECT = 1 };               /* estimator */
 enum { SPMC_U0_NODAL = 0, SPMC_U0_PHI_COEF = 1 };
@@ -82,7 +83,8 @@ typedef struct {
                                random sub-step time; SPMC_WALK_FIXED (1): the fixed-radius
                                walk of Lemma Xlocation with the residual at the step centres
                                (Eqs. indexL, interIQ; n_sub is then 1, d <= 2, cohort sweep).
-                               The second diverges at high spectral degrees. */
+                               The second diverges at high spectral degrees.  SPMC_WALK_STABLE (2):
+                               the alpha-stable walk of the fractional case (see alpha). */
   int estimator;            /* SPMC_EST_RESIDUAL (0): the residual iteration of Algorithm 1 (u <- u + eps,
                                eps the mean of Q_L of the residual, Eq. varepsilon_1);
                                SPMC_EST_DIRECT (1): the direct estimator of Eq. Phi_ast, a Picard
@@ -92,8 +94,18 @@ typedef struct {
                                the boundary (raw boundary data), plus the quadrature of f(u*) + f_add.
                                Its sampling error does not fall with the iterations.  Event sweep only
                                (d <= 2, walk_mode 0). */
+  double alpha;             /* 0 (or 2): L = -kappa Delta.  In (0, 2), with walk_mode SPMC_WALK_STABLE and
+                               d = 1: the fractional case of Section 4, Ex. 2 and 3,
+                               d_t u + kappa (-Delta)^{alpha/2} u = f(u) + f_add, u = 0 outside Omega:
+                               spatial nodes are the Jacobi-Gauss (alpha/2, alpha/2) nodes, the basis
+                               the generalised Jacobi functions (1-x^2)^{alpha/2} P_p^{(alpha/2,alpha/2)}
+                               ((-Delta)^{alpha/2} of one is Gamma(alpha+p+1)/p! P_p), and the walk the
+                               alpha-stable walk: steps of time Delta, each the exit from the ball of
+                               radius r = (kappa Delta Gamma(1+alpha))^{1/alpha} around the current point,
+                               at distance r / sqrt(U), U ~ Beta(alpha/2, 1-alpha/2), in direction +-1;
+                               the residual at the step centres (Eqs. indexL, interIQ); the cohort sweep. */
 } spmc_plan_desc;
-enum { SPMC_WALK_BALLS = 0, SPMC_WALK_FIXED = 1 };
+enum { SPMC_WALK_BALLS = 0, SPMC_WALK_FIXED = 1, SPMC_WALK_STABLE = 2 };
 
 /* One instance: partition, degrees, reaction, manufactured source, boundary
  * data, u0.  Eq. mainproblem; f_add makes the closed form named by ex_kind an

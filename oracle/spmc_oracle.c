@@ -642,7 +642,7 @@ double orc_source(const orc_problem* pb, const double* x, double t) {
  * G, d_t G and Delta G at (x, t); zeros unless bc_kind == 1. */
 void orc_lift(const orc_problem* pb, const double* x, double t, double* G, double* Gt, double* lapG) {
   *G = 0.0; *Gt = 0.0; *lapG = 0.0;
-  if (pb->bc_kind != 1 || pb->ex_kind < 4) return;
+  if (pb->bc_kind != 1 || (pb->ex_kind != 4 && pb->ex_kind != 5)) return;
   int d = pb->dim;
   for (int A = 1; A < (1 << d); ++A) {
     int na = 0, idx[ORC_MAXD];

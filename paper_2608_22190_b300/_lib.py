@@ -18,12 +18,12 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5:
 TIME_LGL, TIME_RADAU_LEFT = 0, 1
 FP64, MIXED = 0, 1
 F_POLY3, F_SIN = 0, 1
-EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS = 0, 1, 2, 3, 4, 5
+EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS, EX_FRAC_SIN, EX_FRAC_POLY = range(8)
 BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
 EST_RESIDUAL, EST_DIRECT = 0, 1
 U0_NODAL, U0_PHI_COEF = 0, 1
 SPMC_SWEEP_EVENTS, SPMC_SWEEP_COHORT, SPMC_SWEEP_EVENTS_ALU = 0, 1, 2
-WALK_BALLS, WALK_FIXED = 0, 1
+WALK_BALLS, WALK_FIXED, WALK_STABLE = 0, 1, 2
 ACCEL_NONE, ACCEL_AITKEN = 0, 1
 
 
@@ -33,7 +33,7 @@ class PlanDesc(C.Structure):
         ("max_degree", C.c_int), ("M", C.c_longlong), ("K", C.c_int), ("tol", C.c_double),
         ("n_ref", C.c_int), ("n_sub", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int),
         ("kappa", C.c_double), ("seed", C.c_ulonglong), ("precision", C.c_int), ("batch", C.c_int),
-        ("walk_mode", C.c_int), ("estimator", C.c_int),
+        ("walk_mode", C.c_int), ("estimator", C.c_int), ("alpha", C.c_double),
     ]
 
 

@@ -26,7 +26,7 @@ def _stream_ptr(stream) -> Optional[int]:
 class Plan:
     def __init__(self, dim, n_space, time_family, max_intervals, max_degree, M, K, tol=0.0, n_ref=80, n_sub=4,
                  shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1, walk_mode=L.WALK_BALLS,
-                 estimator=L.EST_RESIDUAL):
+                 estimator=L.EST_RESIDUAL, alpha=0.0):
         d = L.PlanDesc()
         d.dim, d.n_space, d.time_family = dim, n_space, time_family
         d.max_intervals, d.max_degree, d.M, d.K, d.tol = max_intervals, max_degree, M, K, tol
@@ -34,6 +34,7 @@ class Plan:
         d.kappa, d.seed, d.precision, d.batch = kappa, seed, precision, batch
         d.walk_mode = walk_mode
         d.estimator = estimator
+        d.alpha = alpha
         self.desc = d
         self._h = C.c_void_p()
         L.check(L.lib.spmc_plan(C.byref(d), C.byref(self._h)))
@@ -81,6 +82,8 @@ class Plan:
                   max_intervals=max(len(i.degrees) for i in insts), max_degree=max(int(max(i.degrees)) for i in insts),
                   M=wl.M, K=wl.K, n_ref=wl.n_ref, n_sub=wl.n_sub, shell=wl.shell, max_steps=wl.max_steps,
                   kappa=wl.kappa, seed=wl.seed, precision=precision, batch=len(insts))
+        if getattr(wl, "alpha", 0.0):
+            kw.update(alpha=wl.alpha, walk_mode=L.WALK_STABLE)
         kw.update(overrides)
         plan = cls(**kw)
         grid = plan.node_grid()
@@ -92,9 +95,10 @@ class Plan:
                                  inst.ex_kind, inst.ex_beta, np.ascontiguousarray(inst.u0_coef.T).ravel(),
                                  L.U0_PHI_COEF, nc)
             else:
+                u0 = (W.frac_exact(wl.alpha, inst.ex_kind, grid[:, 0], inst.t_breaks[0])[0]
+                      if getattr(wl, "alpha", 0.0) else W.u0_nodal(inst, grid))
                 plan.set_problem(b, inst.t_breaks, inst.degrees, inst.f_kind, inst.f_coef, inst.f_scale,
-                                 inst.ex_kind, inst.ex_beta, W.u0_nodal(inst, grid),
-                                 bc_kind=getattr(inst, "bc_kind", L.BC_ZERO))
+                                 inst.ex_kind, inst.ex_beta, u0, bc_kind=getattr(inst, "bc_kind", L.BC_ZERO))
         return plan
 
     # ------------------------------------------------------------------ layout

@@ -400,7 +400,7 @@ __device__ __forceinline__ R exact_bv(const InstanceParams& ip, const R* y, R Tt
 template <int D, typename R>
 __device__ __forceinline__ void lift_bv(const InstanceParams& ip, const R* y, R Tt, R t, R& G, R& Gt, R& lapG) {
   G = R(0); Gt = R(0); lapG = R(0);
-  if (ip.bc_kind != 1 || ip.ex_kind < 4) return;
+  if (ip.bc_kind != 1 || (ip.ex_kind != 4 && ip.ex_kind != 5)) return;
   if (ip.ex_kind == 5) { G = R(0.5) * t; Gt = R(0.5); return; }
   const R cm = R(0.20791169081775945), cp = R(0.7431448254773942);   // c(-1), c(1)
   R c[D], dl[D], pc = R(1), pd = R(1);
@@ -563,6 +563,99 @@ __device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int 
   R u, G;
   slice_parts<D, NMAX, R>(kappa, n, sC, sH, y, u, G);
   return reaction<R>(ip, u) + source<D, R>(ip, kappa, y, Tt, dTt) + G;
+}
+
+// ---------------------------------------------------------------- fractional
+// The fractional case (Section 4, Ex. 2; d = 1): L = kappa (-Delta)^{alpha/2},
+// basis phi_p = (1-y^2)^a P_p^{(a,a)} (a = alpha/2) with
+// (-Delta)^{alpha/2} phi_p = lam_p P_p^{(a,a)}.  `tab` is the plan's table
+// (recurrence coefficients, lam_p, the sine series of Ex. 2's solution; layout
+// kFrac* in spmc_tables.h).
+constexpr int kFracRaD = 0, kFracRbD = 40, kFracLamD = 80, kFracSinD = 120, kFracAD = 160, kFracAlphaD = 161,
+              kFracGammaD = 162, kFracModesD = 40;
+
+// Regularised incomplete beta I_x(p, q) = x^p (1-x)^q / (p B(p,q)) F(p+q, 1; p+1; x)
+// (x <= 1/2; 1 - I_{1-x}(q, p) above); lnB = ln B(p, q).
+__device__ __forceinline__ double ibeta_d(double x, double p, double q, double lnB) {
+  bool flip = x > 0.5;
+  if (flip) { x = 1.0 - x; const double t = p; p = q; q = t; }
+  if (!(x > 0.0)) return flip ? 1.0 : 0.0;
+  const double pre = exp(p * log(x) + q * log1p(-x) - lnB) / p;
+  double term = 1.0, sum = 1.0;
+  for (int k = 0; k < 400; ++k) {
+    term *= (p + q + k) / (p + 1.0 + k) * x;
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  const double v = pre * sum;
+  return flip ? 1.0 - v : v;
+}
+
+// Exit distance from a ball of radius r of the alpha-stable process started at
+// its centre: r / sqrt(U), U ~ Beta(a, 1-a) (the Blumenthal-Getoor-Ray law),
+// U = I^{-1}_{1-omega}(a, 1-a) by Newton's method kept inside a bisection bracket.
+__device__ __forceinline__ double stable_jump_d(double r, double a, double omega) {
+  const double p = a, q = 1.0 - a, target = 1.0 - omega;
+  const double lnB = lgamma(p) + lgamma(q) - lgamma(p + q);
+  double lo = 0.0, hi = 1.0;
+  // start from the leading term at the nearer end
+  double x = exp((log(target) + log(p) + lnB) / p);
+  if (!(x < 0.5)) x = 1.0 - exp((log1p(-target) + log(q) + lnB) / q);
+  if (!(x > 0.0 && x < 1.0)) x = 0.5;
+  for (int it = 0; it < 100; ++it) {
+    const double F = ibeta_d(x, p, q, lnB) - target;
+    if (F < 0.0) lo = x; else hi = x;
+    const double dF = exp((p - 1.0) * log(x) + (q - 1.0) * log1p(-x) - lnB);
+    double xn = x - F / dF;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    const bool done = fabs(xn - x) <= 1e-16 * xn || hi - lo <= 1e-17;
+    x = xn;
+    if (done) break;
+  }
+  return r / sqrt(x);
+}
+
+// The residual at y (|y| < 1) from a slice of the fractional case:
+//   u* = sum C_p phi_p(y),  G = sum H_p phi_p(y) - kappa sum C_p lam_p P_p(y),
+//   r = f(u*) + f_add + G,
+// f_add of the fractional examples: 6, u = (1-y^2)^a sin(y) T(t) (Ex. 2),
+// (-Delta)^{alpha/2} u = T sum s_p lam_p P_p; 7, u = T (1-y^2)^a (1 + P_1/2), T = 1+t.
+template <typename R>
+__device__ __forceinline__ R residual_frac(const InstanceParams& ip, R kappa, int n, const R* __restrict__ sC,
+                                           const R* __restrict__ sH, R y, R Tt, R dTt,
+                                           const double* __restrict__ tab) {
+  const R a = (R)tab[kFracAD];
+  const R wgt = pow(R(1) - y * y, a);
+  R pm2 = R(1), pm1 = (a + R(1)) * y;
+  R u = R(0), G = R(0), cl = R(0), fr = R(0);
+  const bool sine = ip.ex_kind == 6;
+  const int top = sine ? kFracModesD : n;
+  for (int p = 0; p < top; ++p) {
+    R P;
+    if (p == 0) P = R(1);
+    else if (p == 1) P = pm1;
+    else { P = (R)tab[kFracRaD + p] * y * pm1 - (R)tab[kFracRbD + p] * pm2; pm2 = pm1; pm1 = P; }
+    const R lam = (R)tab[kFracLamD + p];
+    if (p < n) {
+      u += sC[p] * P;
+      G += sH[p] * P;
+      cl += sC[p] * lam * P;
+    }
+    if (sine) fr += (R)tab[kFracSinD + p] * lam * P;
+  }
+  u *= wgt;
+  G = G * wgt - kappa * cl;
+  R fadd = R(0);
+  if (sine) {
+    const R ws = wgt * sin(y);
+    fadd = dTt * ws + kappa * Tt * fr - reaction<R>(ip, Tt * ws);
+  } else if (ip.ex_kind == 7) {
+    const R P1 = (a + R(1)) * y;
+    const R lam0 = (R)tab[kFracLamD], lam1 = (R)tab[kFracLamD + 1];
+    const R shape = wgt * (R(1) + R(0.5) * P1);
+    fadd = dTt * shape + kappa * Tt * (lam0 + R(0.5) * lam1 * P1) - reaction<R>(ip, Tt * shape);
+  }
+  return reaction<R>(ip, u) + fadd + G;
 }
 
 }  // namespace spmc

@@ -140,6 +140,10 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
     si.tau = tau;
     si.kind = kind;
     if (P.ex_kind == 3) { si.Tt = 1.0 + tau + tau * tau; si.dTt = 1.0 + 2.0 * tau; }
+    else if (P.ex_kind == 6) {   // e^{cos t} / (1 + t^2)
+      si.Tt = exp(cos(tau)) / (1.0 + tau * tau);
+      si.dTt = si.Tt * (-sin(tau) - 2.0 * tau / (1.0 + tau * tau));
+    } else if (P.ex_kind == 7) { si.Tt = 1.0 + tau; si.dTt = 1.0; }
     else if (P.ex_kind >= 1) { si.Tt = exp(-P.ex_beta * tau); si.dTt = -P.ex_beta * si.Tt; }
     else { si.Tt = 0.0; si.dTt = 0.0; }
     sinfo[s] = si;
@@ -181,7 +185,9 @@ struct SweepArgs {
   double kappa, shell;
   uint32_t k0, k1;
   int interval, iteration;
-  int walk_mode;            // 0: inside-ball walk; 1: fixed-radius walk with centre points
+  int walk_mode;            // 0: inside-ball walk; 1: fixed-radius walk with centre points;
+                            // 2: the alpha-stable walk of the fractional case (d = 1)
+  const double* frac;       // walk_mode 2: the plan's fractional table (kFrac* layout)
   // adjoint sweep only
   const double* lambda;     // adjoint of the nodal values (layout of U)
   double* gT;               // per slice: 3 S accumulators (coefficient order)
@@ -214,8 +220,32 @@ struct WalkState {
 template <int D, typename R>
 __device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, const WalkStream& ws, R J, R delta,
                                              R sub, int Ktot, int G, int gbits, R shell, R kappa, int max_steps,
-                                             double& acc, unsigned long long& capped, int walk_mode = 0) {
+                                             double& acc, unsigned long long& capped, int walk_mode = 0,
+                                             const double* frac = nullptr, double r_stable = 0.0) {
   int q = st.q[s];
+  if (walk_mode == 2) {
+    // the alpha-stable walk (d = 1): step q jumps out of the ball of radius
+    // r_stable around X_q, by J_q = r_stable / sqrt(U_q) in direction +-1 (words
+    // 2q and 2q + 1 of one Philox block); the term of step q counts if X_{q+1}
+    // is still inside.  st.r holds the signed jump.
+    if (q >= max_steps || q >= Ktot) {
+      if (q >= max_steps && q < Ktot) ++capped;
+      st.mnext[s] = -1;
+      return;
+    }
+    const Philox4 b = ws.block((uint32_t)q >> 1);
+    const uint32_t wd = b.v[(2 * q) & 3], wo = b.v[(2 * q + 1) & 3];
+    const double omega = U01<double>::one(wo);
+    const double Jq = stable_jump_d(r_stable, frac[kFracAD], omega);
+    const double step = (wd >> 31) ? -Jq : Jq;
+    const double xn = (double)st.X[0][s] + step;
+    if (!(xn > -1.0 && xn < 1.0)) { st.mnext[s] = -1; return; }
+    st.w[s] = delta;
+    st.r[s] = (R)step;
+    st.mnext[s] = q;
+    st.last[s] = (q + 1 >= Ktot) ? 1 : 0;
+    return;
+  }
   if (walk_mode == 1) {
     if (q >= max_steps || q >= Ktot) {
       if (q >= max_steps && q < Ktot) ++capped;
@@ -388,6 +418,12 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
     const R J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
     const R sub = Ar<R>::div(delta, (R)G);
     const int Ktot = G * node.nstar;
+    // the alpha-stable walk's ball radius: its mean exit time r^alpha / (kappa Gamma(1+alpha)) is Delta
+    double r_stable = 0.0;
+    if (a.walk_mode == 2) {
+      const double dd = (node.t_node - node.t0) / (double)node.nstar;
+      r_stable = pow(a.kappa * dd * a.frac[kFracGammaD], 1.0 / a.frac[kFracAlphaD]);
+    }
     const uint32_t tag = ((uint32_t)(node.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
                          (uint32_t)(a.iteration & 0x3ff);
     const long long sample0 = (long long)chunk * CC;
@@ -408,7 +444,7 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
       ws.node = (uint32_t)(node.ell * S + j);
       ws.sample = (uint32_t)(sample0 + s);
       prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps, dummy_acc, capped,
-                         a.walk_mode);
+                         a.walk_mode, a.frac, r_stable);
       if (mnext[wk] >= 0) ++cnt;
     }
     __syncthreads();
@@ -483,8 +519,8 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
           const R r = st.r[wk];
           R Y[D];
           R w = st.w[wk];
-          if (a.walk_mode == 1) {
-            // fixed-radius walk: the residual at the step centre
+          if (a.walk_mode >= 1) {
+            // fixed-radius and alpha-stable walks: the residual at the step centre
 #pragma unroll
             for (int e = 0; e < D; ++e) Y[e] = st.X[e][wk];
           } else {
@@ -511,7 +547,11 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
               const double cw = a.lambda[node.u_off + (long long)node.ell * S + j0 + jj] * (double)w / (double)a.M;
               ds_acc += adjoint_at<D, NMAX, R>(ip, n, sc, Y, cw, sAcc + (long long)bsl * 3 * S, S, (R)s_Tt[bsl]);
             } else {
-              R res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)s_Tt[bsl], (R)s_dTt[bsl]);
+              R res;
+              if (D == 1 && a.walk_mode == 2)
+                res = residual_frac<R>(ip, kappa, n, sc, sc + half, Y[0], (R)s_Tt[bsl], (R)s_dTt[bsl], a.frac);
+              else
+                res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + half, Y, (R)s_Tt[bsl], (R)s_dTt[bsl]);
               st.S[wk] += w * res;
             }
             ++points;
@@ -519,13 +559,14 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
           if (st.last[wk]) { mnext[wk] = -1; break; }
           // step to the sphere of the ball (fixed-radius walk: to the next centre)
           R th[D];
-          if (a.walk_mode == 1) literal_direction<D, R>(ws, q, th);
+          if (a.walk_mode == 2) th[0] = R(1);   // st.r holds the signed jump
+          else if (a.walk_mode == 1) literal_direction<D, R>(ws, q, th);
           else direction<D, R>(ws, w0, th);
 #pragma unroll
           for (int e = 0; e < D; ++e) st.X[e][wk] = Ar<R>::add(st.X[e][wk], Ar<R>::mul(r, th[e]));
           st.q[wk] = q + 1;
           prepare_step<D, R>(st, wk, ws, J, delta, sub, Ktot, G, a.gbits, shell, kappa, a.max_steps,
-                             dummy_acc, capped, a.walk_mode);
+                             dummy_acc, capped, a.walk_mode, a.frac, r_stable);
           mv = mnext[wk];
         }
       }

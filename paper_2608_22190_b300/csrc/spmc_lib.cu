@@ -19,6 +19,12 @@
 #include "spmc_tc5.cuh"
 #include "spmc_tables.h"
 
+static_assert(spmc::kFracRa == spmc::kFracRaD && spmc::kFracRb == spmc::kFracRbD &&
+                  spmc::kFracLam == spmc::kFracLamD && spmc::kFracSin == spmc::kFracSinD &&
+                  spmc::kFracA == spmc::kFracAD && spmc::kFracAlpha == spmc::kFracAlphaD &&
+                  spmc::kFracGamma == spmc::kFracGammaD && spmc::kFracModes == spmc::kFracModesD,
+              "the fractional table's host and device layouts agree");
+
 using namespace spmc;
 
 namespace {
@@ -92,6 +98,7 @@ struct spmc_plan_s {
   // device
   double* d_x = nullptr;
   double* d_times = nullptr;     // t_{n,l} of one interval (spmc_get_solution)
+  double* d_frac = nullptr;      // the fractional case's table (kFrac* layout of spmc_tables.h)
   double* d_A = nullptr;
   double* d_B = nullptr;
   double* d_hw = nullptr;
@@ -380,6 +387,7 @@ SweepArgs sweep_args(spmc_plan_t plan, const Round& rd, int interval, int iterat
   a.k0 = (uint32_t)(d.seed & 0xffffffffULL); a.k1 = (uint32_t)(d.seed >> 32);
   a.interval = interval; a.iteration = iteration;
   a.walk_mode = d.walk_mode;
+  a.frac = plan->d_frac;
   a.M = d.M;
   a.sl_stride = plan->sl_stride;
   a.half = plan->half;
@@ -502,7 +510,7 @@ bool uses_events(spmc_plan_t plan) {
 spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   const int S = plan->S, n = plan->d.n_space, D = plan->d.dim;
   if (rd.ii.empty()) return SPMC_OK;
-  const double t_off = plan->d.walk_mode == 1 ? 0.0 : 0.5;   // step centres / sub-step midpoints
+  const double t_off = plan->d.walk_mode >= 1 ? 0.0 : 0.5;   // step centres / sub-step midpoints
   const int* ab = plan->d_abort;
   if (D >= 3) {
     // reconstruction in global memory: time axis, then each space axis
@@ -1258,7 +1266,8 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
       (d.n_sub & (d.n_sub - 1)) || !(d.shell >= 0.0) || d.shell >= 0.5 || d.max_steps < 1 || !(d.kappa > 0.0) || d.batch < 1 ||
       (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
       (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL ||
-      (d.walk_mode != 0 && d.walk_mode != 1) || (d.estimator != SPMC_EST_RESIDUAL && d.estimator != SPMC_EST_DIRECT))
+      (d.walk_mode < 0 || d.walk_mode > 2) || (d.estimator != SPMC_EST_RESIDUAL && d.estimator != SPMC_EST_DIRECT) ||
+      (d.walk_mode == 2) != (d.alpha > 0.0 && d.alpha < 2.0))
     return SPMC_ERR_INVALID;
   if (d.dim != 1 && d.dim != 2 && d.dim != 5) return SPMC_ERR_UNSUPPORTED;
   if (d.dim == 5 && d.n_space > 8) return SPMC_ERR_UNSUPPORTED;
@@ -1269,10 +1278,11 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   }
   if (d.tol > 0.0 && d.batch > 1) return SPMC_ERR_UNSUPPORTED;
   if (d.walk_mode == 1 && d.dim > 2) return SPMC_ERR_UNSUPPORTED;
+  if (d.walk_mode == 2 && d.dim != 1) return SPMC_ERR_UNSUPPORTED;   // the fractional case: d = 1
   if (d.estimator == SPMC_EST_DIRECT && (d.dim > 2 || d.walk_mode != 0)) return SPMC_ERR_UNSUPPORTED;
   spmc_plan_t plan = new spmc_plan_s();
   plan->d = d;
-  if (d.walk_mode == 1) plan->d.n_sub = 1;   // one evaluation time per step: its centre
+  if (d.walk_mode >= 1) plan->d.n_sub = 1;   // one evaluation time per step: its centre
   plan->S = 1;
   for (int e = 0; e < d.dim; ++e) plan->S *= d.n_space;
   plan->probs.assign(d.batch, HostProblem());
@@ -1286,15 +1296,23 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   plan->threads = 256;
   // tables
   const int n = d.n_space;
+  const bool frac = d.walk_mode == 2;
   plan->xnodes.resize(n);
-  space_nodes(n, plan->xnodes.data());
+  if (frac) space_nodes_frac(n, d.alpha, plan->xnodes.data());
+  else space_nodes(n, plan->xnodes.data());
   // shell == 0: half the distance of the outermost node to the boundary, at most 2e-3
   plan->shell = d.shell > 0.0 ? d.shell : std::min(2e-3, 0.5 * (1.0 - std::fabs(plan->xnodes[0])));
   std::vector<double> A(n * n);
-  space_analysis(n, A.data());
+  if (frac) space_analysis_frac(n, d.alpha, A.data());
+  else space_analysis(n, A.data());
   spmc_status st;
   if ((st = upload(plan, &plan->d_x, plan->xnodes)) != SPMC_OK) { spmc_destroy(plan); return st; }
   if ((st = upload(plan, &plan->d_A, A)) != SPMC_OK) { spmc_destroy(plan); return st; }
+  if (frac) {
+    std::vector<double> T(kFracTable);
+    frac_table(d.alpha, T.data());
+    if ((st = upload(plan, &plan->d_frac, T)) != SPMC_OK) { spmc_destroy(plan); return st; }
+  }
   double ra[kMaxModes], rb[kMaxModes], lam[kMaxModes];
   float raf[kMaxModes], rbf[kMaxModes], lamf[kMaxModes];
   for (int p = 0; p < kMaxModes; ++p) {
@@ -1342,14 +1360,20 @@ spmc_status spmc_set_problem(spmc_plan_t plan, int instance, const spmc_problem*
     if (p.degrees[m] < 1 || p.degrees[m] > d.max_degree) return fail(plan, SPMC_ERR_INVALID, "degree out of range");
   }
   if (p.f_kind != SPMC_F_POLY3 && p.f_kind != SPMC_F_SIN) return fail(plan, SPMC_ERR_INVALID, "bad f_kind");
-  if (p.ex_kind < SPMC_EX_NONE || p.ex_kind > SPMC_EX_SINPLUS) return fail(plan, SPMC_ERR_INVALID, "bad ex_kind");
+  if (p.ex_kind < SPMC_EX_NONE || p.ex_kind > SPMC_EX_FRAC_POLY) return fail(plan, SPMC_ERR_INVALID, "bad ex_kind");
   if (p.bc_kind < SPMC_BC_ZERO || p.bc_kind > SPMC_BC_RAW) return fail(plan, SPMC_ERR_INVALID, "bad bc_kind");
-  if (p.ex_kind >= SPMC_EX_COSTHIRD && p.bc_kind == SPMC_BC_ZERO)
+  if ((p.ex_kind == SPMC_EX_COSTHIRD || p.ex_kind == SPMC_EX_SINPLUS) && p.bc_kind == SPMC_BC_ZERO)
     return fail(plan, SPMC_ERR_INVALID, "ex_kind 4 and 5 have non-zero boundary values: bc_kind LIFT or RAW");
   if (p.bc_kind == SPMC_BC_RAW && d.estimator != SPMC_EST_DIRECT)
     return fail(plan, SPMC_ERR_UNSUPPORTED, "raw boundary data enters through the direct estimator only");
   if (p.bc_kind != SPMC_BC_ZERO && (d.dim > 2 || d.walk_mode != 0))
     return fail(plan, SPMC_ERR_UNSUPPORTED, "boundary data: d <= 2 and the inside-ball walk only");
+  const bool frac_kind = p.ex_kind == SPMC_EX_FRAC_SIN || p.ex_kind == SPMC_EX_FRAC_POLY;
+  if (d.walk_mode == 2 && !(frac_kind || p.ex_kind == SPMC_EX_NONE))
+    return fail(plan, SPMC_ERR_INVALID, "the fractional case takes ex_kind 0, 6 or 7");
+  if (d.walk_mode != 2 && frac_kind) return fail(plan, SPMC_ERR_INVALID, "ex_kind 6 and 7 need the fractional case");
+  if (d.walk_mode == 2 && p.u0_kind != SPMC_U0_NODAL)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "the fractional case takes nodal initial values");
   HostProblem& H = plan->probs[instance];
   bool same_layout = H.set && H.n_int == p.n_intervals &&
                      std::equal(H.deg.begin(), H.deg.end(), p.degrees) &&
@@ -1660,6 +1684,7 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
   const int R = (int)plan->rounds.size();
   if (d.tol > 0.0) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad needs a fixed iteration count (tol <= 0)");
   if (d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: dimensions 1 and 2 only");
+  if (d.walk_mode == 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: not for the fractional case");
   for (const HostProblem& P : plan->probs)
     if (P.ip.bc_kind != SPMC_BC_ZERO || d.estimator != SPMC_EST_RESIDUAL)
       return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: zero boundary data and the residual iteration only");

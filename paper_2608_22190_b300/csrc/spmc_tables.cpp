@@ -130,6 +130,64 @@ void time_analysis(int family, int M, double* B) {
   }
 }
 
+// The fractional case (generalised Jacobi functions (1-x^2)^a P^{(a,a)}_p,
+// a = alpha/2): nodes = zeros of P^{(a,a)}_n; analysis
+// A[p][j] = w_j P_p(x_j) / ((1-x_j^2)^a gamma_p) with the Gauss-Jacobi weights
+// w_j = 2^{2a+1} Gamma(n+a+1)^2 / (n! Gamma(n+2a+1) (1-x_j^2) P_n'(x_j)^2) and
+// gamma_p = 2^{2a+1} Gamma(p+a+1)^2 / ((2p+2a+1) p! Gamma(p+2a+1)).
+static double gj_norm(double a, int p) {
+  return std::exp((2.0 * a + 1.0) * std::log(2.0) + 2.0 * std::lgamma(p + a + 1.0) - std::lgamma(p + 1.0) -
+                  std::lgamma(p + 2.0 * a + 1.0)) / (2.0 * p + 2.0 * a + 1.0);
+}
+static void gj_weights(int n, double a, const double* x, double* w) {
+  const double c = std::exp((2.0 * a + 1.0) * std::log(2.0) + 2.0 * std::lgamma(n + a + 1.0) - std::lgamma(n + 1.0) -
+                            std::lgamma(n + 2.0 * a + 1.0));
+  for (int j = 0; j < n; ++j) {
+    double pn, dpn;
+    jacobi_and_derivative(n, a, a, x[j], &pn, &dpn);
+    w[j] = c / ((1.0 - x[j] * x[j]) * dpn * dpn);
+  }
+}
+void space_nodes_frac(int n, double alpha, double* x) { jacobi_zeros(n, 0.5 * alpha, 0.5 * alpha, x); }
+void space_analysis_frac(int n, double alpha, double* A) {
+  const double a = 0.5 * alpha;
+  std::vector<double> x(n), w(n), P(n + 1);
+  space_nodes_frac(n, alpha, x.data());
+  gj_weights(n, a, x.data(), w.data());
+  for (int j = 0; j < n; ++j) {
+    jacobi_values(n - 1, a, a, x[j], P.data());
+    for (int p = 0; p < n; ++p) A[p * n + j] = w[j] * P[p] / (std::pow(1.0 - x[j] * x[j], a) * gj_norm(a, p));
+  }
+}
+
+// Device table of the fractional case (layout in spmc_tables.h): recurrence
+// P_p = ra_p x P_{p-1} - rb_p P_{p-2} of P^{(a,a)} (p >= 2), the eigenvalues
+// lam_p = Gamma(alpha+p+1)/p! of (-Delta)^{alpha/2} on the basis, and the
+// coefficients s_p of sin(x) = sum_p s_p P^{(a,a)}_p(x) (40-point Gauss-Jacobi
+// quadrature: exact for the sine's Taylor polynomial to degree 79).
+void frac_table(double alpha, double* T) {
+  const double a = 0.5 * alpha;
+  for (int i = 0; i < kFracTable; ++i) T[i] = 0.0;
+  for (int p = 2; p < kFracModes; ++p) {
+    const double c = 2.0 * p + 2.0 * a;
+    T[kFracRa + p] = (c - 1.0) * c / (2.0 * p * (p + 2.0 * a));
+    T[kFracRb + p] = (p + a - 1.0) * (p + a - 1.0) * c / (p * (p + 2.0 * a) * (c - 2.0));
+  }
+  for (int p = 0; p < kFracModes; ++p) T[kFracLam + p] = std::exp(std::lgamma(alpha + p + 1.0) - std::lgamma(p + 1.0));
+  const int nq = kFracModes;
+  std::vector<double> x(nq), w(nq), P(nq + 1);
+  jacobi_zeros(nq, a, a, x.data());
+  gj_weights(nq, a, x.data(), w.data());
+  for (int j = 0; j < nq; ++j) {
+    jacobi_values(nq - 1, a, a, x[j], P.data());
+    for (int p = 0; p < nq; ++p) T[kFracSin + p] += w[j] * std::sin(x[j]) * P[p];
+  }
+  for (int p = 0; p < nq; ++p) T[kFracSin + p] /= gj_norm(a, p);
+  T[kFracA] = a;
+  T[kFracAlpha] = alpha;
+  T[kFracGamma] = std::exp(std::lgamma(1.0 + alpha));
+}
+
 // phi_p(x) = (1-x^2) P^{(1,1)}_p(x), p < n (u0 from coefficients).
 void phi_values(int n, double x, double* phi) {
   std::vector<double> P(n);

@@ -11,4 +11,11 @@ void time_weights(int family, int M, const double* xi, double* w);
 void space_analysis(int n, double* A);                            // a_pj, [p][j]
 void time_analysis(int family, int M, double* B);                 // b_qk, [q][k]
 void phi_values(int n, double x, double* phi);                    // phi_0..phi_{n-1}
+// fractional case (alpha in (0, 2), a = alpha / 2)
+void space_nodes_frac(int n, double alpha, double* x);            // zeros of P^{(a,a)}_n
+void space_analysis_frac(int n, double alpha, double* A);         // [p][j]
+constexpr int kFracModes = 40;
+constexpr int kFracRa = 0, kFracRb = 40, kFracLam = 80, kFracSin = 120, kFracA = 160, kFracAlpha = 161,
+              kFracGamma = 162, kFracTable = 164;                 // Gamma(1 + alpha) at kFracGamma
+void frac_table(double alpha, double* T);
 }  // namespace spmc

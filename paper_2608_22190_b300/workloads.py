@@ -20,6 +20,9 @@ Workloads (sizes as the benchmarks state them; Section 4 examples they stand in 
   w6  2-D non-homogeneous boundary data, u = e^{-0.1 t} prod cos(pi (x_e - 0.3) / 3)
       (different non-zero values on opposite faces), f = sin u + source, lifted,
       T = 20 in 20 intervals of h = 1, 24 x 24 JG x 16 LGL, M = 65536, K = 8
+  w8  1-D fractional Allen-Cahn (Section 4, Ex. 2): d_t u + (-Delta)^{alpha/2} u + u^3 - u = f_add,
+      u = (1-x^2)_+^{alpha/2} sin(x) e^{cos t}/(1+t^2), alpha = 0.4, 10 Jacobi-Gauss (alpha/2, alpha/2)
+      nodes x 7 LGL (M_n = 6), h = 0.5 (0.1..1), alpha-stable walk with N_ref = 20
   w7  1-D long time for the direct estimator and the classical comparison,
       u = e^{-t/4} sin(pi x) + t/2 (boundary data t/2), f = sin u + source, kappa = 1/(4 pi^2),
       T = 20 in 20 intervals of degree 8 (or one interval: the classical single solve)
@@ -40,7 +43,7 @@ import numpy as np
 # enums shared by name with the C-ABI header (values fixed there)
 TIME_LGL, TIME_RADAU_LEFT = 0, 1
 F_POLY3, F_SIN = 0, 1
-EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS = 0, 1, 2, 3, 4, 5
+EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS, EX_FRAC_SIN, EX_FRAC_POLY = range(8)
 BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
 
 
@@ -73,6 +76,7 @@ class Workload:
     shell: float = 0.0          # 0: half the outermost node's distance to the boundary
     max_steps: int = 512
     instances: List[Instance] = field(default_factory=list)
+    alpha: float = 0.0          # (0, 2): the fractional case (alpha-stable walk, d = 1)
 
     @property
     def n_nodes_space(self) -> int:
@@ -173,6 +177,21 @@ def w7(M: int = 16384, K: int = 4, seed: int = 0, n_space: int = 14, degree: int
                     n_ref=40, instances=[inst])
 
 
+def w8(M: int = 4096, K: int = 10, seed: int = 0, n_space: int = 10, degree: int = 6, alpha: float = 0.4,
+       h: float = 0.5, T: float = 5.0, n_ref: int = 20) -> Workload:
+    n_int = int(round(T / h))
+    inst = Instance(t_breaks=uniform_mesh(n_int * h, n_int), degrees=np.full(n_int, degree),
+                    f_coef=(0.0, 1.0, 0.0, -1.0), ex_kind=EX_FRAC_SIN, ex_beta=0.0)
+    return Workload("w8-1d-fractional-allen-cahn", 1, n_space, TIME_LGL, M, K, seed=seed, n_ref=n_ref, n_sub=1,
+                    instances=[inst], alpha=alpha)
+
+
+def frac_nodes(n: int, alpha: float) -> np.ndarray:
+    """Jacobi-Gauss (alpha/2, alpha/2) nodes (scipy), for the closed forms."""
+    import scipy.special as sps
+    return np.sort(sps.roots_jacobi(n, alpha / 2, alpha / 2)[0])
+
+
 def u0_nodal(inst: Instance, grid: np.ndarray) -> np.ndarray:
     """Initial values at the spatial nodes (grid: (S, d) coordinates): the
     closed form at t = 0 of the manufactured solution, or the singular profile
@@ -189,7 +208,22 @@ def u0_nodal(inst: Instance, grid: np.ndarray) -> np.ndarray:
         return np.prod(np.cos(np.pi * (grid - 0.3) / 3.0), axis=1)
     if inst.ex_kind == EX_SINPLUS:
         return np.prod(np.sin(np.pi * grid), axis=1)
+    if inst.ex_kind in (EX_FRAC_SIN, EX_FRAC_POLY):
+        raise ValueError("fractional kinds: use frac_exact with the workload's alpha")
     raise ValueError("instance has no closed-form initial condition")
+
+
+def frac_exact(alpha: float, ex_kind: int, x: np.ndarray, t) -> np.ndarray:
+    """The fractional examples' closed forms at points x (|x| < 1) and times t:
+    6, (1-x^2)^{alpha/2} sin(x) e^{cos t}/(1+t^2) (Section 4, Ex. 2); 7,
+    (1+t)(1-x^2)^{alpha/2}(1 + P_1^{(a,a)}(x)/2), P_1 = (alpha/2 + 1) x.
+    Returns (len(t), len(x))."""
+    a = alpha / 2
+    t = np.atleast_1d(np.asarray(t, dtype=float))[:, None]
+    w = (1 - x ** 2) ** a
+    if ex_kind == EX_FRAC_SIN:
+        return w * np.sin(x) * np.exp(np.cos(t)) / (1 + t ** 2)
+    return (1 + t) * w * (1 + 0.5 * (a + 1) * x)
 
 
 def time_nodes_reference(family: int, Mt: int) -> np.ndarray:
