@@ -351,6 +351,7 @@ def run_ours(args):
         line["w4_5d"] = w4_leg(args, peaks)
         line["w5_adjoint"] = w5_leg(args)
         line["boundary"] = boundary_leg(args)
+        line["fractional"] = fractional_leg(args)
         line["cpu_baseline"] = cpu_baseline(wl)
     plan.close()
     if rank == 0:
@@ -678,6 +679,53 @@ def boundary_leg(args, tol=1e-6):
     out["w7_hp_direct_raw"] = solve_err(W.w7(bc_kind=W.BC_RAW), 1)
     out["w7_classical_residual_lifted"] = solve_err(W.w7(bc_kind=W.BC_LIFT, n_intervals=1, degree=16, K=16), 0)
     out["w7_classical_direct_raw"] = solve_err(W.w7(bc_kind=W.BC_RAW, n_intervals=1, degree=16, K=16), 1)
+    return out
+
+
+def fractional_leg(args):
+    """The fractional Allen-Cahn problem of Section 4, Ex. 2 (alpha-stable walk,
+    generalised Jacobi functions; 10 Jacobi-Gauss (alpha/2, alpha/2) nodes x 7 LGL,
+    f = u - u^3 + source, exact u = (1-x^2)^{alpha/2} sin(x) e^{cos t}/(1+t^2)),
+    mixed, M = 4096, K = 12 iterations per interval, T = 10: the L-inf error of
+    every node against the closed form for time steps h = 1, 0.5, 0.25 (Fig.
+    EX2, left) at alpha = 0.4 and 1.2, and the classical single interval over
+    [0, 10] (degree 16, K = 24) at alpha = 0.4 (Fig. EX2, right); GPU time of
+    the solve (CUDA events) and node-samples/s."""
+    import numpy as np
+    import torch
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    from paper_2608_22190_b300.api import Plan
+    out = {}
+
+    def run(alpha, h, T=10.0, degree=6, K=12, M=4096):
+        wl = W.w8(M=M, K=K, alpha=alpha, h=h, T=T, degree=degree)
+        plan = Plan.from_workload(wl, precision=L.MIXED)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.solve()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        x = plan.space_nodes()
+        inst = wl.instances[0]
+        errs = []
+        for m in range(len(inst.degrees)):
+            xi = W.time_nodes_reference(wl.time_family, degree)
+            t = inst.t_breaks[m] + (xi + 1) * 0.5 * (inst.t_breaks[m + 1] - inst.t_breaks[m])
+            errs.append(float(np.abs(plan.get_nodes(0, m).cpu().numpy() - W.frac_exact(alpha, W.EX_FRAC_SIN, x, t)).max()))
+        plan.close()
+        ns = sum(int(d) * wl.n_space * M * K for d in inst.degrees)
+        return {"linf": max(errs), "linf_final_interval": errs[-1], "ms": ms, "node_samples_per_s": ns / (ms / 1e3),
+                "intervals": len(errs), "h": h, "alpha": alpha, "M": M, "K": K}
+    for alpha in (0.4, 1.2):
+        for h in (1.0, 0.5, 0.25):
+            out[f"alpha{alpha}_h{h}"] = run(alpha, h)
+    for T in (2.0, 10.0):
+        try:
+            out[f"alpha0.4_classical_single_interval_T{T:g}"] = run(0.4, T, T=T, degree=16, K=24)
+        except L.SpmcError as e:   # the Picard iteration over one long interval does not contract
+            out[f"alpha0.4_classical_single_interval_T{T:g}"] = {"diverged": True, "status": str(e)}
     return out
 
 

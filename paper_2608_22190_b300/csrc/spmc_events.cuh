@@ -560,6 +560,104 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
   }
 }
 
+// The fixed-radius walk (walk_mode 1, Lemma Xlocation, Eqs. indexL and
+// interIQ) and the alpha-stable walk of the fractional case (walk_mode 2), one
+// thread per walk: the walk's steps, the residual at each step centre X_q at
+// time t_{n,l} - q Delta from the slice of step q (read through the cache), and
+// the walk's Q = Delta sum_q r(X_q) counted while X_{q+1} stays inside Omega.
+// Walk ids are node M + sample (sample fastest), node = ti S + j, so the walks of
+// a node are adjacent lanes: their Q are summed exactly per node (fixed-point
+// run sums, as in the event sweep) into the node's limb counters.
+template <int D, int NMAX, typename R>
+__global__ void __launch_bounds__(256) fixed_walk_kernel(SweepArgs a, long long n_walks,
+                                                         unsigned long long* __restrict__ acc) {
+  const int S = a.S, n = a.n;
+  const R kappa = (R)a.kappa;
+  const R* slices = reinterpret_cast<const R*>(a.slices);
+  const unsigned int lane = threadIdx.x & 31;
+  unsigned long long capped = 0, points = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long top = (n_walks + 31) / 32 * 32;   // whole warps: the run sums are warp-wide
+  for (long long wid = (long long)blockIdx.x * blockDim.x + threadIdx.x; wid < top; wid += stride) {
+    const bool has = wid < n_walks;
+    __int128 val = 0;
+    unsigned int key = 0xffffffffu;
+    if (has) {
+      const long long node = wid / a.M;
+      const long long ti = node / S;
+      const int j = (int)(node - ti * S);
+      const TimeNode tn = a.tn[ti];
+      const InstanceParams ip = a.ip[tn.inst];
+      WalkStream ws;
+      ws.k0 = a.k0; ws.k1 = a.k1;
+      ws.tag = ((uint32_t)(tn.inst & 0xfff) << 20) | ((uint32_t)(a.interval & 0x3ff) << 10) |
+               (uint32_t)(a.iteration & 0x3ff);
+      ws.node = (uint32_t)(tn.ell * S + j);
+      ws.sample = (uint32_t)(wid - node * a.M);
+      const R sdur = Ar<R>::sub((R)tn.t_node, (R)tn.t0);
+      const R delta = Ar<R>::div(sdur, (R)tn.nstar);
+      const R J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
+      double r_stable = 0.0;
+      if (a.walk_mode == 2)
+        r_stable = pow(a.kappa * ((tn.t_node - tn.t0) / (double)tn.nstar) * a.frac[kFracGammaD],
+                       1.0 / a.frac[kFracAlphaD]);
+      R X[D];
+      int jr = j;
+#pragma unroll
+      for (int e = 0; e < D; ++e) { X[e] = (R)a.xnodes[jr % n]; jr /= n; }
+      R Q = R(0);
+      for (int q = 0; q < tn.nstar; ++q) {
+        if (q >= a.max_steps) { ++capped; break; }
+        R Xn[D];
+        bool inside = true;
+        if (a.walk_mode == 2) {
+          const Philox4 b = ws.block((uint32_t)q >> 1);
+          const double Jq = stable_jump_d(r_stable, a.frac[kFracAD], U01<double>::one(b.v[(2 * q + 1) & 3]));
+          const double xn = (double)X[0] + ((b.v[(2 * q) & 3] >> 31) ? -Jq : Jq);
+          inside = xn > -1.0 && xn < 1.0;
+          Xn[0] = (R)xn;
+        } else {
+          R th[D];
+          literal_direction<D, R>(ws, q, th);
+#pragma unroll
+          for (int e = 0; e < D; ++e) {
+            Xn[e] = Ar<R>::add(X[e], Ar<R>::mul(J, th[e]));
+            if (!(Xn[e] > R(-1) && Xn[e] < R(1))) inside = false;
+          }
+        }
+        if (!inside) break;
+        const long long sl = tn.slice_base + q;
+        const R* sc = slices + sl * a.sl_stride;
+        const SliceInfo si = a.sinfo[sl];
+        R res;
+        if (D == 1 && a.walk_mode == 2)
+          res = residual_frac<R>(ip, kappa, n, sc, sc + a.half, X[0], (R)si.Tt, (R)si.dTt, a.frac);
+        else
+          res = residual_at<D, NMAX, R>(ip, kappa, n, sc, sc + a.half, X, (R)si.Tt, (R)si.dTt);
+        Q += delta * res;
+        ++points;
+#pragma unroll
+        for (int e = 0; e < D; ++e) X[e] = Xn[e];
+      }
+      if (!fix_from<R>(Q, val)) atomicOr(a.status, 1);
+      key = (unsigned int)node;
+    }
+    // per-node sums: walks of a node are adjacent lanes
+    val = warp_run_sum(val, key, lane);
+    const unsigned int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (has && (lane == 0 || kprev != key)) fix_atomic_add(acc + 4 * (long long)key, val);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    points += __shfl_xor_sync(0xffffffffu, points, o);
+    capped += __shfl_xor_sync(0xffffffffu, capped, o);
+  }
+  if (lane == 0) {
+    if (points) atomicAdd(&a.counters[0], points);
+    if (capped) atomicAdd(&a.counters[1], capped);
+  }
+}
+
 // The adjoint of one iteration's sweep on the event pipeline (the forward
 // iteration's own events: same walks, weights and points).  One block per
 // slice.  Per event p at node i: cw = lambda_i w_p / M, u* from the slice's C,

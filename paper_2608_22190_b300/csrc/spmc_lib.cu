@@ -893,6 +893,39 @@ __global__ void counters_snapshot_kernel(const unsigned long long* __restrict__ 
 
 // One residual iteration on interval r for every instance that has it,
 // enqueued without synchronising the stream.
+// The fixed-radius and alpha-stable walks (walk_mode 1, 2; d <= 2) run one
+// thread per walk unless the cohort kernel is chosen.
+bool uses_fixed_walk(spmc_plan_t plan) {
+  return plan->d.dim <= 2 && plan->d.walk_mode >= 1 && plan->sweep_mode != SPMC_SWEEP_COHORT;
+}
+
+template <typename R>
+spmc_status fixed_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd, int interval, int iteration) {
+  const long long n_tn = (long long)rd.tn.size(), S = plan->S;
+  if (plan->acc_cap < n_tn * S) {
+    pfree(plan, plan->d_acc);
+    plan->d_acc = nullptr; plan->acc_cap = 0;
+    SPMC_CUDA(pmalloc(plan, (void**)&plan->d_acc, 4 * sizeof(unsigned long long) * n_tn * S));
+    plan->acc_cap = n_tn * S;
+  }
+  SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, 4 * sizeof(unsigned long long) * n_tn * S, stream));
+  if (n_tn * S > 0xffffffffLL) return fail(plan, SPMC_ERR_UNSUPPORTED, "fixed walks: too many nodes");
+  const SweepArgs a = sweep_args(plan, rd, interval, iteration);
+  const long long n_walks = n_tn * S * plan->d.M;
+  int dev = 0, sms = 0;
+  SPMC_CUDA(cudaGetDevice(&dev));
+  SPMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned blocks = (unsigned)std::max(1LL, std::min((n_walks + 255) / 256, (long long)sms * 16));
+  const int n = plan->d.n_space;
+  if (plan->d.dim == 1) fixed_walk_kernel<1, 32, R><<<blocks, 256, 0, stream>>>(a, n_walks, plan->d_acc);
+  else if (n <= 8) fixed_walk_kernel<2, 8, R><<<blocks, 256, 0, stream>>>(a, n_walks, plan->d_acc);
+  else if (n <= 16) fixed_walk_kernel<2, 16, R><<<blocks, 256, 0, stream>>>(a, n_walks, plan->d_acc);
+  else if (n <= 24) fixed_walk_kernel<2, 24, R><<<blocks, 256, 0, stream>>>(a, n_walks, plan->d_acc);
+  else fixed_walk_kernel<2, 32, R><<<blocks, 256, 0, stream>>>(a, n_walks, plan->d_acc);
+  SPMC_CUDA(cudaGetLastError());
+  return SPMC_OK;
+}
+
 spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   Round& rd = plan->rounds[r];
   const int S = plan->S;
@@ -903,6 +936,8 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
   if (pst != SPMC_OK) return pst;
   bool fp64 = plan->d.precision == SPMC_FP64;
   const bool events = uses_events(plan);
+  const bool fixed = uses_fixed_walk(plan);
+  const bool exact_sums = events || fixed;   // per-node limb counters (else per-chunk FP64 sums)
   std::pair<cudaEvent_t, cudaEvent_t> tev{nullptr, nullptr};
   if (events && plan->timing) {
     if (!plan->ev_free.empty()) { tev = plan->ev_free.back(); plan->ev_free.pop_back(); }
@@ -910,8 +945,10 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
     SPMC_CUDA(cudaEventRecord(tev.first, stream));
   }
   spmc_status st = events ? event_sweep(plan, stream, rd, r, iteration)
-                          : (fp64 ? dispatch_sweep<double>(plan, stream, rd, r, iteration)
-                                  : dispatch_sweep<float>(plan, stream, rd, r, iteration));
+                   : fixed ? (fp64 ? fixed_sweep_t<double>(plan, stream, rd, r, iteration)
+                                   : fixed_sweep_t<float>(plan, stream, rd, r, iteration))
+                           : (fp64 ? dispatch_sweep<double>(plan, stream, rd, r, iteration)
+                                   : dispatch_sweep<float>(plan, stream, rd, r, iteration));
   if (st != SPMC_OK) return st;
   if (events && plan->timing) {
     SPMC_CUDA(cudaEventRecord(tev.second, stream));
@@ -930,7 +967,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
       plan->eps_cap = nn;
     }
     if (!plan->d_omega) SPMC_CUDA(pmalloc(plan, (void**)&plan->d_omega, sizeof(double) * plan->d.batch));
-    if (events)
+    if (exact_sums)
       eps_out_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
           plan->d_acc, plan->d_eps_cur, 0, nn, 1.0 / (double)plan->d.M, plan->d_status, rd.d_tn, plan->d_U, S,
           plan->d.estimator, plan->d_abort);
@@ -944,7 +981,7 @@ spmc_status iterate_once(spmc_plan_t plan, cudaStream_t stream, int r) {
                                                                     plan->d_abort);
     SPMC_CUDA(cudaGetLastError());
   } else if (nn > 0) {
-    if (events)
+    if (exact_sums)
       update_fixed_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(
           rd.d_tn, plan->d_acc, plan->d_U, nullptr, plan->d_maxeps, plan->d_status, nn, S, 1.0 / (double)plan->d.M,
           plan->d.estimator, plan->d_abort);
