@@ -34,7 +34,7 @@ class Problem(C.Structure):
         ("f_kind", C.c_int), ("f_coef", C.c_double * 4), ("f_scale", C.c_double),
         ("ex_kind", C.c_int), ("ex_beta", C.c_double), ("n_threads", C.c_int),
         ("walk_mode", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int), ("n_sub", C.c_int),
-        ("bc_kind", C.c_int), ("estimator", C.c_int), ("alpha", C.c_double),
+        ("bc_kind", C.c_int), ("estimator", C.c_int), ("alpha", C.c_double), ("basis", C.c_int),
     ]
 
 
@@ -83,6 +83,8 @@ def lib():
             "orc_ibeta": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "orc_ibeta_inv": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "orc_stable_jump": (C.c_double, [C.c_double, C.c_double, C.c_double]),
+            "orc_cheb": (None, [C.c_int, C.c_double, D, D]),
+            "orc_cgl_nodes": (None, [C.c_int, D]),
             "orc_reconstruct": (None, [P, C.c_int, C.c_double, D, D, D]),
             "orc_eval": (None, [P, C.c_int, D, D, D, C.c_double, D, D, D]),
             "orc_residual": (C.c_double, [P, C.c_int, C.c_double, C.c_double, D, D, D, C.c_double]),
@@ -122,7 +124,7 @@ BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
 EST_RESIDUAL, EST_DIRECT = 0, 1
 EX_FRAC_SIN, EX_FRAC_POLY = 6, 7
 WALK_BALLS, WALK_FIXED, WALK_STABLE = 0, 1, 2
-TIME_LGL, TIME_RADAU_LEFT = 0, 1
+TIME_LGL, TIME_RADAU_LEFT, TIME_CHEB = 0, 1, 2
 
 
 @dataclass
@@ -149,6 +151,7 @@ class Spec:
     bc_kind: int = 0             # 0 g = 0; 1 lifted (Gordon-Hall); 2 g at absorption (direct estimator)
     estimator: int = 0           # 0 residual iteration; 1 direct estimator S_i (Eq. Phi_ast)
     alpha: float = 0.0           # 0: -kappa Delta; (0, 2): kappa (-Delta)^{alpha/2} (d = 1, walk_mode 2)
+    basis: int = 0               # 0 Jacobi/Legendre; 1 Chebyshev in space and time (time_family 2)
 
     def struct(self) -> Problem:
         p = Problem()
@@ -159,7 +162,7 @@ class Spec:
             p.f_coef[i] = c
         p.n_threads = self.n_threads
         p.walk_mode, p.shell, p.max_steps, p.n_sub = self.walk_mode, self.shell, self.max_steps, self.n_sub
-        p.bc_kind, p.estimator, p.alpha = self.bc_kind, self.estimator, self.alpha
+        p.bc_kind, p.estimator, p.alpha, p.basis = self.bc_kind, self.estimator, self.alpha, self.basis
         return p
 
 
@@ -190,7 +193,22 @@ def radau_left_nodes(M):
     return x, w
 
 
+def cgl_nodes(M):
+    xi = np.zeros(M + 1)
+    lib().orc_cgl_nodes(M, _dp(xi))
+    return xi, np.zeros(M + 1)
+
+
+def cheb(m, x):
+    """T_0..T_m at x and their second derivatives."""
+    T, T2 = np.zeros(m + 1), np.zeros(m + 1)
+    lib().orc_cheb(m, float(x), _dp(T), _dp(T2))
+    return T, T2
+
+
 def time_nodes(family, M):
+    if family == TIME_CHEB:
+        return cgl_nodes(M)
     return lgl_nodes(M) if family == TIME_LGL else radau_left_nodes(M)
 
 

@@ -387,9 +387,35 @@ void orc_radau_left_nodes(int M, double* xi, double* w) {
   }
 }
 
+/* Chebyshev polynomials T_0..T_m at x and their second derivatives:
+ * T_{k+1} = 2x T_k - T_{k-1}, T'_{k+1} = 2 T_k + 2x T'_k - T'_{k-1},
+ * T''_{k+1} = 4 T'_k + 2x T''_k - T''_{k-1}. */
+void orc_cheb(int m, double x, double* T, double* T2) {
+  double T1[ORC_MAXN + 4];
+  T[0] = 1.0; T1[0] = 0.0; T2[0] = 0.0;
+  if (m >= 1) { T[1] = x; T1[1] = 1.0; T2[1] = 0.0; }
+  for (int k = 1; k < m; ++k) {
+    T[k + 1] = 2.0 * x * T[k] - T[k - 1];
+    T1[k + 1] = 2.0 * T[k] + 2.0 * x * T1[k] - T1[k - 1];
+    T2[k + 1] = 4.0 * T1[k] + 2.0 * x * T2[k] - T2[k - 1];
+  }
+}
+
+/* Chebyshev-Gauss-Lobatto points -cos(pi k / M), k = 0..M (the Chebyshev
+ * basis of the remark on quasi-linear reconstruction after Algorithm 1). */
+void orc_cgl_nodes(int M, double* xi) {
+  for (int k = 0; k <= M; ++k) xi[k] = -cos(ORC_PI * k / M);
+  xi[0] = -1.0;
+  xi[M] = 1.0;
+}
+
 void orc_time_nodes(int family, int M, double* xi, double* w) {
   if (family == 0) orc_lgl_nodes(M, xi, w);
-  else orc_radau_left_nodes(M, xi, w);
+  else if (family == 1) orc_radau_left_nodes(M, xi, w);
+  else {
+    orc_cgl_nodes(M, xi);
+    for (int k = 0; k <= M; ++k) w[k] = 0.0;   /* not used by the Chebyshev transform */
+  }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -410,9 +436,25 @@ void orc_space_analysis(int n, double* A) {
 }
 
 /* B[q*(M+1) + k] = L_q(xi_k) w_k / gamma_q on the reference interval:
- * gamma_q = 2/(2q+1) for q < M, gamma_M = sum_k L_M(xi_k)^2 w_k. */
+ * gamma_q = 2/(2q+1) for q < M, gamma_M = sum_k L_M(xi_k)^2 w_k.
+ * Chebyshev family (2): the discrete Chebyshev transform (DCT-I) of the
+ * values at the CGL points, B[q][k] = 2 T_q(xi_k) / (M c_q c~_k), c_q = 2 for
+ * q = 0, M (else 1), c~_k likewise (the end values count half). */
 void orc_time_analysis(int family, int M, double* B) {
   double xi[ORC_MAXN + 1], w[ORC_MAXN + 1], L[ORC_MAXN + 2];
+  if (family == 2) {
+    double T[ORC_MAXN + 4], T2[ORC_MAXN + 4];
+    orc_cgl_nodes(M, xi);
+    for (int k = 0; k <= M; ++k) {
+      orc_cheb(M, xi[k], T, T2);
+      double ck = (k == 0 || k == M) ? 2.0 : 1.0;
+      for (int q = 0; q <= M; ++q) {
+        double cq = (q == 0 || q == M) ? 2.0 : 1.0;
+        B[q * (M + 1) + k] = 2.0 * T[q] / (M * cq * ck);
+      }
+    }
+    return;
+  }
   double Lv[(ORC_MAXN + 1) * (ORC_MAXN + 1)];
   orc_time_nodes(family, M, xi, w);
   for (int k = 0; k <= M; ++k) {
@@ -460,6 +502,8 @@ typedef struct {
                        S_i of Eq. Phi_ast (Picard iteration, Eq. linearized_func) */
   double alpha;     /* 0: L = -kappa Delta; in (0, 2): L = kappa (-Delta)^{alpha/2} (d = 1, walk_mode 2,
                        generalised Jacobi functions with a = alpha/2) */
+  int basis;        /* 0: Jacobi/Legendre (Section 2.3); 1: Chebyshev in space and time (time_family 2):
+                       CGL points, phi_p = T_p - T_{p+2}, T_q in time, coefficients by the DCT-I */
 } orc_problem;
 
 static int is_frac(const orc_problem* pb) { return pb->alpha > 0.0 && pb->alpha < 2.0; }
@@ -467,7 +511,12 @@ static int is_frac(const orc_problem* pb) { return pb->alpha > 0.0 && pb->alpha 
 /* Spatial nodes of the problem: Jacobi-Gauss (1,1), or (a,a) in the fractional case. */
 void orc_space_nodes(const orc_problem* pb, double* x, double* w) {
   if (is_frac(pb)) orc_gj_nodes(pb->n_space, 0.5 * pb->alpha, x, w);
-  else orc_jg11_nodes(pb->n_space, x, w);
+  else if (pb->basis == 1) {
+    /* the interior Chebyshev-Gauss-Lobatto points -cos(pi j / (n+1)), j = 1..n */
+    double xx[ORC_MAXN + 2];
+    orc_cgl_nodes(pb->n_space + 1, xx);
+    for (int j = 0; j < pb->n_space; ++j) { x[j] = xx[j + 1]; w[j] = 0.0; }
+  } else orc_jg11_nodes(pb->n_space, x, w);
 }
 
 /* The space analysis matrix of the problem: (1,1) as above, or in the
@@ -475,6 +524,23 @@ void orc_space_nodes(const orc_problem* pb, double* x, double* w) {
  * (Gauss-Jacobi (a,a) quadrature of u (1-x^2)^{-a} P_p against the weight). */
 void orc_space_analysis_pb(const orc_problem* pb, double* A) {
   int n = pb->n_space;
+  if (pb->basis == 1) {
+    /* Chebyshev: the DCT-I of (0, u_1..u_n, 0) at the N+1 = n+2 CGL points gives
+     * a_k = (2 / (N c_k)) sum_j u_j T_k(x_j) (c_0 = c_N = 2); the interpolant
+     * vanishes at +-1, so a = sum c_p (T_p - T_{p+2}) with c_p = a_p + c_{p-2}. */
+    int N = n + 1;
+    double x[ORC_MAXN], w[ORC_MAXN], T[ORC_MAXN + 4], T2[ORC_MAXN + 4];
+    orc_space_nodes(pb, x, w);
+    for (int j = 0; j < n; ++j) {
+      orc_cheb(N, x[j], T, T2);
+      for (int p = 0; p < n; ++p) {
+        double acc = 0.0;
+        for (int k = p; k >= 0; k -= 2) acc += 2.0 * T[k] / (N * (k == 0 ? 2.0 : 1.0));
+        A[p * n + j] = acc;
+      }
+    }
+    return;
+  }
   if (!is_frac(pb)) { orc_space_analysis(n, A); return; }
   double a = 0.5 * pb->alpha, x[ORC_MAXN], w[ORC_MAXN], P[ORC_MAXN + 2];
   orc_gj_nodes(n, a, x, w);
@@ -703,12 +769,18 @@ void orc_reconstruct(const orc_problem* pb, int Mt, double h, const double* U, d
     double* t = cur; cur = nxt; nxt = t;
   }
   memcpy(cu, cur, sizeof(double) * tot);
-  /* d/dt: ct_q = (2/h)(2q+1) sum_{l>q, l+q odd} cu_l  (Legendre derivative identity) */
+  /* d/dt: ct_q = (2/h)(2q+1) sum_{l>q, l+q odd} cu_l  (Legendre derivative identity);
+   * Chebyshev: ct_q = (2/h)(2/c_q) sum_{l>q, l+q odd} l cu_l, c_0 = 2, else 1 */
   for (int q = 0; q <= Mt; ++q)
     for (int64_t p = 0; p < S; ++p) {
       double acc = 0.0;
-      for (int l = q + 1; l <= Mt; l += 2) acc += cu[l * S + p];
-      ct[q * S + p] = (2.0 / h) * (2.0 * q + 1.0) * acc;
+      if (pb->basis == 1) {
+        for (int l = q + 1; l <= Mt; l += 2) acc += l * cu[l * S + p];
+        ct[q * S + p] = (2.0 / h) * (q == 0 ? 1.0 : 2.0) * acc;
+      } else {
+        for (int l = q + 1; l <= Mt; l += 2) acc += cu[l * S + p];
+        ct[q * S + p] = (2.0 / h) * (2.0 * q + 1.0) * acc;
+      }
     }
   free(A); free(B); free(cur); free(nxt);
 }
@@ -723,7 +795,13 @@ void orc_eval(const orc_problem* pb, int Mt, const double* cu, const double* ct,
   double phi[ORC_MAXD][ORC_MAXN + 2], P[ORC_MAXD][ORC_MAXN + 2], L[ORC_MAXN + 2], lam[ORC_MAXN + 2];
   for (int p = 0; p < n; ++p) lam[p] = is_frac(pb) ? orc_frac_lambda(pb->alpha, p) : (p + 1.0) * (p + 2.0);
   for (int e = 0; e < d; ++e) {
-    if (is_frac(pb)) {
+    if (pb->basis == 1) {
+      /* phi_p = T_p - T_{p+2}; -phi_p'' = T''_{p+2} - T''_p, kept in P with lam = 1 */
+      double T[ORC_MAXN + 4], T2[ORC_MAXN + 4];
+      orc_cheb(n + 1, x[e], T, T2);
+      for (int p = 0; p < n; ++p) { phi[e][p] = T[p] - T[p + 2]; P[e][p] = T2[p + 2] - T2[p]; }
+      for (int p = 0; p < n; ++p) lam[p] = 1.0;
+    } else if (is_frac(pb)) {
       /* phi_p = (1-x^2)^a P_p^{(a,a)}; (-Delta)^{alpha/2} phi_p = lam_p P_p^{(a,a)} */
       double a = 0.5 * pb->alpha;
       orc_jacobi_aa(n - 1, a, x[e], P[e]);
@@ -734,7 +812,8 @@ void orc_eval(const orc_problem* pb, int Mt, const double* cu, const double* ct,
       orc_phi(n - 1, x[e], phi[e]);
     }
   }
-  orc_legendre(Mt, xi, L);
+  if (pb->basis == 1) { double T2[ORC_MAXN + 4]; orc_cheb(Mt, xi, L, T2); }
+  else orc_legendre(Mt, xi, L);
   double u = 0.0, dtu = 0.0, mlap = 0.0;
   for (int q = 0; q <= Mt; ++q)
     for (int64_t idx = 0; idx < S; ++idx) {
