@@ -686,7 +686,7 @@ def fractional_leg(args):
     """The fractional Allen-Cahn problem of Section 4, Ex. 2 (alpha-stable walk,
     generalised Jacobi functions; 10 Jacobi-Gauss (alpha/2, alpha/2) nodes x 7 LGL,
     f = u - u^3 + source, exact u = (1-x^2)^{alpha/2} sin(x) e^{cos t}/(1+t^2)),
-    mixed, M = 4096, K = 12 iterations per interval, T = 10: the L-inf error of
+    mixed, M = 2048, K = 12 iterations per interval, T = 10: the L-inf error of
     every node against the closed form for time steps h = 1, 0.5, 0.25 (Fig.
     EX2, left) at alpha = 0.4 and 1.2, and the classical single interval over
     [0, 10] (degree 16, K = 24) at alpha = 0.4 (Fig. EX2, right); GPU time of
@@ -698,7 +698,7 @@ def fractional_leg(args):
     from paper_2608_22190_b300.api import Plan
     out = {}
 
-    def run(alpha, h, T=10.0, degree=6, K=12, M=4096):
+    def run(alpha, h, T=10.0, degree=6, K=12, M=2048):
         wl = W.w8(M=M, K=K, alpha=alpha, h=h, T=T, degree=degree)
         plan = Plan.from_workload(wl, precision=L.MIXED)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

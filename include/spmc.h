@@ -45,7 +45,8 @@ typedef enum {
   SPMC_ERR_NONFINITE = 6     /* a non-finite eps was produced */
 } spmc_status;
 
-enum { SPMC_TIME_LGL = 0, SPMC_TIME_RADAU_LEFT = 1 };     /* time nodes per interval */
+enum { SPMC_TIME_LGL = 0, SPMC_TIME_RADAU_LEFT = 1, SPMC_TIME_CHEB = 2 };   /* time nodes per interval */
+enum { SPMC_BASIS_JACOBI = 0, SPMC_BASIS_CHEB = 1 };       /* spectral basis */
 enum { SPMC_FP64 = 0, SPMC_MIXED = 1 };                    /* sweep arithmetic */
 enum { SPMC_F_POLY3 = 0, SPMC_F_SIN = 1 };                 /* reaction f(u) */
 enum { SPMC_EX_NONE = 0, SPMC_EX_SIN = 1, SPMC_EX_COSHALF = 2, SPMC_EX_POLY = 3,
@@ -104,6 +105,14 @@ typedef struct {
                                radius r = (kappa Delta Gamma(1+alpha))^{1/alpha} around the current point,
                                at distance r / sqrt(U), U ~ Beta(alpha/2, 1-alpha/2), in direction +-1;
                                the residual at the step centres (Eqs. indexL, interIQ); the cohort sweep. */
+  int basis;                /* SPMC_BASIS_JACOBI (0): Jacobi-Gauss (1,1) nodes, Babuska-Shen basis, Legendre
+                               in time (Section 2.3).  SPMC_BASIS_CHEB (1): the Chebyshev basis of the remark
+                               on quasi-linear reconstruction after Algorithm 1, with time_family
+                               SPMC_TIME_CHEB: interior Chebyshev-Gauss-Lobatto points in space, phi_p =
+                               T_p - T_{p+2}, T_q in time at the CGL points; coefficients by the discrete
+                               Chebyshev transform (DCT-I, through the FFT of the even extension for
+                               power-of-two lengths); d <= 2, the inside-ball walk, the event sweep with
+                               the FP64/FP32 evaluation (not the tensor-core one). */
 } spmc_plan_desc;
 enum { SPMC_WALK_BALLS = 0, SPMC_WALK_FIXED = 1, SPMC_WALK_STABLE = 2 };
 

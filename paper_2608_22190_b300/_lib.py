@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libspmc.so")
 SPMC_OK, SPMC_ERR_INVALID, SPMC_ERR_UNSUPPORTED, SPMC_ERR_CUDA, SPMC_ERR_OOM, SPMC_ERR_TIMEOUT, \
     SPMC_ERR_NONFINITE = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5: "TIMEOUT", 6: "NONFINITE"}
-TIME_LGL, TIME_RADAU_LEFT = 0, 1
+TIME_LGL, TIME_RADAU_LEFT, TIME_CHEB = 0, 1, 2
+BASIS_JACOBI, BASIS_CHEB = 0, 1
 FP64, MIXED = 0, 1
 F_POLY3, F_SIN = 0, 1
 EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS, EX_FRAC_SIN, EX_FRAC_POLY = range(8)
@@ -33,7 +34,7 @@ class PlanDesc(C.Structure):
         ("max_degree", C.c_int), ("M", C.c_longlong), ("K", C.c_int), ("tol", C.c_double),
         ("n_ref", C.c_int), ("n_sub", C.c_int), ("shell", C.c_double), ("max_steps", C.c_int),
         ("kappa", C.c_double), ("seed", C.c_ulonglong), ("precision", C.c_int), ("batch", C.c_int),
-        ("walk_mode", C.c_int), ("estimator", C.c_int), ("alpha", C.c_double),
+        ("walk_mode", C.c_int), ("estimator", C.c_int), ("alpha", C.c_double), ("basis", C.c_int),
     ]
 
 

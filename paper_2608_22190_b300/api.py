@@ -26,7 +26,7 @@ def _stream_ptr(stream) -> Optional[int]:
 class Plan:
     def __init__(self, dim, n_space, time_family, max_intervals, max_degree, M, K, tol=0.0, n_ref=80, n_sub=4,
                  shell=1e-4, max_steps=512, kappa=1.0, seed=0, precision=L.FP64, batch=1, walk_mode=L.WALK_BALLS,
-                 estimator=L.EST_RESIDUAL, alpha=0.0):
+                 estimator=L.EST_RESIDUAL, alpha=0.0, basis=L.BASIS_JACOBI):
         d = L.PlanDesc()
         d.dim, d.n_space, d.time_family = dim, n_space, time_family
         d.max_intervals, d.max_degree, d.M, d.K, d.tol = max_intervals, max_degree, M, K, tol
@@ -35,6 +35,7 @@ class Plan:
         d.walk_mode = walk_mode
         d.estimator = estimator
         d.alpha = alpha
+        d.basis = basis
         self.desc = d
         self._h = C.c_void_p()
         L.check(L.lib.spmc_plan(C.byref(d), C.byref(self._h)))
@@ -84,6 +85,8 @@ class Plan:
                   kappa=wl.kappa, seed=wl.seed, precision=precision, batch=len(insts))
         if getattr(wl, "alpha", 0.0):
             kw.update(alpha=wl.alpha, walk_mode=L.WALK_STABLE)
+        if wl.time_family == L.TIME_CHEB:
+            kw.update(basis=L.BASIS_CHEB)
         kw.update(overrides)
         plan = cls(**kw)
         grid = plan.node_grid()

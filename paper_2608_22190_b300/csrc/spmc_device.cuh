@@ -557,6 +557,66 @@ __device__ __forceinline__ void slice_parts(R kappa, int n, const R* __restrict_
   u_out = u;
   G_out = G;
 }
+// The Chebyshev basis phi_p = T_p - T_{p+2} (p < n) and its second derivatives
+// at y, from T_{k+1} = 2y T_k - T_{k-1} and the recurrences of T' and T''.
+template <int NMAX, typename R>
+__device__ __forceinline__ void cheb_basis(int n, R y, R* phi, R* phi2) {
+  R T[NMAX + 2], T2[NMAX + 2];
+  R t1m = R(0), t1 = R(1);   // T'_{k-1}, T'_k
+  T[0] = R(1); T2[0] = R(0);
+  T[1] = y; T2[1] = R(0);
+#pragma unroll
+  for (int k = 1; k < NMAX + 1; ++k) {
+    T[k + 1] = R(2) * y * T[k] - T[k - 1];
+    const R t1n = R(2) * T[k] + R(2) * y * t1 - t1m;
+    T2[k + 1] = R(4) * t1 + R(2) * y * T2[k] - T2[k - 1];
+    t1m = t1;
+    t1 = t1n;
+  }
+#pragma unroll
+  for (int p = 0; p < NMAX; ++p) {
+    phi[p] = (p < n) ? T[p] - T[p + 2] : R(0);
+    phi2[p] = (p < n) ? T2[p] - T2[p + 2] : R(0);
+  }
+}
+
+// u* and G = -d_t u* + kappa Delta u* at y from a slice in the Chebyshev basis
+// (same layout as the Jacobi slices: C, H as coefficients of phi, d = 2 rows [p_x][p_y]).
+template <int D, int NMAX, typename R>
+__device__ __forceinline__ void slice_parts_cheb(R kappa, int n, const R* __restrict__ sC,
+                                                 const R* __restrict__ sH, const R* y, R& u_out, R& G_out) {
+  R px[NMAX], px2[NMAX];
+  cheb_basis<NMAX, R>(n, y[0], px, px2);
+  R u = R(0), G = R(0), lap = R(0);
+  if (D == 1) {
+#pragma unroll
+    for (int p = 0; p < NMAX; ++p) {
+      u += sC[p] * px[p];
+      G += sH[p] * px[p];
+      lap += sC[p] * px2[p];
+    }
+  } else {
+    R py[NMAX], py2[NMAX];
+    cheb_basis<NMAX, R>(n, y[1], py, py2);
+    for (int p1 = 0; p1 < n; ++p1) {
+      const R* c = sC + p1 * NMAX;
+      const R* hh = sH + p1 * NMAX;
+      R cu = R(0), cl = R(0), ch = R(0);
+#pragma unroll
+      for (int p2 = 0; p2 < NMAX; ++p2) {
+        cu += c[p2] * py[p2];
+        cl += c[p2] * py2[p2];
+        ch += hh[p2] * py[p2];
+      }
+      u += px[p1] * cu;
+      G += px[p1] * ch;
+      lap += px2[p1] * cu + px[p1] * cl;
+    }
+  }
+  u_out = u;
+  G_out = G + kappa * lap;
+}
+
 template <int D, int NMAX, typename R>
 __device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int n, const R* __restrict__ sC,
                                          const R* __restrict__ sH, const R* y, R Tt, R dTt) {
@@ -572,43 +632,54 @@ __device__ __forceinline__ R residual_at(const InstanceParams& ip, R kappa, int 
 // (recurrence coefficients, lam_p, the sine series of Ex. 2's solution; layout
 // kFrac* in spmc_tables.h).
 constexpr int kFracRaD = 0, kFracRbD = 40, kFracLamD = 80, kFracSinD = 120, kFracAD = 160, kFracAlphaD = 161,
-              kFracGammaD = 162, kFracModesD = 40;
+              kFracGammaD = 162, kFracLnBD = 163, kFracRpD = 164, kFracRqD = 244, kFracSeriesD = 80,
+              kFracModesD = 40;
 
-// Regularised incomplete beta I_x(p, q) = x^p (1-x)^q / (p B(p,q)) F(p+q, 1; p+1; x)
-// (x <= 1/2; 1 - I_{1-x}(q, p) above); lnB = ln B(p, q).
-__device__ __forceinline__ double ibeta_d(double x, double p, double q, double lnB) {
-  bool flip = x > 0.5;
-  if (flip) { x = 1.0 - x; const double t = p; p = q; q = t; }
-  if (!(x > 0.0)) return flip ? 1.0 : 0.0;
-  const double pre = exp(p * log(x) + q * log1p(-x) - lnB) / p;
-  double term = 1.0, sum = 1.0;
-  for (int k = 0; k < 400; ++k) {
-    term *= (p + q + k) / (p + 1.0 + k) * x;
+// I_u(a, 1-a) of the jump law, regularised incomplete beta by its series
+// I_x(p,q) = x^p (1-x)^q / (p B(p,q)) sum_k prod_{i<k} x (p+q+i)/(p+1+i)
+// (x <= 1/2; 1 - I_{1-x}(q, p) above), the ratios (p+q+i)/(p+1+i) and ln B from
+// the plan's table (p + q = 1).  R = double for the FP64 sweep, float for the
+// FP32 one.
+template <typename R>
+__device__ __forceinline__ R ibeta_jump(R x, const double* __restrict__ tab) {
+  const R a = (R)tab[kFracAD];
+  const bool flip = x > R(0.5);
+  const R p = flip ? R(1) - a : a, q = flip ? a : R(1) - a;
+  const double* r = tab + (flip ? kFracRqD : kFracRpD);
+  if (flip) x = R(1) - x;
+  if (!(x > R(0))) return flip ? R(1) : R(0);
+  const R pre = exp(p * log(x) + q * log1p(-x) - (R)tab[kFracLnBD]) / p;
+  const R eps = sizeof(R) == 8 ? R(1e-18) : R(1e-9);
+  R term = R(1), sum = R(1);
+  for (int k = 0; k < kFracSeriesD; ++k) {
+    term *= (R)r[k] * x;
     sum += term;
-    if (term < 1e-18 * sum) break;
+    if (term < eps * sum) break;
   }
-  const double v = pre * sum;
-  return flip ? 1.0 - v : v;
+  const R v = pre * sum;
+  return flip ? R(1) - v : v;
 }
 
 // Exit distance from a ball of radius r of the alpha-stable process started at
 // its centre: r / sqrt(U), U ~ Beta(a, 1-a) (the Blumenthal-Getoor-Ray law),
 // U = I^{-1}_{1-omega}(a, 1-a) by Newton's method kept inside a bisection bracket.
-__device__ __forceinline__ double stable_jump_d(double r, double a, double omega) {
-  const double p = a, q = 1.0 - a, target = 1.0 - omega;
-  const double lnB = lgamma(p) + lgamma(q) - lgamma(p + q);
-  double lo = 0.0, hi = 1.0;
+template <typename R>
+__device__ __forceinline__ R stable_jump(R r, const double* __restrict__ tab, double omega) {
+  const R p = (R)tab[kFracAD], q = R(1) - p, lnB = (R)tab[kFracLnBD];
+  const R target = (R)(1.0 - omega);
+  const R tol = sizeof(R) == 8 ? R(1e-16) : R(1e-7);
+  R lo = R(0), hi = R(1);
   // start from the leading term at the nearer end
-  double x = exp((log(target) + log(p) + lnB) / p);
-  if (!(x < 0.5)) x = 1.0 - exp((log1p(-target) + log(q) + lnB) / q);
-  if (!(x > 0.0 && x < 1.0)) x = 0.5;
+  R x = exp((log(target) + log(p) + lnB) / p);
+  if (!(x < R(0.5))) x = R(1) - exp((log1p(-target) + log(q) + lnB) / q);
+  if (!(x > R(0) && x < R(1))) x = R(0.5);
   for (int it = 0; it < 100; ++it) {
-    const double F = ibeta_d(x, p, q, lnB) - target;
-    if (F < 0.0) lo = x; else hi = x;
-    const double dF = exp((p - 1.0) * log(x) + (q - 1.0) * log1p(-x) - lnB);
-    double xn = x - F / dF;
-    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    const bool done = fabs(xn - x) <= 1e-16 * xn || hi - lo <= 1e-17;
+    const R F = ibeta_jump<R>(x, tab) - target;
+    if (F < R(0)) lo = x; else hi = x;
+    const R dF = exp((p - R(1)) * log(x) + (q - R(1)) * log1p(-x) - lnB);
+    R xn = x - F / dF;
+    if (!(xn > lo && xn < hi)) xn = R(0.5) * (lo + hi);
+    const bool done = fabs(xn - x) <= tol * xn || hi - lo <= tol * R(0.1);
     x = xn;
     if (done) break;
   }

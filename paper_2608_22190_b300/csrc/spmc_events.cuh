@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
                                                           const void* __restrict__ events_v,
                                                           unsigned long long* __restrict__ acc, int n, int S,
                                                           long long sl_stride, int half, double kappa_d, int direct,
-                                                          const unsigned long long* __restrict__ n_events_p,
+                                                          int cheb, const unsigned long long* __restrict__ n_events_p,
                                                           int* status, const int* __restrict__ abort) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (*abort) return;
@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(256) eval_events_kernel(const long long* __res
       Y[0] = e.y[0];
       if (D == 2) Y[1] = e.y[1];
       R u, G;
-      slice_parts<D, NMAX, R>(kappa, n, sC, sC + half, Y, u, G);
+      if (cheb) slice_parts_cheb<D, NMAX, R>(kappa, n, sC, sC + half, Y, u, G);
+      else slice_parts<D, NMAX, R>(kappa, n, sC, sC + half, Y, u, G);
       R term;
       if (si.kind == 0) {
         // w (f + f_add [+ lifting terms]) [+ w (-d_t u* + kappa Delta u*) for the residual iteration]
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(256) fixed_walk_kernel(SweepArgs a, long long 
         bool inside = true;
         if (a.walk_mode == 2) {
           const Philox4 b = ws.block((uint32_t)q >> 1);
-          const double Jq = stable_jump_d(r_stable, a.frac[kFracAD], U01<double>::one(b.v[(2 * q + 1) & 3]));
+          const double Jq = (double)stable_jump<R>((R)r_stable, a.frac, U01<double>::one(b.v[(2 * q + 1) & 3]));
           const double xn = (double)X[0] + ((b.v[(2 * q) & 3] >> 31) ? -Jq : Jq);
           inside = xn > -1.0 && xn < 1.0;
           Xn[0] = (R)xn;

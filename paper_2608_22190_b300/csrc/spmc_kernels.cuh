@@ -100,6 +100,117 @@ __global__ void reconstruct_kernel(const InstInterval* __restrict__ ii, const do
   }
 }
 
+// The Chebyshev basis (the remark on quasi-linear reconstruction after
+// Algorithm 1): coefficients from the discrete Chebyshev transform (DCT-I) of
+// the values at Chebyshev-Gauss-Lobatto points, per axis.  dct1 returns
+// F_k = f_0 + (-1)^k f_N + 2 sum_{0<j<N} f_j cos(pi j k / N), k = 0..N, through
+// the FFT of the even extension (length 2N) when N is a power of two, by the
+// direct sum otherwise (N <= 40).
+__device__ __forceinline__ void dct1(const double* f, double* F, int N) {
+  if ((N & (N - 1)) == 0 && N <= 32) {
+    const int L = 2 * N;
+    double re[64], im[64];
+    for (int j = 0; j <= N; ++j) re[j] = f[j];
+    for (int j = N + 1; j < L; ++j) re[j] = f[L - j];
+    for (int j = 0; j < L; ++j) im[j] = 0.0;
+    // bit-reversal permutation
+    for (int i = 1, j = 0; i < L; ++i) {
+      int bit = L >> 1;
+      for (; j & bit; bit >>= 1) j ^= bit;
+      j ^= bit;
+      if (i < j) { double t = re[i]; re[i] = re[j]; re[j] = t; t = im[i]; im[i] = im[j]; im[j] = t; }
+    }
+    // radix-2 butterflies, twiddles e^{-2 pi i k / len}
+    for (int len = 2; len <= L; len <<= 1) {
+      const int hl = len >> 1;
+      for (int k = 0; k < hl; ++k) {
+        double sn, cs;
+        sincospi(-2.0 * k / len, &sn, &cs);
+        for (int i = 0; i < L; i += len) {
+          const double vr = re[i + k + hl] * cs - im[i + k + hl] * sn;
+          const double vi = re[i + k + hl] * sn + im[i + k + hl] * cs;
+          re[i + k + hl] = re[i + k] - vr; im[i + k + hl] = im[i + k] - vi;
+          re[i + k] += vr; im[i + k] += vi;
+        }
+      }
+    }
+    for (int k = 0; k <= N; ++k) F[k] = re[k];
+    return;
+  }
+  for (int k = 0; k <= N; ++k) {
+    double acc = f[0] + ((k & 1) ? -f[N] : f[N]);
+    for (int j = 1; j < N; ++j) acc += 2.0 * f[j] * cospi((double)(j * k) / N);
+    F[k] = acc;
+  }
+}
+
+// Reconstruction in the Chebyshev basis, one block per active instance: the
+// time axis (CGL points -cos(pi k / M)) gives T_q coefficients
+// e_q = (-1)^q F_q / (M c_q) (c_0 = c_M = 2, else 1); each space axis the DCT of
+// (0, u_1..u_n, 0) at the n+2 CGL points, a_k = (-1)^k F_k / ((n+1) c_k), turned
+// into coefficients of phi_p = T_p - T_{p+2} by c_p = a_p + c_{p-2}.  The time
+// derivative by ct_q = (2/h)(2/c_q) sum_{l>q, l+q odd} l cu_l.
+template <int D>
+__global__ void cheb_reconstruct_kernel(const InstInterval* __restrict__ ii, const double* __restrict__ U,
+                                        double* __restrict__ coef, int n, const int* __restrict__ abort) {
+  extern __shared__ double sm[];
+  if (abort && *abort) return;
+  const InstInterval w = ii[blockIdx.x];
+  int S = 1;
+  for (int e = 0; e < D; ++e) S *= n;
+  const int T = w.Mt + 1, M = w.Mt;
+  const int tot = T * S;
+  double* a = sm;
+  double* b = sm + tot;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) a[i] = U[w.u_off + i];
+  __syncthreads();
+  double f[41], F[41];
+  // time axis: one line per spatial node
+  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    for (int k = 0; k < T; ++k) f[k] = a[k * S + j];
+    dct1(f, F, M);
+    for (int q = 0; q < T; ++q) b[q * S + j] = ((q & 1) ? -F[q] : F[q]) / (M * ((q == 0 || q == M) ? 2.0 : 1.0));
+  }
+  __syncthreads();
+  double* src = b;
+  double* dst = a;
+  int stride = 1;
+  const int N = n + 1;
+  for (int e = 0; e < D; ++e) {
+    // one line per (q, the other indices)
+    const int lines = tot / n;
+    for (int li = threadIdx.x; li < lines; li += blockDim.x) {
+      const int q = li / (S / n), rest = li - q * (S / n);
+      const int lo = rest % stride, hi = rest / stride;
+      const int base = q * S + hi * stride * n + lo;
+      f[0] = 0.0;
+      f[N] = 0.0;
+      for (int j = 0; j < n; ++j) f[j + 1] = src[base + j * stride];
+      dct1(f, F, N);
+      double cm2 = 0.0, cm1 = 0.0;
+      for (int p = 0; p < n; ++p) {
+        const double ak = ((p & 1) ? -F[p] : F[p]) / (N * (p == 0 ? 2.0 : 1.0));
+        const double cp = ak + cm2;
+        dst[base + p * stride] = cp;
+        cm2 = cm1;
+        cm1 = cp;
+      }
+    }
+    __syncthreads();
+    double* t = src; src = dst; dst = t;
+    stride *= n;
+  }
+  double* cu = coef + w.c_off;
+  double* ct = cu + tot;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int q = i / S, p = i - q * S;
+    cu[i] = src[i];
+    double acc = 0.0;
+    for (int l = q + 1; l < T; l += 2) acc += l * src[l * S + p];
+    ct[i] = (2.0 / w.h) * (q == 0 ? 1.0 : 2.0) * acc;
+  }
+}
+
 // ----------------------------------------------------------------- slices
 // For every node's walk grid tau_m = t_node - (m + t_off) delta / n_sub (t_off =
 // 1/2: the sub-step midpoints of the inside-ball walk; 0 with n_sub = 1: the step
@@ -113,7 +224,7 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
                              const InstInterval* __restrict__ inst_of_node, const double* __restrict__ coef,
                              const InstanceParams* __restrict__ ip, R* __restrict__ slices,
                              SliceInfo* __restrict__ sinfo, int n, int n_sub, int row, long long sl_stride,
-                             double t_off, const int* __restrict__ abort) {
+                             double t_off, const int* __restrict__ abort, int cheb = 0) {
   __shared__ double L[41];
   if (abort && *abort) return;
   long long s = blockIdx.x;
@@ -134,7 +245,9 @@ __global__ void slice_kernel(const TimeNode* __restrict__ tn, const long long* _
     double xi = (2.0 * tau - node.t0 - (node.t0 + node.h)) / node.h;
     L[0] = 1.0;
     if (node.Mt >= 1) L[1] = xi;
-    for (int k = 1; k < node.Mt; ++k) L[k + 1] = ((2.0 * k + 1.0) * xi * L[k] - k * L[k - 1]) / (k + 1.0);
+    // Legendre L_q, or Chebyshev T_q for the Chebyshev basis
+    for (int k = 1; k < node.Mt; ++k)
+      L[k + 1] = cheb ? 2.0 * xi * L[k] - L[k - 1] : ((2.0 * k + 1.0) * xi * L[k] - k * L[k - 1]) / (k + 1.0);
     const InstanceParams P = ip[node.inst];
     SliceInfo si;
     si.tau = tau;
@@ -236,7 +349,7 @@ __device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, c
     const Philox4 b = ws.block((uint32_t)q >> 1);
     const uint32_t wd = b.v[(2 * q) & 3], wo = b.v[(2 * q + 1) & 3];
     const double omega = U01<double>::one(wo);
-    const double Jq = stable_jump_d(r_stable, frac[kFracAD], omega);
+    const double Jq = (double)stable_jump<R>((R)r_stable, frac, omega);
     const double step = (wd >> 31) ? -Jq : Jq;
     const double xn = (double)st.X[0][s] + step;
     if (!(xn > -1.0 && xn < 1.0)) { st.mnext[s] = -1; return; }

@@ -22,7 +22,9 @@
 static_assert(spmc::kFracRa == spmc::kFracRaD && spmc::kFracRb == spmc::kFracRbD &&
                   spmc::kFracLam == spmc::kFracLamD && spmc::kFracSin == spmc::kFracSinD &&
                   spmc::kFracA == spmc::kFracAD && spmc::kFracAlpha == spmc::kFracAlphaD &&
-                  spmc::kFracGamma == spmc::kFracGammaD && spmc::kFracModes == spmc::kFracModesD,
+                  spmc::kFracGamma == spmc::kFracGammaD && spmc::kFracModes == spmc::kFracModesD &&
+                  spmc::kFracLnB == spmc::kFracLnBD && spmc::kFracRp == spmc::kFracRpD &&
+                  spmc::kFracRq == spmc::kFracRqD && spmc::kFracSeries == spmc::kFracSeriesD,
               "the fractional table's host and device layouts agree");
 
 using namespace spmc;
@@ -355,11 +357,12 @@ bool uses_events(spmc_plan_t plan);
 
 // Non-zero boundary data and the direct estimator run on the event sweep only.
 spmc_status check_event_only(spmc_plan_t plan) {
-  bool need = plan->d.estimator == SPMC_EST_DIRECT;
+  bool need = plan->d.estimator == SPMC_EST_DIRECT || plan->d.basis == SPMC_BASIS_CHEB;
   for (const HostProblem& P : plan->probs) need = need || P.ip.bc_kind != SPMC_BC_ZERO;
   if (need && (plan->d.dim > 2 || !uses_events(plan)))
     return fail(plan, SPMC_ERR_UNSUPPORTED,
-                "boundary data and the direct estimator need the event sweep (d <= 2, inside-ball walk)");
+                "boundary data, the direct estimator and the Chebyshev basis need the event sweep (d <= 2, "
+                "inside-ball walk)");
   return SPMC_OK;
 }
 
@@ -544,9 +547,9 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
     }
     if (rd.n_slices > 0) {
       if (plan->d.precision == SPMC_FP64)
-        slice_kernel<5, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
+        slice_kernel<5, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab, plan->d.basis);
       else
-        slice_kernel<5, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
+        slice_kernel<5, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab, plan->d.basis);
       SPMC_CUDA(cudaGetLastError());
     }
     return SPMC_OK;
@@ -554,7 +557,16 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
   int maxT = 0;
   for (auto& w : rd.ii) maxT = std::max(maxT, w.Mt + 1);
   size_t smem = sizeof(double) * 2 * (size_t)maxT * S;
-  if (D == 1) {
+  if (plan->d.basis == SPMC_BASIS_CHEB) {
+    // the discrete Chebyshev transforms (FFT of the even extension for power-of-two lengths)
+    if (D == 1) {
+      SPMC_CUDA(cudaFuncSetAttribute(cheb_reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      cheb_reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 128, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_coef, n, ab);
+    } else {
+      SPMC_CUDA(cudaFuncSetAttribute(cheb_reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      cheb_reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 128, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_coef, n, ab);
+    }
+  } else if (D == 1) {
     SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_A, plan->d_B,
                                                                           plan->d_coef, n, ab);
@@ -567,11 +579,11 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
   const bool fp64 = plan->d.precision == SPMC_FP64;
   if (rd.n_slices > 0) {
     if (D == 1) {
-      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
-      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
+      if (fp64) slice_kernel<1, double><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab, plan->d.basis);
+      else slice_kernel<1, float><<<(unsigned)rd.n_slices, 128, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab, plan->d.basis);
     } else {
-      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
-      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab);
+      if (fp64) slice_kernel<2, double><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (double*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab, plan->d.basis);
+      else slice_kernel<2, float><<<(unsigned)rd.n_slices, 256, 0, stream>>>(rd.d_tn, rd.d_slice_node, rd.d_ii_of_node, plan->d_coef, plan->d_ip, (float*)plan->d_slices, plan->d_sinfo, n, plan->d.n_sub, plan->row, plan->sl_stride, t_off, ab, plan->d.basis);
     }
     SPMC_CUDA(cudaGetLastError());
   }
@@ -646,7 +658,7 @@ void launch_eval(spmc_plan_t plan, cudaStream_t stream, const Round& rd) {
   eval_events_kernel<D, NMAX, R><<<(unsigned)rd.n_slices, 256, esmem, stream>>>(
       rd.d_slice_node, rd.d_tn, plan->d_ip, plan->d_slices, plan->d_sinfo, plan->d_starts, plan->d_events,
       plan->d_acc, plan->d.n_space, plan->S, plan->sl_stride, plan->half, plan->d.kappa, plan->d.estimator,
-      plan->d_total, plan->d_status, plan->d_abort);
+      plan->d.basis, plan->d_total, plan->d_status, plan->d_abort);
 }
 
 // Tensor-core evaluation (d = 2, FP32 sweep).  The dynamic shared memory is
@@ -838,7 +850,8 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
     SPMC_CUDA(cudaGetLastError());
     if (timer_end(plan, stream, tf, 3) != SPMC_OK) return SPMC_ERR_CUDA;
     if (timer_begin(plan, stream, te) != SPMC_OK) return SPMC_ERR_CUDA;
-    const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS;
+    const bool tensor = D == 2 && sizeof(R) == 4 && plan->sweep_mode == SPMC_SWEEP_EVENTS &&
+                        plan->d.basis != SPMC_BASIS_CHEB;
     if (adjoint) {
       if constexpr (D <= 2) {
         spmc_status as = D == 1 ? launch_adj_eval<1, 32, R>(plan, stream, rd)
@@ -1301,7 +1314,9 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   if (d.dim < 1 || d.dim > 5 || d.n_space < 2 || d.n_space > 32 || d.max_intervals < 1 || d.max_degree < 1 ||
       d.max_degree > 39 || d.M < 1 || d.K < 1 || d.n_ref < 1 || d.n_sub < 1 || d.n_sub > 16 ||
       (d.n_sub & (d.n_sub - 1)) || !(d.shell >= 0.0) || d.shell >= 0.5 || d.max_steps < 1 || !(d.kappa > 0.0) || d.batch < 1 ||
-      (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT) ||
+      (d.time_family != SPMC_TIME_LGL && d.time_family != SPMC_TIME_RADAU_LEFT && d.time_family != SPMC_TIME_CHEB) ||
+      (d.basis != SPMC_BASIS_JACOBI && d.basis != SPMC_BASIS_CHEB) ||
+      ((d.basis == SPMC_BASIS_CHEB) != (d.time_family == SPMC_TIME_CHEB)) ||
       (d.precision != SPMC_FP64 && d.precision != SPMC_MIXED) || d.M > 0x7fffffffLL ||
       (d.walk_mode < 0 || d.walk_mode > 2) || (d.estimator != SPMC_EST_RESIDUAL && d.estimator != SPMC_EST_DIRECT) ||
       (d.walk_mode == 2) != (d.alpha > 0.0 && d.alpha < 2.0))
@@ -1316,6 +1331,7 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   if (d.tol > 0.0 && d.batch > 1) return SPMC_ERR_UNSUPPORTED;
   if (d.walk_mode == 1 && d.dim > 2) return SPMC_ERR_UNSUPPORTED;
   if (d.walk_mode == 2 && d.dim != 1) return SPMC_ERR_UNSUPPORTED;   // the fractional case: d = 1
+  if (d.basis == SPMC_BASIS_CHEB && (d.dim > 2 || d.walk_mode != 0)) return SPMC_ERR_UNSUPPORTED;
   if (d.estimator == SPMC_EST_DIRECT && (d.dim > 2 || d.walk_mode != 0)) return SPMC_ERR_UNSUPPORTED;
   spmc_plan_t plan = new spmc_plan_s();
   plan->d = d;
@@ -1336,11 +1352,13 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   const bool frac = d.walk_mode == 2;
   plan->xnodes.resize(n);
   if (frac) space_nodes_frac(n, d.alpha, plan->xnodes.data());
+  else if (d.basis == SPMC_BASIS_CHEB) space_nodes_cheb(n, plan->xnodes.data());
   else space_nodes(n, plan->xnodes.data());
   // shell == 0: half the distance of the outermost node to the boundary, at most 2e-3
   plan->shell = d.shell > 0.0 ? d.shell : std::min(2e-3, 0.5 * (1.0 - std::fabs(plan->xnodes[0])));
   std::vector<double> A(n * n);
   if (frac) space_analysis_frac(n, d.alpha, A.data());
+  else if (d.basis == SPMC_BASIS_CHEB) space_analysis_cheb(n, A.data());
   else space_analysis(n, A.data());
   spmc_status st;
   if ((st = upload(plan, &plan->d_x, plan->xnodes)) != SPMC_OK) { spmc_destroy(plan); return st; }
@@ -1409,8 +1427,8 @@ spmc_status spmc_set_problem(spmc_plan_t plan, int instance, const spmc_problem*
   if (d.walk_mode == 2 && !(frac_kind || p.ex_kind == SPMC_EX_NONE))
     return fail(plan, SPMC_ERR_INVALID, "the fractional case takes ex_kind 0, 6 or 7");
   if (d.walk_mode != 2 && frac_kind) return fail(plan, SPMC_ERR_INVALID, "ex_kind 6 and 7 need the fractional case");
-  if (d.walk_mode == 2 && p.u0_kind != SPMC_U0_NODAL)
-    return fail(plan, SPMC_ERR_UNSUPPORTED, "the fractional case takes nodal initial values");
+  if ((d.walk_mode == 2 || d.basis != SPMC_BASIS_JACOBI) && p.u0_kind != SPMC_U0_NODAL)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "the fractional case and the Chebyshev basis take nodal initial values");
   HostProblem& H = plan->probs[instance];
   bool same_layout = H.set && H.n_int == p.n_intervals &&
                      std::equal(H.deg.begin(), H.deg.end(), p.degrees) &&
@@ -1585,8 +1603,9 @@ spmc_status spmc_iterate_static(spmc_plan_t plan, void* cuda_stream, int interva
     return fail(plan, SPMC_ERR_INVALID, "spmc_iterate_static needs a built plan: call spmc_begin_interval first");
   if (plan->d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_iterate_static: dimensions 1 and 2 only");
   for (const HostProblem& P : plan->probs)
-    if (P.ip.bc_kind != SPMC_BC_ZERO || plan->d.estimator != SPMC_EST_RESIDUAL)
-      return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_iterate_static: zero boundary data and the residual iteration only");
+    if (P.ip.bc_kind != SPMC_BC_ZERO || plan->d.estimator != SPMC_EST_RESIDUAL || plan->d.basis != SPMC_BASIS_JACOBI)
+      return fail(plan, SPMC_ERR_UNSUPPORTED,
+                  "spmc_iterate_static: zero boundary data, the residual iteration and the Jacobi basis only");
   if (interval < 0 || interval >= (int)plan->rounds.size()) return fail(plan, SPMC_ERR_INVALID, "bad interval");
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   Round& rd = plan->rounds[interval];
@@ -1721,7 +1740,8 @@ spmc_status spmc_grad(spmc_plan_t plan, void* cuda_stream, const double* dloss_d
   const int R = (int)plan->rounds.size();
   if (d.tol > 0.0) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad needs a fixed iteration count (tol <= 0)");
   if (d.dim > 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: dimensions 1 and 2 only");
-  if (d.walk_mode == 2) return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: not for the fractional case");
+  if (d.walk_mode == 2 || d.basis != SPMC_BASIS_JACOBI)
+    return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: not for the fractional case or the Chebyshev basis");
   for (const HostProblem& P : plan->probs)
     if (P.ip.bc_kind != SPMC_BC_ZERO || d.estimator != SPMC_EST_RESIDUAL)
       return fail(plan, SPMC_ERR_UNSUPPORTED, "spmc_grad: zero boundary data and the residual iteration only");

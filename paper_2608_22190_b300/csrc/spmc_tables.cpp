@@ -76,6 +76,11 @@ void space_nodes(int n, double* x) { jacobi_zeros(n, 1.0, 1.0, x); }
 
 void time_nodes(int family, int M, double* xi) {
   xi[0] = -1.0;
+  if (family == 2) {   // Chebyshev-Gauss-Lobatto -cos(pi k / M)
+    for (int k = 1; k < M; ++k) xi[k] = -std::cos(kPi * k / M);
+    xi[M] = 1.0;
+    return;
+  }
   if (family == 0) {
     xi[M] = 1.0;
     if (M >= 2) jacobi_zeros(M - 1, 1.0, 1.0, xi + 1);
@@ -115,6 +120,17 @@ void space_analysis(int n, double* A) {
 // b_qk (row-major [q][k]) of Eq. timeLag on the reference interval; gamma_q =
 // 2/(2q+1) for q < M and the discrete norm sum_k L_M(xi_k)^2 w_k for q = M.
 void time_analysis(int family, int M, double* B) {
+  if (family == 2) {
+    // the DCT-I at the CGL points: B[q][k] = 2 T_q(xi_k) / (M c_q c_k), c = 2 at the ends
+    std::vector<double> xi(M + 1);
+    time_nodes(2, M, xi.data());
+    for (int q = 0; q <= M; ++q)
+      for (int k = 0; k <= M; ++k) {
+        const double cq = (q == 0 || q == M) ? 2.0 : 1.0, ck = (k == 0 || k == M) ? 2.0 : 1.0;
+        B[q * (M + 1) + k] = 2.0 * std::cos(q * std::acos(xi[k])) / (M * cq * ck);
+      }
+    return;
+  }
   std::vector<double> xi(M + 1), w(M + 1), L(M + 1), Lk((M + 1) * (M + 1));
   time_nodes(family, M, xi.data());
   time_weights(family, M, xi.data(), w.data());
@@ -186,6 +202,33 @@ void frac_table(double alpha, double* T) {
   T[kFracA] = a;
   T[kFracAlpha] = alpha;
   T[kFracGamma] = std::exp(std::lgamma(1.0 + alpha));
+  // the jump law U ~ Beta(a, 1-a): ln B(a, 1-a) and the term ratios of the series
+  // I_x(p,q) = x^p (1-x)^q / (p B) sum_k prod_{i<k} x (p+q+i)/(p+1+i) for (p,q) = (a, 1-a), (1-a, a)
+  T[kFracLnB] = std::lgamma(a) + std::lgamma(1.0 - a);
+  for (int k = 0; k < kFracSeries; ++k) {
+    T[kFracRp + k] = (1.0 + k) / (a + 1.0 + k);
+    T[kFracRq + k] = (1.0 + k) / (2.0 - a + k);
+  }
+}
+
+// The Chebyshev basis: interior CGL points -cos(pi j / (n+1)), j = 1..n; the
+// analysis matrix maps nodal values to coefficients of phi_p = T_p - T_{p+2}:
+// a_k = 2 / ((n+1) c_k) sum_j u_j T_k(x_j) (c_0 = 2), c_p = a_p + c_{p-2}.
+void space_nodes_cheb(int n, double* x) {
+  for (int j = 0; j < n; ++j) x[j] = -std::cos(kPi * (j + 1) / (n + 1));
+}
+void space_analysis_cheb(int n, double* A) {
+  std::vector<double> x(n);
+  space_nodes_cheb(n, x.data());
+  const int N = n + 1;
+  for (int j = 0; j < n; ++j) {
+    const double th = std::acos(x[j]);
+    for (int p = 0; p < n; ++p) {
+      double acc = 0.0;
+      for (int k = p; k >= 0; k -= 2) acc += 2.0 * std::cos(k * th) / (N * (k == 0 ? 2.0 : 1.0));
+      A[p * n + j] = acc;
+    }
+  }
 }
 
 // phi_p(x) = (1-x^2) P^{(1,1)}_p(x), p < n (u0 from coefficients).

@@ -41,7 +41,7 @@ from typing import List, Optional
 import numpy as np
 
 # enums shared by name with the C-ABI header (values fixed there)
-TIME_LGL, TIME_RADAU_LEFT = 0, 1
+TIME_LGL, TIME_RADAU_LEFT, TIME_CHEB = 0, 1, 2
 F_POLY3, F_SIN = 0, 1
 EX_NONE, EX_SIN, EX_COSHALF, EX_POLY, EX_COSTHIRD, EX_SINPLUS, EX_FRAC_SIN, EX_FRAC_POLY = range(8)
 BC_ZERO, BC_LIFT, BC_RAW = 0, 1, 2
@@ -226,10 +226,18 @@ def frac_exact(alpha: float, ex_kind: int, x: np.ndarray, t) -> np.ndarray:
     return (1 + t) * w * (1 + 0.5 * (a + 1) * x)
 
 
+def chebyshev(wl: Workload) -> Workload:
+    """The same workload in the Chebyshev basis (Chebyshev-Gauss-Lobatto points
+    in space and time)."""
+    return replace(wl, time_family=TIME_CHEB, name=wl.name + "-chebyshev")
+
+
 def time_nodes_reference(family: int, Mt: int) -> np.ndarray:
-    """Reference-interval time nodes (LGL or left Radau) from scipy's Jacobi zeros,
+    """Reference-interval time nodes (LGL, left Radau or Chebyshev-Gauss-Lobatto),
     for evaluating closed-form solutions at the nodes."""
     import scipy.special as sps
+    if family == TIME_CHEB:
+        return -np.cos(np.pi * np.arange(Mt + 1) / Mt)
     if family == TIME_LGL:
         inner = sps.roots_jacobi(Mt - 1, 1.0, 1.0)[0] if Mt >= 2 else np.zeros(0)
         return np.concatenate([[-1.0], inner, [1.0]])

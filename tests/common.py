@@ -11,7 +11,8 @@ def oracle_spec(O, wl, inst, **over):
     kw = dict(dim=wl.dim, n_space=wl.n_space, time_family=wl.time_family, n_ref=wl.n_ref, M=wl.M,
               kappa=wl.kappa, seed=wl.seed, f_kind=inst.f_kind, f_coef=tuple(inst.f_coef), f_scale=inst.f_scale,
               ex_kind=inst.ex_kind, ex_beta=inst.ex_beta, n_sub=wl.n_sub, shell=wl.shell,
-              max_steps=wl.max_steps, n_threads=os.cpu_count() or 1, bc_kind=getattr(inst, "bc_kind", 0))
+              max_steps=wl.max_steps, n_threads=os.cpu_count() or 1, bc_kind=getattr(inst, "bc_kind", 0),
+              basis=1 if wl.time_family == 2 else 0)
     kw.update(over)
     return O.Spec(**kw)
 
