@@ -352,6 +352,7 @@ def run_ours(args):
         line["w5_adjoint"] = w5_leg(args)
         line["boundary"] = boundary_leg(args)
         line["fractional"] = fractional_leg(args)
+        line["chebyshev"] = chebyshev_leg(args)
         line["cpu_baseline"] = cpu_baseline(wl)
     plan.close()
     if rank == 0:
@@ -425,7 +426,7 @@ def fp64_leg(args):
                        "step": "one FP64 iteration of interval 1", "l2": "flushed before the timed region"}}
 
 
-def hp_time_to_tol(wl, prec, tol, kmax, accel="none", estimator=0):
+def hp_time_to_tol(wl, prec, tol, kmax, accel="none", estimator=0, sweep=None):
     """Time until every node of every interval is within tol of the closed form:
     the hp solve interval by interval (hand-off, then iterations until the
     interval's L-inf error <= tol, at most kmax).  GPU time of the hand-offs and
@@ -439,6 +440,8 @@ def hp_time_to_tol(wl, prec, tol, kmax, accel="none", estimator=0):
     inst = wl.instances[0]
     plan = Plan.from_workload(wl, precision=prec, estimator=estimator)
     plan.set_acceleration(accel)
+    if sweep:
+        plan.set_sweep(sweep)
     grid = plan.node_grid()
     ms_total, iters, errs = 0.0, [], []
 
@@ -679,6 +682,19 @@ def boundary_leg(args, tol=1e-6):
     out["w7_hp_direct_raw"] = solve_err(W.w7(bc_kind=W.BC_RAW), 1)
     out["w7_classical_residual_lifted"] = solve_err(W.w7(bc_kind=W.BC_LIFT, n_intervals=1, degree=16, K=16), 0)
     out["w7_classical_direct_raw"] = solve_err(W.w7(bc_kind=W.BC_RAW, n_intervals=1, degree=16, K=16), 1)
+    return out
+
+
+def chebyshev_leg(args, tol=1e-6):
+    """The Chebyshev basis (CGL points, DCT-I reconstruction) against the Jacobi
+    basis on the 2-D long-time workload, all 20 intervals, mixed, M = 2048,
+    both with the FP32 evaluation kernel (the tensor-core one is Jacobi-only):
+    GPU time and iterations to L-inf 1e-6 against the closed form."""
+    from paper_2608_22190_b300 import _lib as L
+    from paper_2608_22190_b300 import workloads as W
+    out = {}
+    out["w2_chebyshev_M2048"] = hp_time_to_tol(W.chebyshev(W.w2(M=2048)), L.MIXED, tol, 16)
+    out["w2_jacobi_alu_M2048"] = hp_time_to_tol(W.w2(M=2048), L.MIXED, tol, 16, sweep="events_alu")
     return out
 
 
