@@ -37,9 +37,11 @@ def parse():
     ap.add_argument("--intervals", type=int, default=20, help="intervals of the workload (20 = full)")
     ap.add_argument("--M", type=int, default=65536)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU legs")
-    ap.add_argument("--case", default=None, choices=["iterate1", "iterate1_5d"],
+    ap.add_argument("--case", default=None, choices=["iterate1", "iterate1_5d", "iterate1_frac", "iterate1_cheb"],
                     help="profiling case: build the plan and run one iteration of the first interval, untimed "
-                         "(iterate1_5d: the 5-D workload at --M samples)")
+                         "(iterate1_5d: the 5-D workload; iterate1_frac: the fractional Allen-Cahn problem, "
+                         "alpha = 0.4, h = 0.5; iterate1_cheb: the 2-D workload in the Chebyshev basis; all at "
+                         "--M samples)")
     return ap.parse_args()
 
 
@@ -806,9 +808,13 @@ def run_case(args):
     from paper_2608_22190_b300 import _lib as L
     from paper_2608_22190_b300.api import Plan
     torch.cuda.set_device(0)
+    from paper_2608_22190_b300 import workloads as W
     if args.case == "iterate1_5d":
-        from paper_2608_22190_b300 import workloads as W
         wl = W.w4(M=args.M, K=1)
+    elif args.case == "iterate1_frac":
+        wl = W.w8(M=args.M, K=1, alpha=0.4, h=0.5, T=0.5)
+    elif args.case == "iterate1_cheb":
+        wl = W.chebyshev(workload(args, 0))
     else:
         wl = workload(args, 0)
     plan = Plan.from_workload(wl, precision=L.MIXED if args.precision == "mixed" else L.FP64)

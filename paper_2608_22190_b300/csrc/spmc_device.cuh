@@ -637,18 +637,18 @@ constexpr int kFracRaD = 0, kFracRbD = 40, kFracLamD = 80, kFracSinD = 120, kFra
 
 // I_u(a, 1-a) of the jump law, regularised incomplete beta by its series
 // I_x(p,q) = x^p (1-x)^q / (p B(p,q)) sum_k prod_{i<k} x (p+q+i)/(p+1+i)
-// (x <= 1/2; 1 - I_{1-x}(q, p) above), the ratios (p+q+i)/(p+1+i) and ln B from
-// the plan's table (p + q = 1).  R = double for the FP64 sweep, float for the
-// FP32 one.
-template <typename R>
-__device__ __forceinline__ R ibeta_jump(R x, const double* __restrict__ tab) {
-  const R a = (R)tab[kFracAD];
+// (x <= 1/2; 1 - I_{1-x}(q, p) above); rp, rq hold the ratios (p+q+i)/(p+1+i)
+// for (p, q) = (a, 1-a) and (1-a, a) (the plan's table, or a copy of it in
+// the sweep's precision), lnB = ln B(a, 1-a).  R = double for the FP64 sweep,
+// float for the FP32 one.
+template <typename R, typename T>
+__device__ __forceinline__ R ibeta_jump(R x, R a, R lnB, const T* __restrict__ rp, const T* __restrict__ rq) {
   const bool flip = x > R(0.5);
   const R p = flip ? R(1) - a : a, q = flip ? a : R(1) - a;
-  const double* r = tab + (flip ? kFracRqD : kFracRpD);
+  const T* r = flip ? rq : rp;
   if (flip) x = R(1) - x;
   if (!(x > R(0))) return flip ? R(1) : R(0);
-  const R pre = exp(p * log(x) + q * log1p(-x) - (R)tab[kFracLnBD]) / p;
+  const R pre = exp(p * log(x) + q * log1p(-x) - lnB) / p;
   const R eps = sizeof(R) == 8 ? R(1e-18) : R(1e-9);
   R term = R(1), sum = R(1);
   for (int k = 0; k < kFracSeriesD; ++k) {
@@ -663,9 +663,10 @@ __device__ __forceinline__ R ibeta_jump(R x, const double* __restrict__ tab) {
 // Exit distance from a ball of radius r of the alpha-stable process started at
 // its centre: r / sqrt(U), U ~ Beta(a, 1-a) (the Blumenthal-Getoor-Ray law),
 // U = I^{-1}_{1-omega}(a, 1-a) by Newton's method kept inside a bisection bracket.
-template <typename R>
-__device__ __forceinline__ R stable_jump(R r, const double* __restrict__ tab, double omega) {
-  const R p = (R)tab[kFracAD], q = R(1) - p, lnB = (R)tab[kFracLnBD];
+template <typename R, typename T>
+__device__ __forceinline__ R stable_jump(R r, R a, R lnB, const T* __restrict__ rp, const T* __restrict__ rq,
+                                         double omega) {
+  const R p = a, q = R(1) - a;
   const R target = (R)(1.0 - omega);
   const R tol = sizeof(R) == 8 ? R(1e-16) : R(1e-7);
   R lo = R(0), hi = R(1);
@@ -674,7 +675,7 @@ __device__ __forceinline__ R stable_jump(R r, const double* __restrict__ tab, do
   if (!(x < R(0.5))) x = R(1) - exp((log1p(-target) + log(q) + lnB) / q);
   if (!(x > R(0) && x < R(1))) x = R(0.5);
   for (int it = 0; it < 100; ++it) {
-    const R F = ibeta_jump<R>(x, tab) - target;
+    const R F = ibeta_jump<R, T>(x, a, lnB, rp, rq) - target;
     if (F < R(0)) lo = x; else hi = x;
     const R dF = exp((p - R(1)) * log(x) + (q - R(1)) * log1p(-x) - lnB);
     R xn = x - F / dF;

@@ -577,6 +577,18 @@ __global__ void __launch_bounds__(256) fixed_walk_kernel(SweepArgs a, long long 
   const R* slices = reinterpret_cast<const R*>(a.slices);
   const unsigned int lane = threadIdx.x & 31;
   unsigned long long capped = 0, points = 0;
+  // the alpha-stable jump law's series ratios in the sweep's precision
+  __shared__ R s_rp[kFracSeriesD], s_rq[kFracSeriesD];
+  R s_a = R(0), s_lnB = R(0);
+  if (a.walk_mode == 2) {
+    for (int k = threadIdx.x; k < kFracSeriesD; k += blockDim.x) {
+      s_rp[k] = (R)a.frac[kFracRpD + k];
+      s_rq[k] = (R)a.frac[kFracRqD + k];
+    }
+    s_a = (R)a.frac[kFracAD];
+    s_lnB = (R)a.frac[kFracLnBD];
+  }
+  __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long top = (n_walks + 31) / 32 * 32;   // whole warps: the run sums are warp-wide
   for (long long wid = (long long)blockIdx.x * blockDim.x + threadIdx.x; wid < top; wid += stride) {
@@ -613,7 +625,8 @@ __global__ void __launch_bounds__(256) fixed_walk_kernel(SweepArgs a, long long 
         bool inside = true;
         if (a.walk_mode == 2) {
           const Philox4 b = ws.block((uint32_t)q >> 1);
-          const double Jq = (double)stable_jump<R>((R)r_stable, a.frac, U01<double>::one(b.v[(2 * q + 1) & 3]));
+          const double Jq = (double)stable_jump<R, R>((R)r_stable, s_a, s_lnB, s_rp, s_rq,
+                                                      U01<double>::one(b.v[(2 * q + 1) & 3]));
           const double xn = (double)X[0] + ((b.v[(2 * q) & 3] >> 31) ? -Jq : Jq);
           inside = xn > -1.0 && xn < 1.0;
           Xn[0] = (R)xn;

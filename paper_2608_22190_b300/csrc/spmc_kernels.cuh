@@ -105,10 +105,11 @@ __global__ void reconstruct_kernel(const InstInterval* __restrict__ ii, const do
 // the values at Chebyshev-Gauss-Lobatto points, per axis.  dct1 returns
 // F_k = f_0 + (-1)^k f_N + 2 sum_{0<j<N} f_j cos(pi j k / N), k = 0..N, through
 // the FFT of the even extension (length 2N) when N is a power of two, by the
-// direct sum otherwise (N <= 40).
-__device__ __forceinline__ void dct1(const double* f, double* F, int N) {
+// direct sum otherwise (N <= 40).  cs[m], sn[m] = cos, sin(pi m / N), m < 2N
+// (the twiddles of the FFT and the cosines of the direct sum).
+__device__ __forceinline__ void dct1(const double* f, double* F, int N, const double* cs, const double* sn) {
+  const int L = 2 * N;
   if ((N & (N - 1)) == 0 && N <= 32) {
-    const int L = 2 * N;
     double re[64], im[64];
     for (int j = 0; j <= N; ++j) re[j] = f[j];
     for (int j = N + 1; j < L; ++j) re[j] = f[L - j];
@@ -120,15 +121,14 @@ __device__ __forceinline__ void dct1(const double* f, double* F, int N) {
       j ^= bit;
       if (i < j) { double t = re[i]; re[i] = re[j]; re[j] = t; t = im[i]; im[i] = im[j]; im[j] = t; }
     }
-    // radix-2 butterflies, twiddles e^{-2 pi i k / len}
+    // radix-2 butterflies, twiddles e^{-2 pi i k / len} = cs[m] - i sn[m], m = k L / len
     for (int len = 2; len <= L; len <<= 1) {
-      const int hl = len >> 1;
+      const int hl = len >> 1, step = L / len;
       for (int k = 0; k < hl; ++k) {
-        double sn, cs;
-        sincospi(-2.0 * k / len, &sn, &cs);
+        const double c = cs[k * step], sg = -sn[k * step];
         for (int i = 0; i < L; i += len) {
-          const double vr = re[i + k + hl] * cs - im[i + k + hl] * sn;
-          const double vi = re[i + k + hl] * sn + im[i + k + hl] * cs;
+          const double vr = re[i + k + hl] * c - im[i + k + hl] * sg;
+          const double vi = re[i + k + hl] * sg + im[i + k + hl] * c;
           re[i + k + hl] = re[i + k] - vr; im[i + k + hl] = im[i + k] - vi;
           re[i + k] += vr; im[i + k] += vi;
         }
@@ -139,7 +139,7 @@ __device__ __forceinline__ void dct1(const double* f, double* F, int N) {
   }
   for (int k = 0; k <= N; ++k) {
     double acc = f[0] + ((k & 1) ? -f[N] : f[N]);
-    for (int j = 1; j < N; ++j) acc += 2.0 * f[j] * cospi((double)(j * k) / N);
+    for (int j = 1; j < N; ++j) acc += 2.0 * f[j] * cs[(j * k) % L];
     F[k] = acc;
   }
 }
@@ -162,20 +162,23 @@ __global__ void cheb_reconstruct_kernel(const InstInterval* __restrict__ ii, con
   const int tot = T * S;
   double* a = sm;
   double* b = sm + tot;
+  __shared__ double tcs[80], tsn[80], xcs[80], xsn[80];   // cos, sin(pi m / M) and (pi m / (n+1))
+  const int N = n + 1;
+  for (int m = threadIdx.x; m < 2 * M; m += blockDim.x) sincospi((double)m / M, &tsn[m], &tcs[m]);
+  for (int m = threadIdx.x; m < 2 * N; m += blockDim.x) sincospi((double)m / N, &xsn[m], &xcs[m]);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) a[i] = U[w.u_off + i];
   __syncthreads();
   double f[41], F[41];
   // time axis: one line per spatial node
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
     for (int k = 0; k < T; ++k) f[k] = a[k * S + j];
-    dct1(f, F, M);
+    dct1(f, F, M, tcs, tsn);
     for (int q = 0; q < T; ++q) b[q * S + j] = ((q & 1) ? -F[q] : F[q]) / (M * ((q == 0 || q == M) ? 2.0 : 1.0));
   }
   __syncthreads();
   double* src = b;
   double* dst = a;
   int stride = 1;
-  const int N = n + 1;
   for (int e = 0; e < D; ++e) {
     // one line per (q, the other indices)
     const int lines = tot / n;
@@ -186,7 +189,7 @@ __global__ void cheb_reconstruct_kernel(const InstInterval* __restrict__ ii, con
       f[0] = 0.0;
       f[N] = 0.0;
       for (int j = 0; j < n; ++j) f[j + 1] = src[base + j * stride];
-      dct1(f, F, N);
+      dct1(f, F, N, xcs, xsn);
       double cm2 = 0.0, cm1 = 0.0;
       for (int p = 0; p < n; ++p) {
         const double ak = ((p & 1) ? -F[p] : F[p]) / (N * (p == 0 ? 2.0 : 1.0));
@@ -349,7 +352,8 @@ __device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, c
     const Philox4 b = ws.block((uint32_t)q >> 1);
     const uint32_t wd = b.v[(2 * q) & 3], wo = b.v[(2 * q + 1) & 3];
     const double omega = U01<double>::one(wo);
-    const double Jq = (double)stable_jump<R>((R)r_stable, frac, omega);
+    const double Jq = (double)stable_jump<R, double>((R)r_stable, (R)frac[kFracAD], (R)frac[kFracLnBD],
+                                                     frac + kFracRpD, frac + kFracRqD, omega);
     const double step = (wd >> 31) ? -Jq : Jq;
     const double xn = (double)st.X[0][s] + step;
     if (!(xn > -1.0 && xn < 1.0)) { st.mnext[s] = -1; return; }

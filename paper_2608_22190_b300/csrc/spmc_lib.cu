@@ -561,10 +561,10 @@ spmc_status prepare_slices(spmc_plan_t plan, cudaStream_t stream, const Round& r
     // the discrete Chebyshev transforms (FFT of the even extension for power-of-two lengths)
     if (D == 1) {
       SPMC_CUDA(cudaFuncSetAttribute(cheb_reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      cheb_reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 128, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_coef, n, ab);
+      cheb_reconstruct_kernel<1><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_coef, n, ab);
     } else {
       SPMC_CUDA(cudaFuncSetAttribute(cheb_reconstruct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      cheb_reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 128, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_coef, n, ab);
+      cheb_reconstruct_kernel<2><<<(unsigned)rd.ii.size(), 256, smem, stream>>>(rd.d_ii, plan->d_U, plan->d_coef, n, ab);
     }
   } else if (D == 1) {
     SPMC_CUDA(cudaFuncSetAttribute(reconstruct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -48,7 +48,9 @@ def test_fp64_chebyshev_stepwise(O, api, dim, n, Mt):
     wl = W.chebyshev(base)
     wl.n_ref = 12
     for g, r in _stepwise(O, api, wl, 2):
-        assert np.all(np.abs(g - r) <= parity_tol(r)), np.abs(g - r).max()
+        # with n odd the middle node's exact value is 0: both sides hold rounding
+        # noise of a few ulps of the largest values there
+        assert np.all(np.abs(g - r) <= parity_tol(r) + 8e-15 * np.abs(r).max()), np.abs(g - r).max()
 
 
 def test_mixed_chebyshev_matches_oracle(O, api):
