@@ -35,6 +35,33 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
   return o;
 }
 
+// ------------------------------------------------------------------ division
+// Quotient of a 32-bit unsigned n by a divisor d fixed for a launch, by one
+// high multiply, a subtract, an add and two shifts (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Sec. 4):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// floor(n / d) = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n),
+// exact for every n < 2^32 and 1 <= d < 2^32.
+struct FastDiv {
+  uint32_t d = 1, m = 1, s1 = 0, s2 = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t dd) : d(dd) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)dd) ++l;
+    m = (uint32_t)((((1ull << l) - dd) << 32) / dd + 1);
+    s1 = l < 1 ? (uint32_t)l : 1u;
+    s2 = l > 1 ? (uint32_t)(l - 1) : 0u;
+  }
+  __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(m, n);
+#else
+    const uint32_t t = (uint32_t)(((unsigned long long)m * n) >> 32);
+#endif
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
 // The stream of one walk: key = seed, counter = (block, sample, node, tag).
 struct WalkStream {
   uint32_t k0, k1, sample, node, tag;

@@ -47,6 +47,9 @@ struct EventArgs {
   const TimeNode* tn;
   const InstanceParams* ip;
   const double* xnodes;
+  const void* xy;                // coordinates of every spatial node in R: [j][e], S x D
+  FastDiv div_nb, div_S;         // by the batch's samples and by the nodes per time node
+  int fast32;                    // walk ids and (time node, node) indices below 2^32: the FastDiv decode
   unsigned int* counts;          // COUNT: (slice, node) histogram; FILL: placement cursors
   void* events;                  // Event<R>[cap] grouped by (slice, node) (FILL)
   unsigned long long cap;        // events the buffer holds (FILL)
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
   if (*a.abort) return;
   __shared__ unsigned long long s_next;
   __shared__ EmitQueue<D, R> s_q[FILL ? 8 : 1];   // one queue per warp of the 256-thread block
-  const int S = a.S, n = a.n, G = a.n_sub;
+  const int S = a.S, G = a.n_sub;
   const long long nb = a.nb;
   const R kappa = (R)a.kappa, shell = (R)a.shell;
   Ev* ev = reinterpret_cast<Ev*>(a.events);
@@ -192,18 +195,22 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
           more = false;
         } else {
           const long long wid = (long long)blockIdx.x + (long long)kk * gridDim.x;
-          long long node, il;
-          if (total < (1ll << 32)) {   // 32-bit division (the usual case: about 2^25 walks per batch)
-            const uint32_t w32 = (uint32_t)wid, nb32 = (uint32_t)nb;
-            const uint32_t q32 = w32 / nb32;
-            node = q32; il = w32 - q32 * nb32;
+          long long node, il, ti;
+          int j;
+          if (a.fast32) {   // the usual case: about 2^25 walks per batch
+            const uint32_t w32 = (uint32_t)wid;
+            const uint32_t q32 = a.div_nb.div(w32);
+            il = w32 - q32 * a.div_nb.d;
+            const uint32_t nd = q32 + (uint32_t)a.node_lo;
+            const uint32_t t32 = a.div_S.div(nd);
+            node = nd; ti = t32; j = (int)(nd - t32 * (uint32_t)S);
           } else {
             node = wid / nb;
             il = wid - node * nb;
+            node += a.node_lo;
+            ti = node / S;
+            j = (int)(node - ti * S);
           }
-          node += a.node_lo;
-          const long long ti = node / S;
-          const int j = (int)(node - ti * S);
           if (ti != cached_ti) {   // time-node parameters, as the CPU reference computes them
             const TimeNode node = a.tn[ti];
             const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
@@ -219,9 +226,9 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
                      (uint32_t)(a.iteration & 0x3ff);
             cached_ti = ti;
           }
-          int jr = j;
+          const R* xy = reinterpret_cast<const R*>(a.xy) + (size_t)j * D;
 #pragma unroll
-          for (int e = 0; e < D; ++e) { X[e] = (R)a.xnodes[jr % n]; jr /= n; }
+          for (int e = 0; e < D; ++e) X[e] = xy[e];
           f = R(0); k = 0; q = 0;
           key_j = j;
           ws.node = node_ell * (uint32_t)S + (uint32_t)j;

@@ -99,6 +99,8 @@ struct spmc_plan_s {
   std::vector<double> xnodes;
   // device
   double* d_x = nullptr;
+  double* d_xyd = nullptr;       // coordinates of every spatial node, [j][e] (S x dim), FP64
+  float* d_xyf = nullptr;        // the same rounded to FP32
   double* d_times = nullptr;     // t_{n,l} of one interval (spmc_get_solution)
   double* d_frac = nullptr;      // the fractional case's table (kFrac* layout of spmc_tables.h)
   double* d_A = nullptr;
@@ -793,6 +795,8 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   SPMC_CUDA(cudaMemsetAsync(plan->d_acc, 0, 4 * sizeof(unsigned long long) * n_tn * S, stream));
   EventArgs a;
   a.tn = rd.d_tn; a.ip = plan->d_ip; a.xnodes = plan->d_x; a.counts = plan->d_counts;
+  a.xy = sizeof(R) == 4 ? (const void*)plan->d_xyf : (const void*)plan->d_xyd;
+  a.div_S = FastDiv((uint32_t)S);
   a.direct = d.estimator == SPMC_EST_DIRECT ? 1 : 0;
   a.status = plan->d_status;
   a.abort = plan->d_abort;
@@ -821,6 +825,8 @@ spmc_status event_sweep_t(spmc_plan_t plan, cudaStream_t stream, const Round& rd
   for (long long i0 = 0; i0 < d.M; i0 += nb) {
     a.i0 = i0;
     a.nb = std::min<long long>(nb, d.M - i0);
+    a.div_nb = FastDiv((uint32_t)std::min<long long>(a.nb, 0xffffffffLL));
+    a.fast32 = (node_cnt * a.nb < (1LL << 32) && node_lo + node_cnt < (1LL << 32)) ? 1 : 0;
     std::pair<cudaEvent_t, cudaEvent_t> tw{nullptr, nullptr}, te{nullptr, nullptr};
     if (timer_begin(plan, stream, tw) != SPMC_OK) return SPMC_ERR_CUDA;
     SPMC_CUDA(cudaMemsetAsync(plan->d_counts, 0, sizeof(unsigned int) * nkeys, stream));
@@ -1362,6 +1368,21 @@ spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out) {
   else space_analysis(n, A.data());
   spmc_status st;
   if ((st = upload(plan, &plan->d_x, plan->xnodes)) != SPMC_OK) { spmc_destroy(plan); return st; }
+  {
+    // node j's coordinates: digit e of j in base n (x fastest) picks xnodes
+    std::vector<double> xyd((size_t)plan->S * d.dim);
+    std::vector<float> xyf(xyd.size());
+    for (long long j = 0; j < plan->S; ++j) {
+      long long jr = j;
+      for (int e = 0; e < d.dim; ++e) {
+        xyd[(size_t)j * d.dim + e] = plan->xnodes[jr % n];
+        xyf[(size_t)j * d.dim + e] = (float)plan->xnodes[jr % n];
+        jr /= n;
+      }
+    }
+    if ((st = upload(plan, &plan->d_xyd, xyd)) != SPMC_OK) { spmc_destroy(plan); return st; }
+    if ((st = upload(plan, &plan->d_xyf, xyf)) != SPMC_OK) { spmc_destroy(plan); return st; }
+  }
   if ((st = upload(plan, &plan->d_A, A)) != SPMC_OK) { spmc_destroy(plan); return st; }
   if (frac) {
     std::vector<double> T(kFracTable);
