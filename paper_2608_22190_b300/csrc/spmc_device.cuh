@@ -97,6 +97,7 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
   static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double abs_(double a) { return ::fabs(a); }
   static __device__ __forceinline__ double log_(double a) { return log(a); }
   static __device__ __forceinline__ void sincos2pi(double U, double* s, double* c) { sincospi(2.0 * U, s, c); }
   static __device__ __forceinline__ double sinpi_(double x) { return sinpi(x); }
@@ -111,6 +112,7 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
   static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
   static __device__ __forceinline__ float log_(float a) { return logf(a); }
   static __device__ __forceinline__ void sincos2pi(float U, float* s, float* c) { sincospif(2.0f * U, s, c); }
   static __device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }
@@ -242,7 +244,9 @@ __device__ __forceinline__ bool roulette_keep(uint32_t rw, R p) {
   const R P = p * R(33554432.0);            // exact (a power-of-two scale)
   if (P >= R(33554432.0)) return true;      // p >= 1: every uniform is below it
   if (!(P >= R(0))) return false;           // negative or NaN: never below it
-  const int c = (int)ceil(P);               // exact: an integer in [0, 2^25]
+  int c;                                    // ceil(P), exact: an integer in [0, 2^25]
+  if constexpr (sizeof(R) == 4) c = __float2int_ru(P);
+  else c = __double2int_ru(P);
   return (int)(2u * (rw >> 8) + 1u) < c;
 }
 

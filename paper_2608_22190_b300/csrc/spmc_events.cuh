@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
       int near = 0;
 #pragma unroll
       for (int e = 0; e < D; ++e) {
-        const R de = Ar<R>::sub(R(1), fabs(X[e]));
+        const R de = Ar<R>::sub(R(1), Ar<R>::abs_(X[e]));
         if (de < dist) { dist = de; near = e; }
       }
       if (q >= a.max_steps || dist < shell) {
