@@ -479,7 +479,8 @@ def time_to_tol_legs(args, tol=1e-6):
       w1_mixed / w1_fp64: the 1-D single-interval workload at its full size
         (M = 4096), with the L-inf distance of every iterate from the FP64
         oracle's iterate on the same streams (computed on the host cores
-        meanwhile)."""
+        meanwhile); w1_mixed_aitken / w1_fp64_aitken: the same with Aitken's
+        relaxation of the update."""
     import os
     import numpy as np
     import torch
@@ -510,9 +511,11 @@ def time_to_tol_legs(args, tol=1e-6):
     pool = ThreadPoolExecutor(1)
     fut = pool.submit(oracle_iterates)
     gpu_iterates = {}
-    for name, prec in (("w1_mixed", L.MIXED), ("w1_fp64", L.FP64)):
+    for name, prec, accel in (("w1_mixed", L.MIXED, "none"), ("w1_fp64", L.FP64, "none"),
+                              ("w1_mixed_aitken", L.MIXED, "aitken"), ("w1_fp64_aitken", L.FP64, "aitken")):
         wl = W.w1()
         plan = Plan.from_workload(wl, precision=prec)
+        plan.set_acceleration(accel)
         ex = W.exact_block(wl, wl.instances[0], plan.node_grid(), 0)
         plan.begin_interval(0)
         ms_total, errs, reached, its = 0.0, [], None, []
