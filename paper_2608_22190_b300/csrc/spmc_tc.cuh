@@ -149,12 +149,14 @@ __host__ __device__ constexpr uint32_t kmajor_offset(int row, int k, int KC) {
 // event = one TMEM lane: it writes its row of A, then contracts its TMEM row
 // with P(y) on the FP32 pipe.
 //
-// A block holds NT tile groups of 128 threads; each group has its own A rows,
-// TMEM accumulator (128 columns) and mbarrier, and works through the tiles of
-// the current slice segment independently of the others (named barriers), so
-// that while one group waits for its products the others write rows or finish
-// residuals.  The groups share the slice's B operand, rebuilt at segment
-// boundaries.
+// One block per SM holds all 512 TMEM columns and NT tile groups of 128
+// threads (five at NMAX <= 24: N columns each); each group has its own A rows,
+// TMEM accumulator and mbarrier, and works through the tiles of the current
+// slice segment independently of the others (named barriers), so that while one
+// group waits for its products the others write rows or finish residuals.  The
+// groups share the slice's B operand, rebuilt at segment boundaries.  The
+// epilogue's dependent FP32 chains are what the warps wait on most, so the
+// kernel is built for as many groups as TMEM holds (registers capped at 96).
 template <int NMAX>
 struct TcGeom {
   static constexpr int K = NMAX;                 // contraction length (a multiple of 8)
@@ -164,11 +166,12 @@ struct TcGeom {
   static constexpr uint32_t LBO = 128;           // bytes between K-adjacent core matrices
   static constexpr int A_BYTES = 128 * K * 4;    // one tile's rows, hi or lo
   static constexpr int B_BYTES = N * K * 4;
-  static constexpr int NT = 2;                   // tile groups per block
+  static constexpr int NT_FIT = 512 / N;         // accumulators that fit the SM's 512 TMEM columns
+  static constexpr int NT = NT_FIT < 5 ? NT_FIT : 5;   // tile groups per block (one block per SM)
   static constexpr int THREADS = 128 * NT;
-  static constexpr int TM_STRIDE = 128;          // TMEM columns per group (N <= 128)
-  static constexpr int TM_COLS = NT * TM_STRIDE;
-  static constexpr int BLOCKS_PER_SM = 512 / TM_COLS;
+  static constexpr int TM_STRIDE = N;            // TMEM columns per group, inside one 512-column allocation
+  static constexpr int TM_COLS = 512;
+  static constexpr int BLOCKS_PER_SM = 1;
   static constexpr int SMEM = 2 * NT * A_BYTES + 2 * B_BYTES + 8 * NT + 16;   // A, B, mbarriers, TMEM slot
   static constexpr int CHUNK = 16384;            // events per block and step of the block loop
 };
@@ -339,15 +342,17 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
         float sv[4];
 #pragma unroll
         for (int blk = 0; blk < 4; ++blk) {
-          float v[NMAX];
-#pragma unroll
-          for (int c8 = 0; c8 < NMAX / 8; ++c8) tc::tmem_ld8(lane_base + (uint32_t)(blk * NMAX + c8 * 8), v + 8 * c8);
-          tc::tmem_ld_wait();
           float s = 0.f, s2 = 0.f;
 #pragma unroll
-          for (int q = 0; q < NMAX; q += 2) {
-            s = fmaf(v[q], Py[q], s);
-            s2 = fmaf(v[q + 1], Py[q + 1], s2);
+          for (int c8 = 0; c8 < NMAX / 8; ++c8) {   // eight columns at a time: few live registers
+            float v[8];
+            tc::tmem_ld8(lane_base + (uint32_t)(blk * NMAX + c8 * 8), v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+              s = fmaf(v[q], Py[8 * c8 + q], s);
+              s2 = fmaf(v[q + 1], Py[8 * c8 + q + 1], s2);
+            }
           }
           sv[blk] = s + s2;
         }
