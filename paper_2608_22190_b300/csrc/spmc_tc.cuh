@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
   unsigned char* Al = Ah + Gm::A_BYTES;
   const float kappa = (float)kappa_d;
   uint32_t phase = 0;
-  bool ok = true;          // uniform over the group (a vote after every tile)
+  bool ok = true;          // false: a time-out was seen (voted over the group, then over the block)
   bool timed_out = false;  // this group's last MMA did not complete in time
 
   for (unsigned long long c0 = (unsigned long long)blockIdx.x * Gm::CHUNK; c0 < n_events;
@@ -301,13 +301,18 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
       };
       float4 ev_next;
       bool has_next = load_event(grp, ev_next);
+      bool prev_done = true;   // this thread's wait for the group's previous tile completed
       for (int t = grp; t < n_tiles; t += NT) {
         const float4 ev = ev_next;
         const bool has = has_next;
         has_next = load_event(t + NT, ev_next);
+        // the A rows are free: this thread waited for the previous tile's products
         write_a_row<NMAX, FULL>(Ah, Al, gt, ev.x, n);
         tc::fence_async_smem();
-        tc::named_sync(1 + grp, 128);
+        tc::fence_before();
+        // one barrier per tile: the rows are written and the previous tile's
+        // accumulator has been read by every thread; the group agrees on a time-out
+        if (tc::named_sync_or(1 + grp, 128, !prev_done)) { ok = false; timed_out = true; break; }
         if (gt == 0) {
           tc::fence_after();
 #pragma unroll
@@ -388,17 +393,17 @@ __global__ void __launch_bounds__(TcGeom<NMAX>::THREADS, TcGeom<NMAX>::BLOCKS_PE
 #pragma unroll
         for (int k = 0; k < 5; ++k) L[k] = __reduce_add_sync(peers, L[k]);
         if (done && has && lane == start) fix_atomic_add(acc + 4 * (node0 + (long long)key), fix_from_limbs(L));
-        tc::fence_before();
-        // TMEM read and A free before the group's next tile; the group agrees on a time-out
-        if (tc::named_sync_or(1 + grp, 128, !done)) { ok = false; timed_out = true; break; }
+        prev_done = done;
       }
+      // a time-out in the segment's last tile stops the block at the next block barrier
+      if (!prev_done) { ok = false; timed_out = true; }
       pos = g1;
     }
     if (__syncthreads_or(!ok)) { ok = false; break; }
   }
   if (timed_out) {
     // an MMA of this group did not complete in time: report, give it one more bounded wait
-    if (gt == 0) atomicOr(status, 8);
+    atomicOr(status, 8);
     tc::mbar_wait_bounded(mbar + grp, phase ^ 1u);
   }
   tc::fence_before();
