@@ -48,3 +48,23 @@ def test_invalid_plans_rejected_without_gpu():
         assert not h.value
     assert L.lib.spmc_plan(None, C.byref(h)) == L.SPMC_ERR_INVALID
     assert L.lib.spmc_version().startswith(b"spmc-b300")
+
+
+def test_walk_division_by_invariant_integers(tmp_path):
+    """The walk splits walk ids with a multiply-shift quotient (FastDiv,
+    Granlund-Montgomery); built by nvcc for the host and run on the host
+    cores, it equals the integer quotient for every divisor below 4096 on
+    every numerator below 2^16 and at the top of the 32-bit range, and for
+    random divisors of every bit length next to multiples of the divisor."""
+    import shutil
+    import subprocess
+    nvcc = os.environ.get("NVCC", "nvcc")
+    if shutil.which(nvcc) is None:
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "fastdiv_check")
+    src = os.path.join(ROOT, "tests", "fastdiv_host_check.cu")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17", "-o", exe, src],
+                   check=True, capture_output=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "0 wrong" in r.stdout
