@@ -476,6 +476,8 @@ def time_to_tol_legs(args, tol=1e-6):
         workload, all 20 intervals; mixed at the headline's M = 65536 and at
         M = 2048, plain FP64 at M = 2048 (the FP64 pipe would take about an hour
         at 65536), so mixed and FP64 also compare at equal M;
+      w2_full_mixed_M512 / _M1024 / _M4096: mixed at other sample counts (up
+        to 50 iterations per interval), to find the fastest way to the tolerance;
       w1_mixed / w1_fp64: the 1-D single-interval workload at its full size
         (M = 4096), with the L-inf distance of every iterate from the FP64
         oracle's iterate on the same streams (computed on the host cores
@@ -537,6 +539,8 @@ def time_to_tol_legs(args, tol=1e-6):
         plan.close()
     out["w2_full_mixed"] = hp_time_to_tol(W.w2(M=args.M), L.MIXED, tol, 12)
     out["w2_full_mixed_M2048"] = hp_time_to_tol(W.w2(M=2048), L.MIXED, tol, 16)
+    for m in (512, 1024, 4096):   # the samples per iteration that reach the tolerance fastest
+        out[f"w2_full_mixed_M{m}"] = hp_time_to_tol(W.w2(M=m), L.MIXED, tol, 50)
     out["w2_full_mixed_M2048_aitken"] = hp_time_to_tol(W.w2(M=2048), L.MIXED, tol, 16, accel="aitken")
     out["w2_full_fp64"] = hp_time_to_tol(W.w2(M=2048), L.FP64, tol, 16)
     ref = fut.result()
@@ -545,7 +549,8 @@ def time_to_tol_legs(args, tol=1e-6):
         out[name]["linf_vs_oracle_by_iteration"] = [float(np.abs(g - r).max())
                                                      for g, r in zip(gpu_iterates[name], ref)]
     fp = out["w2_full_fp64"]
-    for name in ("w2_full_mixed", "w2_full_mixed_M2048", "w2_full_mixed_M2048_aitken"):
+    for name in ("w2_full_mixed", "w2_full_mixed_M2048", "w2_full_mixed_M2048_aitken", "w2_full_mixed_M512",
+                 "w2_full_mixed_M1024", "w2_full_mixed_M4096"):
         if out[name]["reached"] and fp["reached"]:
             out[name]["speedup_over_fp64_M2048"] = fp["ms"] / out[name]["ms"]
     return out
