@@ -98,6 +98,8 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
   static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
   static __device__ __forceinline__ double abs_(double a) { return ::fabs(a); }
+  // a / b given inv_b = 1 / b: the FP64 walk divides (step for step as the CPU reference)
+  static __device__ __forceinline__ double divr(double a, double b, double) { return __ddiv_rn(a, b); }
   static __device__ __forceinline__ double log_(double a) { return log(a); }
   static __device__ __forceinline__ void sincos2pi(double U, double* s, double* c) { sincospi(2.0 * U, s, c); }
   static __device__ __forceinline__ double sinpi_(double x) { return sinpi(x); }
@@ -113,6 +115,8 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
   static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
   static __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
+  // a / b given inv_b = 1 / b: the FP32 walk multiplies by the reciprocal
+  static __device__ __forceinline__ float divr(float a, float, float inv_b) { return __fmul_rn(a, inv_b); }
   static __device__ __forceinline__ float log_(float a) { return logf(a); }
   static __device__ __forceinline__ void sincos2pi(float U, float* s, float* c) { sincospif(2.0f * U, s, c); }
   static __device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }

@@ -87,8 +87,8 @@ struct EmitQueue {
 // runs every iteration, and each iteration is a fixed sequence of predicated
 // stages -- take a new walk (lanes whose walk ended), prepare the step (ball,
 // weight, sub-point, roulette), record the event, move to the sphere.  COUNT
-// adds each event to its (slice, node) count at once (lanes with the same key
-// share one atomic).  FILL appends it to its warp's queue; once 32 are queued
+// adds each event to its (slice, node) count at once (one reduction per event,
+// without a return value).  FILL appends it to its warp's queue; once 32 are queued
 // the whole warp computes their Green points (a second Philox block, the radial
 // law, the direction), claims their slots and stores them, all lanes together.
 //
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
   bool live = false, more = true;
   bool pend = false;     // direct estimator: the walk reached t_{n-1}; its initial-term event is next
   bool bc_raw = false;   // direct estimator with raw boundary data: absorbed walks emit the boundary term
-  R X[D], f = R(0), delta = R(0), J = R(0), sub = R(0), t_node = R(0);
+  R X[D], f = R(0), delta = R(0), inv_delta = R(0), J = R(0), sub = R(0), t_node = R(0);
+  const R two_dk = Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), inv_two_dk = Ar<R>::div(R(1), two_dk);
   int k = 0, q = 0, Ktot = 0, key_j = 0;
   long long slice_base = 0, cached_ti = -1;
   uint32_t node_ell = 0;
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
             const TimeNode node = a.tn[ti];
             const R sdur = Ar<R>::sub((R)node.t_node, (R)node.t0);
             delta = Ar<R>::div(sdur, (R)node.nstar);
+            inv_delta = Ar<R>::div(R(1), delta);
             J = Ar<R>::sqrt_(Ar<R>::mul(Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa), delta));
             sub = Ar<R>::div(delta, (R)G);
             Ktot = G * node.nstar;
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
           }
         } else {
           r = dist;
-          w = Ar<R>::div(Ar<R>::mul(r, r), Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa));
+          w = Ar<R>::divr(Ar<R>::mul(r, r), two_dk, inv_two_dk);
           m = k;
           if (w >= left) { w = left; last = true; }
           else {
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
         }
         wstep = w;
         // roulette for shrunk balls
-        if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D) & 3], Ar<R>::div(w, delta)) ? delta : R(0);
+        if (r < J && w > R(0)) w = roulette_keep<R>(b0.v[rword_index(D) & 3], Ar<R>::divr(w, delta, inv_delta)) ? delta : R(0);
         emit = w > R(0);
         // keys fit 32 bits (the host checks n_slices S < 2^32)
         key = ((uint32_t)slice_base + (uint32_t)m) * (uint32_t)S + (uint32_t)key_j;
@@ -315,10 +317,7 @@ __global__ void __launch_bounds__(256, (D <= 2 && sizeof(R) == 4) ? 4 : 2) walk_
     // ---- stage 3: the event
     const unsigned int emask = __ballot_sync(0xffffffffu, emit);
     if (!FILL) {
-      if (emit) {
-        const unsigned int peers = __match_any_sync(emask, key);
-        if ((int)lane == __ffs(peers) - 1) atomicAdd(&a.counts[key], (unsigned int)__popc(peers));
-      }
+      if (emit) atomicAdd(&a.counts[key], 1u);   // a reduction: the old value is not used
     } else if (emask) {
       if (emit) {
         const int pos = qn + __popc(emask & lt_mask);

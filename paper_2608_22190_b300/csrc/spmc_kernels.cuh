@@ -417,7 +417,8 @@ __device__ __forceinline__ void prepare_step(const WalkState<D, R>& st, int s, c
     }
   } else {
     r = dist;
-    w = Ar<R>::div(Ar<R>::mul(r, r), Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa));
+    const R two_dk = Ar<R>::mul(Ar<R>::mul(R(2), R(D)), kappa);
+    w = Ar<R>::divr(Ar<R>::mul(r, r), two_dk, Ar<R>::div(R(1), two_dk));
     m = k;
     if (w >= left) { w = left; last = 1; }
     else {
@@ -654,7 +655,7 @@ sweep_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict__
             // then weighted Delta (unbiased Russian roulette)
             if (r < J && w > R(0)) {
               const uint32_t rw = stream_word(ws, w0 + rword_index(D));
-              w = roulette_keep<R>(rw, Ar<R>::div(w, delta)) ? delta : R(0);
+              w = roulette_keep<R>(rw, Ar<R>::divr(w, delta, Ar<R>::div(R(1), delta))) ? delta : R(0);
             }
           }
           if (w > R(0)) {
@@ -1412,7 +1413,7 @@ sweep5_kernel(SweepArgs a, int JT, int CC, long long n_cohorts, int* __restrict_
           R w = st.w[wk];
           if (r < J && w > R(0)) {
             const uint32_t rw = stream_word(ws, w0 + rword_index(D));
-            w = roulette_keep<R>(rw, Ar<R>::div(w, delta)) ? delta : R(0);
+            w = roulette_keep<R>(rw, Ar<R>::divr(w, delta, Ar<R>::div(R(1), delta))) ? delta : R(0);
           }
           if (w > R(0)) {
             R thg[D];
