@@ -38,7 +38,7 @@ extern "C" {
 typedef enum {
   SPMC_OK = 0,
   SPMC_ERR_INVALID = 1,      /* bad argument or plan state */
-  SPMC_ERR_UNSUPPORTED = 2,  /* valid request outside what this build implements */
+  SPMC_ERR_UNSUPPORTED = 2,  /* valid request outside what this library implements */
   SPMC_ERR_CUDA = 3,         /* a CUDA runtime call failed */
   SPMC_ERR_OOM = 4,          /* device allocation failed */
   SPMC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
@@ -163,7 +163,7 @@ typedef struct {
 
 /* Validate desc, build the node tables and allocate the workspace.
  * Errors: SPMC_ERR_INVALID (out-of-range field), SPMC_ERR_UNSUPPORTED (dim or
- * size this build does not implement), SPMC_ERR_OOM, SPMC_ERR_CUDA.
+ * size this library does not implement), SPMC_ERR_OOM, SPMC_ERR_CUDA.
  * *out is NULL on failure. */
 spmc_status spmc_plan(const spmc_plan_desc* desc, spmc_plan_t* out);
 
