@@ -196,12 +196,18 @@ def sweep_roofline(wl, prec, points, st, peaks, steps, step_ms):
     # DRAM bytes per event from one ncu capture of each kernel as it is now
     # (profiles/walk_events_w2_fullset.md, profiles/eval_tc_w2_fullset.md: M = 1024,
     # 1.0212e8 events), scaled by the events of one launch; traffic grows with the events
-    per_event_bytes = {"walk_count": (0.011807 + 0.0) * 1e9 / 1.02118e8,
-                       "walk_fill": (0.605840 + 2.131090) * 1e9 / 1.02118e8,
+    per_event_bytes = {"walk_fill": (0.605840 + 2.131090) * 1e9 / 1.02118e8,
                        "eval_tc": (1.664608 + 0.005134) * 1e9 / 1.02118e8}
+    # the counting pass reads its tables and keeps the counts in L2: its DRAM traffic
+    # does not grow with the events (0.0118 GB read, nothing written, per launch)
+    per_launch_bytes = {"walk_count": 0.011807e9}
     launches = max(1, st["eval_launches"])
     for k, v in kern.items():
-        v["traffic"] = per_event_bytes[k] * points / launches if (k in per_event_bytes and wl.dim == 2) else None
+        v["traffic"] = None
+        if wl.dim == 2 and k in per_event_bytes:
+            v["traffic"] = per_event_bytes[k] * points / launches
+        elif wl.dim == 2 and k in per_launch_bytes:
+            v["traffic"] = per_launch_bytes[k]
     name = max(kern, key=lambda k: kern[k]["ms"]) if kern else None
     roof = dict(kern[name]) if name else {}
     if name:
